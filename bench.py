@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark: one low-storage RK3 step of the compressible Navier-Stokes residual on the
+256^3 periodic Taylor-Green vortex in binary64, per algorithm family (Jammy, Jacobs &
+Sandham, arXiv 1610.09146: Sections 2-4; the paper times this loop in Table 1).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A "step" is one full RK3 step (three stages: primitives, derivatives, residual, update)
+over all 256^3 points; the metric is point-updates/s = points x steps / seconds.  Each
+family (store-all BL, store-some SS, recompute-all RA) is timed separately; the line's
+`value` is the fastest one.  Inputs: the analytic Taylor-Green initial condition
+(synthetic, no dataset), 671 MB of state per buffer, far above the 129 MB L2, so no
+flush is needed between steps.  Under torchrun (N > 1) every rank advances its own
+256^3 instance (replicas; the single-instance path has no exchange step) and `value`
+is the sum over ranks divided by the slowest rank's time.
+
+`--impl reference` times the FP64 CPU oracle (the checker of the CUDA path) on the
+host cores, one RK3 step of a 256 x 256 x 8 periodic slab per step (same per-point
+arithmetic and grid spacing as the 256^3 grid).
+"""
+from __future__ import annotations
+
+import argparse
+import datetime as _dt
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_GRID = 256
+RE, MACH, PR, GAMMA = 1600.0, 0.1, 0.71, 1.4
+METRIC = "point-updates/s"
+VARIANTS = ["store_all", "store_some", "recompute_all"]
+SHORT = {"store_all": "BL", "store_some": "SS", "recompute_all": "RA"}
+
+# Table 1 (Section 4): run-time in seconds of 500 iterations at 256^3 on one 24-core
+# ARCHER node (24 MPI ranks, Cray C -O3, binary64).  Context only, another machine.
+PAPER_256_SECONDS = {"store_all": 1561.52, "recompute_all": 765.42, "store_some": 685.25}
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# binary64 arithmetic peak of GB300: 152 SMs x 2 FP64 FMA lanes per SM per clock x 2 flop
+# x 2.07 GHz maximum SM clock = 1.26 TFLOP/s (our DFMA-loop probe measured 1.20).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+HBM_FALLBACK_GBS = 6800.0
+
+# Algorithmic cost per grid point of one launch, by (dtype, family, kernel class):
+# (flops with FMA = 2, HBM bytes at ideal reuse, FP64 pipe instructions), each averaged
+# over the three stages.  Counted from the kernel source (see the kernel table of the
+# design notes); the SS fused count agrees with ncu's executed DADD/DMUL/DFMA (257/pt).
+COST = {
+    ("f64", "store_some", "fused"): (395.7, 245.3, 253.7),
+    ("f64", "store_some", "grad"): (45, 96, 36),
+    ("f64", "recompute_all", "fused"): (542.7, 173.3, 357.7),
+    ("f64", "store_all", "fused"): (163, 661.3, 120),
+    ("f64", "store_all", "deriv1"): (225, 576, 180),
+    ("f64", "store_all", "deriv2"): (114, 200, 84),
+    ("f64", "store_all", "products"): (18, 216, 18),
+    ("f64", "*", "prims"): (14, 80, 20),
+    ("f32", "store_some", "fused"): (399.7, 182.7, 0),
+    ("f32", "store_some", "grad"): (45, 48, 0),
+    ("f32", "recompute_all", "fused"): (546.7, 146.7, 0),
+    ("f32", "store_all", "fused"): (167, 390.7, 0),
+    ("f32", "store_all", "deriv1"): (225, 288, 0),
+    ("f32", "store_all", "deriv2"): (114, 100, 0),
+    ("f32", "store_all", "products"): (18, 108, 0),
+    ("f32", "*", "prims"): (14, 80, 2),
+}
+# FP64 pipe issue peak: 2 instructions per SM per clock.
+FP64_PEAK_INSTR = 152 * 2 * 2.07e9
+
+
+def cost_of(dtype, alg, kclass):
+    return COST.get((dtype, alg, kclass)) or COST.get((dtype, "*", kclass))
+
+
+# ---------------------------------------------------------------- utilities
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.windows = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def mark(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = _dt.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            rows.append((ts, parts))
+        inwin = [p for ts, p in rows if any(a <= ts <= b for a, b in self.windows)] or [p for _, p in rows]
+        sm = [float(p[2]) for p in inwin if p[2].replace(".", "", 1).isdigit()]
+        smax = [float(p[3]) for p in inwin if p[3].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in inwin for i in range(4) if p[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(inwin)}
+
+
+def measured_peaks():
+    try:
+        d = json.load(open(MEASURED_PEAKS))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ------------------------------------------------------------- our CUDA path
+
+
+def time_family(fd, torch, alg, dtype, n, steps, warmup, stream, barrier, clocks):
+    from paper_1610_09146_gb300 import native
+    s = fd.Solver(n, Re=RE, Mach=MACH, Pr=PR, gamma=GAMMA, dt=fd.dt_for_grid(n), algorithm=alg, dtype=dtype,
+                  stream=stream)
+    s.step(warmup)
+    torch.cuda.synchronize()
+    native.fd_profile(s.h, 1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    barrier()
+    clocks.mark(t0, t1)
+    ms = e0.elapsed_time(e1)
+    kern = {}
+    for c, name in enumerate(native.KERNEL_CLASS_NAMES):
+        tot, cnt = native.fd_profile_read(s.h, c)
+        if cnt:
+            kern[name] = {"ms_total": tot, "launches": cnt, "ms_avg": tot / cnt}
+    native.fd_profile(s.h, 0)
+    finite = s.check_finite()
+    ke, ens = s.diagnostics()
+    return s, ms, kern, finite, (ke, ens)
+
+
+def roofline_of(dtype, alg, kern, n, hbm_peak, hbm_src):
+    """Roofline entry of the kernel with the largest share of the step."""
+    name, k = max(kern.items(), key=lambda kv: kv[1]["ms_total"])
+    flops_pt, bytes_pt, instr_pt = cost_of(dtype, alg, name)
+    sec = k["ms_avg"] / 1e3
+    gbs = bytes_pt * n / sec / 1e9
+    tflops = flops_pt * n / sec / 1e12
+    if dtype == "f64":
+        entry = {"kernel": f"{SHORT[alg]}:{name}", "bound": "alu", "achieved": round(tflops, 4),
+                 "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                 "peak_source": "FP64 nominal: 152 SMs x 4 flop/clk x 2.07 GHz",
+                 "fp64_pipe_frac": round(instr_pt * n / sec / FP64_PEAK_INSTR, 4),
+                 "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4)}
+    else:
+        entry = {"kernel": f"{SHORT[alg]}:{name}", "bound": "hbm", "achieved": round(gbs, 1),
+                 "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
+                 "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback"}
+    entry["share"] = round(k["ms_total"] / sum(v["ms_total"] for v in kern.values()), 4)
+    entry["traffic"] = TRAFFIC.get((dtype, alg, name))
+    entry["algorithmic_per_point"] = {"flops": flops_pt, "bytes": bytes_pt, "fp64_instr": instr_pt}
+    return entry
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of a 256^3 launch, from one ncu
+# capture of the current kernel on a 160^3 grid (two launches, 249 B per point) scaled by
+# the point count; None where no capture of the current kernel version exists.
+TRAFFIC = {("f64", "store_some", "fused"): 4.18e9}
+
+
+def e2e_run(fd, torch, s, n, steps, stream):
+    """Same metric through the public API with host buffers: each step copies the state in
+    from pinned host memory, advances one RK3 step and copies the state back."""
+    from paper_1610_09146_gb300 import native
+    nel = 5 * n**3
+    hin = torch.empty(nel, dtype=torch.float64, pin_memory=True)
+    hout = torch.empty(nel, dtype=torch.float64, pin_memory=True)
+    native.fd_get_state(s.h, hin.data_ptr(), nel, 0)
+    native.fd_set_state(s.h, hin.data_ptr(), nel, 0)
+    s.step(1)
+    native.fd_get_state(s.h, hout.data_ptr(), nel, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        native.fd_set_state(s.h, hin.data_ptr(), nel, 0)
+        native.fd_step(s.h, 1)
+        native.fd_get_state(s.h, hout.data_ptr(), nel, 0)
+    t1 = time.perf_counter()
+    return {"value": n**3 * steps / (t1 - t0), "unit": METRIC, "h2d_bytes_per_step": nel * 8,
+            "d2h_bytes_per_step": nel * 8, "steps": steps, "path": "fd_set_state(host) + fd_step(1) + "
+            "fd_get_state(host), pinned buffers"}
+
+
+def cpu_baseline_full(n):
+    """The oracle as it stands: one RK3 step of the full n^3 Taylor-Green grid."""
+    import oracle
+    Q = oracle.tgv_ic(n, n, n, GAMMA, MACH)
+    t0 = time.perf_counter()
+    oracle.run(Q, 1, dt=3.385e-3 * 64 / n, Re=RE, Mach=MACH, Pr=PR, gamma=GAMMA)
+    t = time.perf_counter() - t0
+    return {"value": n**3 / t, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"1 RK3 step of the full {n}^3 grid ({t:.1f} s)"}
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1610_09146_gb300 as fd
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    fd.build()
+    if ws > 1:
+        dist.barrier()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    n = args.grid
+    npts = n**3
+    stream = torch.cuda.Stream()
+    hbm_peak, hbm_src = measured_peaks()
+    clocks = ClockSampler(local)
+    clocks.start()
+    results = {}
+    best = None
+    keep = None
+    for alg in args.variants:
+        s, ms, kern, finite, diag = time_family(fd, torch, alg, args.dtype, n, args.steps, args.warmup, stream,
+                                                barrier, clocks)
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        value = ws * npts * args.steps / (ms / 1e3)
+        launches = sum(k["launches"] for k in kern.values())
+        results[alg] = {"value": value, "ms_per_step": ms / args.steps, "finite": finite, "gpu_launches": launches,
+                        "kernels": kern, "roofline": roofline_of(args.dtype, alg, kern, npts, hbm_peak, hbm_src),
+                        "ke": diag[0], "enstrophy": diag[1],
+                        "paper_table1_256_point_updates_per_s": npts * 500 / PAPER_256_SECONDS[alg]}
+        if best is None or value > results[best]["value"]:
+            best = alg
+            if keep is not None:
+                keep.close()
+            keep = s
+        else:
+            s.close()
+    cl = clocks.stop()
+    e2e = e2e_run(fd, torch, keep, n, max(3, min(args.steps, 10)), stream.cuda_stream)
+    if dist is not None:
+        t = torch.tensor([npts * e2e["steps"] / e2e["value"]], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e["value"] = ws * npts * e2e["steps"] / float(t.item())
+    keep.close()
+    r = results[best]
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": r["value"] / r["paper_table1_256_point_updates_per_s"], "dtype": args.dtype,
+        "data": "synthetic (analytic Taylor-Green vortex initial condition)",
+        "config": {"workload": f"Taylor-Green vortex {n}^3, binary64, one low-storage RK3 step per step, "
+                               "each algorithm family timed separately; value = fastest family",
+                   "family": f"{best} ({SHORT[best]})", "grid": [n, n, n], "Re": RE, "Mach": MACH, "Pr": PR,
+                   "gamma": GAMMA, "dt": fd.dt_for_grid(n),
+                   "l2": f"inputs larger than L2 ({40 * npts / 1e6:.0f} MB state per buffer vs 129 MB L2); no flush",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": r["roofline"], "gpu_launches": r["gpu_launches"], "e2e": e2e, "clocks": cl,
+        "variants": {SHORT[a]: {k: v for k, v in results[a].items() if k != "kernels"} | {
+            "kernels": {kk: round(vv["ms_avg"], 4) for kk, vv in results[a]["kernels"].items()}}
+            for a in results},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_full(n)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ reference arm
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    n, slab = args.grid, 8
+    h = (2 * math.pi / n,) * 3
+    dt = 3.385e-3 * 64 / n
+    Q = np.ascontiguousarray(oracle.tgv_ic(n, n, n, GAMMA, MACH)[:, :slab])
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.run(Q, 1, dt=dt, Re=RE, Mach=MACH, Pr=PR, gamma=GAMMA, h=h)
+        t1 = time.perf_counter()
+        if it >= args.warmup:
+            times.append(t1 - t0)
+    pts = n * n * slab
+    ms = 1e3 * sum(times) / len(times)
+    value = pts / (ms / 1e3)
+    sample = f"one RK3 step of a {n}x{n}x{slab} periodic slab of the {n}^3 grid per step (grid spacing 2*pi/{n})"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (analytic Taylor-Green vortex initial condition)",
+        "config": {"workload": f"Taylor-Green vortex {n}^3, binary64, one low-storage RK3 step per step",
+                   "grid": [n, n, n], "Re": RE, "Mach": MACH, "Pr": PR, "gamma": GAMMA, "dt": dt},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--grid", type=int, default=N_GRID)
+    ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--variants", nargs="+", default=VARIANTS, choices=VARIANTS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

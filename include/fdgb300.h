@@ -1,0 +1,181 @@
+/*
+ * fdgb300.h -- C ABI of the GB300 (sm_103a) explicit finite-difference
+ * Navier-Stokes library.
+ *
+ * The library advances the 3-D compressible Navier-Stokes equations with
+ * constant viscosity (Jammy, Jacobs & Sandham, arXiv 1610.09146, Section 2,
+ * Eqs. 1-7) on the periodic cube [0, 2*pi]^3 (Section 3), discretised with
+ * fourth-order central differences, the skew-symmetric convective form
+ * (Eq. skewscalar), viscous terms expanded to second derivatives, and a
+ * three-stage low-storage Runge-Kutta scheme (Section 2, Fig. 1).  The
+ * initial state is the Taylor-Green vortex used for validation (Section 3).
+ *
+ * Conventions for every function below:
+ *  - Return value 0 (FD_OK) on success, a negative FD_E* code on failure;
+ *    fd_last_error() then gives a one-line message.  No function aborts the
+ *    process, and a failed call leaves the handle usable unless it says so.
+ *  - Device buffers are owned by the library (allocated through the caller's
+ *    fd_alloc callbacks when given, else cudaMalloc) and freed by fd_destroy.
+ *    Host buffers are owned by the caller.
+ *  - A handle is not thread-safe and is bound to one CUDA stream (the one
+ *    given to fd_create, or the legacy default stream when NULL) and to the
+ *    device current at fd_create.  Calls that return data synchronise that
+ *    stream; fd_step only enqueues work.
+ *  - State layout (host or device): double Q[5][nz][ny][nx], x fastest,
+ *    var = (rho, rho*u, rho*v, rho*w, rho*E); grid point (i, j, k) sits at
+ *    (i*2*pi/nx, j*2*pi/ny, k*2*pi/nz).
+ */
+#ifndef FDGB300_H
+#define FDGB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define FD_OK 0
+#define FD_EINVAL (-1)    /* bad argument (size, constant, enum, NULL pointer) */
+#define FD_ENOMEM (-2)    /* device or host allocation failed                  */
+#define FD_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed       */
+#define FD_EUNSTABLE (-4) /* non-finite value found by fd_check_finite          */
+#define FD_EBUSY (-5)     /* resource exhausted (batch slots, server capacity)  */
+
+/* ---- algorithm families (Section 2, paragraphs BL, SS, RA) --------------
+ * FD_STORE_ALL     "BL": every derivative (and every product inside a
+ *                  derivative, via a product work array) is written to a
+ *                  grid-sized work array; the residual is then pointwise.
+ * FD_STORE_SOME    "SS": the nine velocity gradients du_i/dx_j are stored in
+ *                  work arrays; every other derivative is evaluated into
+ *                  thread-local registers inside the fused residual kernel.
+ * FD_RECOMPUTE_ALL "RA": no derivative is stored; every derivative is
+ *                  evaluated from its finite-difference formula where used.
+ * In all three the primitive variables u_i, p, T are evaluated and stored
+ * (Section 2, the paragraph after Fig. 1). */
+#define FD_STORE_ALL 0
+#define FD_STORE_SOME 1
+#define FD_RECOMPUTE_ALL 2
+
+/* ---- arithmetic ----------------------------------------------------------
+ * FD_F64        all arithmetic in IEEE binary64 (the paper's precision,
+ *               Section 3).
+ * FD_F32_ACC64  stencils, fluxes and the residual in binary32 on
+ *               perturbation variables (rho-1, p-p0, T-1, rhoE-rhoE0); the
+ *               conserved state, the Runge-Kutta accumulation and the kinetic
+ *               energy / enstrophy reductions stay in binary64.  The paper has
+ *               no counterpart; it is a precision mode of this library. */
+#define FD_F64 0
+#define FD_F32_ACC64 1
+
+/* Device allocator callbacks (for example PyTorch's caching allocator).
+ * alloc returns a device pointer aligned to at least 256 bytes, or NULL;
+ * free releases a pointer returned by alloc.  Both are called only from
+ * fd_create / fd_destroy (and the batch / server create and destroy calls)
+ * on the caller's thread.  `stream` is the handle's cudaStream_t. */
+typedef struct fd_alloc {
+    void* (*alloc)(void* ctx, size_t bytes, void* stream);
+    void (*free)(void* ctx, void* ptr, size_t bytes, void* stream);
+    void* ctx;
+} fd_alloc;
+
+typedef struct fd_handle fd_handle;
+
+/* Create a solver for an nx x ny x nz periodic grid and set the Taylor-Green
+ * initial condition (Section 3): u = sin x cos y cos z, v = -cos x sin y cos z,
+ * w = 0, p = 1/(gamma M^2) + (cos 2x + cos 2y)(cos 2z + 2)/16, rho = gamma M^2 p.
+ *   nx, ny, nz  grid points per axis, each >= 5 (the 5-point stencil needs
+ *               distinct neighbours) and nx*ny*nz < 2^31;
+ *   Re, Mach, Pr, gamma  flow constants (Eqs. 4-7): Re, Mach, Pr > 0,
+ *               gamma > 1; dt > 0 is the time step of every fd_step;
+ *   algorithm   FD_STORE_ALL, FD_STORE_SOME or FD_RECOMPUTE_ALL;
+ *   dtype       FD_F64 or FD_F32_ACC64;
+ *   alloc       NULL for cudaMalloc/cudaFree, else allocator callbacks;
+ *   cuda_stream cudaStream_t for all work of this handle (NULL = default).
+ * On success *out receives the handle.  Errors: FD_EINVAL, FD_ENOMEM,
+ * FD_ECUDA (then *out is NULL and fd_last_error(NULL) has the message). */
+int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, double Pr,
+              double gamma, double dt, int algorithm, int dtype, const fd_alloc* alloc,
+              void* cuda_stream);
+
+/* Enqueue n >= 0 full time steps (Fig. 1): save-state, then three stages of
+ * primitives -> derivatives -> residual -> periodic boundaries -> update.
+ * Asynchronous on the handle's stream.  Errors: FD_EINVAL (n < 0, NULL),
+ * FD_ECUDA (launch failure). */
+int fd_step(fd_handle* h, int n);
+
+/* Copy the conserved state Q (5*nx*ny*nz doubles, layout above) to dst.
+ * dst_is_device = 1: dst is device memory on the handle's device; 0: host
+ * memory (pageable or pinned).  n_elems must equal 5*nx*ny*nz.  Synchronises
+ * the handle's stream.  Errors: FD_EINVAL, FD_ECUDA. */
+int fd_get_state(fd_handle* h, double* dst, size_t n_elems, int dst_is_device);
+
+/* Replace the conserved state with src (same layout and rules as
+ * fd_get_state); checkpoint / resume at a step boundary.  Synchronises. */
+int fd_set_state(fd_handle* h, const double* src, size_t n_elems, int src_is_device);
+
+/* Kinetic energy and enstrophy of the current state (Section 3, Fig. 3):
+ *   ke  = (1/N) sum rho |u|^2 / 2,
+ *   ens = (1/N) sum rho |omega|^2 / 2, omega = curl u with the 4th-order
+ *         first-derivative stencil, N = nx*ny*nz,
+ * accumulated in binary64 in a fixed order (bitwise reproducible run to run).
+ * Synchronises.  Either output pointer may be NULL. */
+int fd_diagnostics(fd_handle* h, double* ke, double* enstrophy);
+
+/* Evaluate the residual R(Q) of the mass, momentum and energy equations
+ * (Section 2, Eqs. 1-5 with Eq. skewscalar) of the current state without
+ * advancing it, with the handle's algorithm and dtype, into R (5*nx*ny*nz
+ * doubles, layout of Q) on the host (dst_is_device = 0) or device (1).
+ * Synchronises.  Errors: FD_EINVAL, FD_ECUDA. */
+int fd_residual(fd_handle* h, double* R, size_t n_elems, int dst_is_device);
+
+/* Scan the state for NaN or infinity.  Returns FD_OK or FD_EUNSTABLE.
+ * Synchronises. */
+int fd_check_finite(fd_handle* h);
+
+/* Bytes of device memory held by the handle (state, primitives, work arrays). */
+size_t fd_device_bytes(const fd_handle* h);
+
+/* ---- per-kernel timing ----------------------------------------------------
+ * Kernel classes of one stage (Fig. 1), for fd_profile_read:
+ *   FD_KERNEL_PRIMS     primitive variables u_i, p, T (Eqs. 6-7), all families
+ *   FD_KERNEL_GRAD      SS: the nine stored velocity gradients
+ *   FD_KERNEL_FUSED     RA / SS: fused derivatives + residual + RK update;
+ *                       BL: pointwise residual + RK update
+ *   FD_KERNEL_PRODUCTS  BL: product work arrays
+ *   FD_KERNEL_DERIV1    BL: first-derivative work arrays
+ *   FD_KERNEL_DERIV2    BL: second- and mixed-derivative work arrays */
+#define FD_KERNEL_PRIMS 0
+#define FD_KERNEL_GRAD 1
+#define FD_KERNEL_FUSED 2
+#define FD_KERNEL_PRODUCTS 3
+#define FD_KERNEL_DERIV1 4
+#define FD_KERNEL_DERIV2 5
+#define FD_KERNEL_CLASSES 6
+
+/* Turn per-kernel timing on (enable != 0) or off; either way the totals are
+ * reset.  While on, every launch of fd_step / fd_residual is bracketed by a
+ * pair of CUDA events recorded on the handle's stream (a few microseconds
+ * per launch); events are created on the first enable and freed by
+ * fd_destroy.  Errors: FD_EINVAL, FD_ECUDA. */
+int fd_profile(fd_handle* h, int enable);
+
+/* Total device time in milliseconds and number of launches of one kernel
+ * class since the last fd_profile call.  Synchronises the stream.  Either
+ * output may be NULL.  Errors: FD_EINVAL (class out of range), FD_ECUDA. */
+int fd_profile_read(fd_handle* h, int kernel_class, double* total_ms, long long* launches);
+
+/* Free every device buffer of the handle and the handle itself.  NULL is a
+ * no-op.  Synchronises the handle's stream first. */
+int fd_destroy(fd_handle* h);
+
+/* Message of the last failed call on h, or of the last failed call that had
+ * no handle (fd_create, or h == NULL) on this thread.  Never NULL; "" when
+ * there was none.  Valid until the next call on the same handle / thread. */
+const char* fd_last_error(const fd_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDGB300_H */

@@ -1,0 +1,153 @@
+"""GB300 (sm_103a) explicit finite-difference compressible Navier-Stokes solver.
+
+The method is that of Jammy, Jacobs & Sandham, "Performance evaluation of
+explicit finite difference algorithms with varying amounts of computational
+and memory intensity" (arXiv 1610.09146): fourth-order central differences,
+skew-symmetric convection, viscous terms expanded to second derivatives and a
+low-storage three-stage Runge-Kutta scheme on the periodic Taylor-Green
+vortex (Sections 2 and 3), in the paper's store-all (BL), store-some (SS)
+and recompute-all (RA) algorithm families.
+
+All arithmetic runs in the CUDA kernels of ``libfdgb300.so`` behind the C ABI
+of ``include/fdgb300.h``; this package only marshals arguments.  PyTorch
+provides device memory (through the allocator callbacks) and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import native
+from .native import (FD_EBUSY, FD_ECUDA, FD_EINVAL, FD_ENOMEM, FD_EUNSTABLE, FD_F32_ACC64, FD_F64, FD_OK,
+                     FD_RECOMPUTE_ALL, FD_STORE_ALL, FD_STORE_SOME, FdAlloc, FdError, fd_check_finite, fd_create,
+                     fd_destroy, fd_device_bytes, fd_diagnostics, fd_get_state, fd_last_error, fd_residual,
+                     fd_set_state, fd_step)
+
+ALGORITHMS = {"store_all": FD_STORE_ALL, "store_some": FD_STORE_SOME, "recompute_all": FD_RECOMPUTE_ALL,
+              "BL": FD_STORE_ALL, "SS": FD_STORE_SOME, "RA": FD_RECOMPUTE_ALL}
+DTYPES = {"f64": FD_F64, "f32": FD_F32_ACC64, "f32_acc64": FD_F32_ACC64}
+
+# Section 3: time step 3.385e-3 on 64^3, halved for each doubling of the grid.
+DT_64 = 3.385e-3
+
+
+def dt_for_grid(n: int) -> float:
+    """Time step of the paper's validation runs for an n^3 grid (n >= 64), following the
+    rule of Section 3 (dt = 3.385e-3 at 64^3, halved per doubling of n); smaller grids
+    keep the 64^3 value."""
+    return DT_64 * 64.0 / max(int(n), 64)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    from .build import build as _b
+    return _b(force=force, verbose=verbose)
+
+
+_torch_alloc_keep = []
+
+
+def torch_allocator() -> FdAlloc:
+    """Allocator callbacks backed by PyTorch's CUDA caching allocator."""
+    import torch
+
+    def _alloc(ctx, nbytes, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device=torch.cuda.current_device(),
+                                                      stream=int(stream or 0))
+        except Exception:  # an out-of-memory error becomes a NULL return (FD_ENOMEM)
+            return None
+
+    def _free(ctx, ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a = FdAlloc(native.ALLOC_FN(_alloc), native.FREE_FN(_free), None)
+    _torch_alloc_keep.append(a)  # the callbacks must outlive every handle using them
+    return a
+
+
+class Solver:
+    """One Taylor-Green instance on an nx x ny x nz periodic grid.
+
+    algorithm: "store_all" | "store_some" | "recompute_all" (or "BL" | "SS" | "RA")
+    dtype: "f64" | "f32" (binary32 stencils, binary64 state and reductions)
+    stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (current torch stream)
+    """
+
+    def __init__(self, n, Re=1600.0, Mach=0.1, Pr=0.71, gamma=1.4, dt=None, algorithm="store_some",
+                 dtype="f64", stream=None, use_torch_allocator=True):
+        nx, ny, nz = (n, n, n) if isinstance(n, int) else tuple(n)
+        self.shape = (nz, ny, nx)
+        self.dt = dt_for_grid(max(nx, ny, nz)) if dt is None else float(dt)
+        self.algorithm = ALGORITHMS[algorithm] if isinstance(algorithm, str) else int(algorithm)
+        self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.stream = int(stream)
+        self._alloc = torch_allocator() if use_torch_allocator else None
+        self.h = fd_create(nx, ny, nz, Re, Mach, Pr, gamma, self.dt, self.algorithm, self.dtype, self._alloc,
+                           self.stream)
+
+    @property
+    def n_elems(self) -> int:
+        return 5 * math.prod(self.shape)
+
+    def step(self, n: int = 1):
+        fd_step(self.h, n)
+
+    def state(self, out=None):
+        """The conserved state [5][nz][ny][nx] as a host numpy array, or into `out`
+        (a numpy array, or a CUDA float64 torch tensor)."""
+        if out is None:
+            out = np.empty((5,) + self.shape)
+        if isinstance(out, np.ndarray):
+            fd_get_state(self.h, out)
+        else:
+            fd_get_state(self.h, out.data_ptr(), out.numel(), 1)
+        return out
+
+    def set_state(self, src):
+        if isinstance(src, np.ndarray):
+            fd_set_state(self.h, np.ascontiguousarray(src, dtype=np.float64))
+        else:
+            fd_set_state(self.h, src.data_ptr(), src.numel(), 1)
+
+    def residual(self, out=None):
+        if out is None:
+            out = np.empty((5,) + self.shape)
+        if isinstance(out, np.ndarray):
+            fd_residual(self.h, out)
+        else:
+            fd_residual(self.h, out.data_ptr(), out.numel(), 1)
+        return out
+
+    def diagnostics(self):
+        """(kinetic energy, enstrophy) of the current state."""
+        return fd_diagnostics(self.h)
+
+    def check_finite(self) -> bool:
+        return fd_check_finite(self.h) == FD_OK
+
+    def device_bytes(self) -> int:
+        return fd_device_bytes(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

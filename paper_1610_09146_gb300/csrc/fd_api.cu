@@ -1,0 +1,538 @@
+// fd_api.cu -- implementation of the C ABI declared in include/fdgb300.h.
+//
+// A handle owns one device allocation, carved into 256-byte-aligned arrays:
+//   Q[2]  ping-pong conserved state (5 arrays each): a stage reads Q[cur]
+//         through its stencils and writes Q[1-cur], so no thread overwrites
+//         a value a neighbour still reads (the race Section 2 avoids by
+//         splitting loops in BL);
+//   Qs    the saved RK register (Fig. 1, save-state), updated pointwise;
+//   W     primitives u, v, w, p, T (stored in every family, Section 2);
+//   work  SS: 9 velocity-gradient arrays; BL: 18 product + 45 first- and 18
+//         second-derivative arrays;
+//   mixed-precision arrays (FD_F32_ACC64) and the reduction scratch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fdgb300.h"
+#include "fd_internal.h"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kRkA[3] = {2.0 / 3.0, 5.0 / 12.0, 3.0 / 5.0};
+constexpr double kRkB[3] = {1.0 / 4.0, 3.0 / 20.0, 0.0};
+
+thread_local std::string g_err;
+
+int fail_global(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+// Per-kernel timing: CUDA events recorded around each launch on the
+// handle's own stream, folded into totals when the ring fills or on read.
+struct Profiler {
+    static constexpr int kCap = 2048;
+    bool on = false;
+    std::vector<cudaEvent_t> ev;  // 2 * kCap events, created on first enable
+    std::vector<int> cls;         // kernel class of each pending pair
+    int used = 0;
+    double total_ms[FD_KERNEL_CLASSES] = {};
+    long long count[FD_KERNEL_CLASSES] = {};
+};
+
+struct fd_handle {
+    int nx = 0, ny = 0, nz = 0, n = 0;
+    double Re = 0, Mach = 0, Pr = 0, gamma = 0, dt = 0;
+    int algorithm = 0, dtype = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    fd_alloc alloc{};
+    bool has_alloc = false;
+    void* block = nullptr;
+    size_t block_bytes = 0;
+    double* Q[2] = {nullptr, nullptr};
+    int cur = 0;
+    double* Qs = nullptr;
+    double* W = nullptr;
+    double* G = nullptr;   // SS
+    double* P = nullptr;   // BL
+    double* D1 = nullptr;  // BL
+    double* D2 = nullptr;  // BL
+    float* Wf = nullptr;   // mixed: perturbation fields (10 arrays)
+    float* Gf = nullptr;   // mixed SS: 9 gradients
+    double* partial = nullptr;
+    double* diag = nullptr;
+    int* flag = nullptr;
+    fd::Grid grid{};
+    fd::Phys phys{};
+    fd::Coef<double> kd{};  // fused-residual coefficients, binary64 mode
+    fd::Coef<float> kf{};   // and binary32 perturbation mode
+    Profiler prof;
+
+    template <class T>
+    const fd::Coef<T>& coef() const;
+    std::string err;
+
+    int fail(int code, const char* fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        err = buf;
+        return code;
+    }
+    int cuda_fail(cudaError_t e, const char* what) {
+        return fail(FD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    }
+};
+
+template <>
+const fd::Coef<double>& fd_handle::coef<double>() const {
+    return kd;
+}
+template <>
+const fd::Coef<float>& fd_handle::coef<float>() const {
+    return kf;
+}
+
+namespace {
+
+// Host-side constants of the fused residual (see fd::Coef).
+template <class T>
+fd::Coef<T> make_coef(const fd::Grid& g, const fd::Phys& ph, bool shifted) {
+    fd::Coef<T> k{};
+    for (int j = 0; j < 3; ++j) {
+        double s1 = g.inv12h[j], s2 = g.inv12h2[j];
+        k.s1[j] = (T)s1;
+        k.c1[j] = (T)(-0.5 * s1);
+        k.cp[j] = (T)(-s1);
+        k.ks2[j] = (T)(ph.kappa * s2);
+        k.vmix1[j] = (T)(ph.nu / 3.0 * s1);
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            k.vs2[i][j] = (T)(ph.nu * g.inv12h2[j] * (i == j ? 4.0 / 3.0 : 1.0));
+            k.vmix[i][j] = (T)(ph.nu / 3.0 * g.inv12h[i] * g.inv12h[j]);
+        }
+    k.nu = (T)ph.nu;
+    k.c_rho = shifted ? (T)-1.0 : (T)0.0;
+    k.c_E = shifted ? (T)(-(ph.rhoE0 + ph.p0)) : (T)0.0;
+    return k;
+}
+
+int check_args(int nx, int ny, int nz, double Re, double Mach, double Pr, double gamma, double dt, int algorithm,
+               int dtype) {
+    if (nx < 5 || ny < 5 || nz < 5)
+        return fail_global(FD_EINVAL, "grid %dx%dx%d: every axis needs at least 5 points", nx, ny, nz);
+    if ((long long)nx * ny * nz >= (1LL << 31))
+        return fail_global(FD_EINVAL, "grid %dx%dx%d: nx*ny*nz must be below 2^31", nx, ny, nz);
+    if (!(Re > 0) || !(Mach > 0) || !(Pr > 0) || !(dt > 0) || !std::isfinite(Re) || !std::isfinite(Mach) ||
+        !std::isfinite(Pr) || !std::isfinite(dt))
+        return fail_global(FD_EINVAL, "Re, Mach, Pr and dt must be positive and finite");
+    if (!(gamma > 1) || !std::isfinite(gamma)) return fail_global(FD_EINVAL, "gamma must be > 1");
+    if (algorithm != FD_STORE_ALL && algorithm != FD_STORE_SOME && algorithm != FD_RECOMPUTE_ALL)
+        return fail_global(FD_EINVAL, "unknown algorithm %d", algorithm);
+    if (dtype != FD_F64 && dtype != FD_F32_ACC64) return fail_global(FD_EINVAL, "unknown dtype %d", dtype);
+    return FD_OK;
+}
+
+// Byte layout of a handle's single device allocation.
+struct Layout {
+    size_t q0, q1, qs, w, g, p, d1, d2, wf, gf, partial, diag, flag, total;
+};
+
+Layout plan(long long n, int algorithm, int dtype) {
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off += align256(bytes);
+        return at;
+    };
+    size_t f5 = 5 * n * sizeof(double);
+    L.q0 = take(f5);
+    L.q1 = take(f5);
+    L.qs = take(f5);
+    L.w = take(f5);
+    L.g = L.p = L.d1 = L.d2 = L.wf = L.gf = (size_t)-1;
+    if (dtype == FD_F64) {
+        if (algorithm == FD_STORE_SOME) L.g = take(9 * n * sizeof(double));
+        if (algorithm == FD_STORE_ALL) {
+            L.p = take(18 * n * sizeof(double));
+            L.d1 = take(45 * n * sizeof(double));
+            L.d2 = take(18 * n * sizeof(double));
+        }
+    } else {
+        L.wf = take(10 * n * sizeof(float));
+        if (algorithm == FD_STORE_SOME) L.gf = take(9 * n * sizeof(float));
+        if (algorithm == FD_STORE_ALL) {
+            L.p = take(18 * n * sizeof(float));
+            L.d1 = take(45 * n * sizeof(float));
+            L.d2 = take(18 * n * sizeof(float));
+        }
+    }
+    L.partial = take(2 * fd::kDiagBlocks * sizeof(double));
+    L.diag = take(2 * sizeof(double));
+    L.flag = take(sizeof(int));
+    L.total = off;
+    return L;
+}
+
+template <class T>
+T* at(void* base, size_t off) {
+    return off == (size_t)-1 ? nullptr : reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+void device_free(fd_handle* h) {
+    if (!h->block) return;
+    if (h->has_alloc)
+        h->alloc.free(h->alloc.ctx, h->block, h->block_bytes, h->stream);
+    else
+        cudaFree(h->block);
+    h->block = nullptr;
+}
+
+cudaError_t prof_fold(fd_handle* h) {
+    Profiler& P = h->prof;
+    if (P.used == 0) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < P.used; ++i) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, P.ev[2 * i], P.ev[2 * i + 1]);
+        if (e != cudaSuccess) return e;
+        P.total_ms[P.cls[i]] += ms;
+        P.count[P.cls[i]] += 1;
+    }
+    P.used = 0;
+    return cudaSuccess;
+}
+
+// Launch one kernel (the callable returns its launch status), bracketed by a
+// pair of events when profiling is on.
+template <class F>
+cudaError_t timed(fd_handle* h, int cls, F launch) {
+    Profiler& P = h->prof;
+    if (!P.on) return launch();
+    if (P.used == Profiler::kCap) {
+        cudaError_t e = prof_fold(h);
+        if (e != cudaSuccess) return e;
+    }
+    cudaEvent_t a = P.ev[2 * P.used], b = P.ev[2 * P.used + 1];
+    cudaError_t e = cudaEventRecord(a, h->stream);
+    if (e != cudaSuccess) return e;
+    e = launch();
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(b, h->stream);
+    if (e != cudaSuccess) return e;
+    P.cls[P.used++] = cls;
+    return cudaSuccess;
+}
+
+// Kernels of one stage of family `alg` in precision T.
+template <class T>
+cudaError_t stage_kernels(fd_handle* h, const fd::RKStage& rk, bool resid, const T* Qf, const T* Wf, T* G, T* P,
+                          T* D1, T* D2, const double* Qin, double* Qout) {
+    const fd::Grid& g = h->grid;
+    const fd::Phys& ph = h->phys;
+    const fd::Coef<T>& k = h->coef<T>();
+    cudaStream_t st = h->stream;
+    cudaError_t e;
+    switch (h->algorithm) {
+        case FD_RECOMPUTE_ALL:
+            return timed(h, FD_KERNEL_FUSED,
+                         [&] { return fd::launch_ra<T>(g, k, rk, resid, Qf, Wf, Qin, Qout, h->Qs, st); });
+        case FD_STORE_SOME:
+            e = timed(h, FD_KERNEL_GRAD, [&] { return fd::launch_ss_grad<T>(g, k, Wf, G, st); });
+            if (e != cudaSuccess) return e;
+            return timed(h, FD_KERNEL_FUSED,
+                         [&] { return fd::launch_ss<T>(g, k, rk, resid, Qf, Wf, G, Qin, Qout, h->Qs, st); });
+        default:
+            e = timed(h, FD_KERNEL_PRODUCTS, [&] { return fd::launch_bl_prod<T>(g, Qf, Wf, P, st); });
+            if (e != cudaSuccess) return e;
+            e = timed(h, FD_KERNEL_DERIV1, [&] { return fd::launch_bl_d1<T>(g, Qf, Wf, P, D1, st); });
+            if (e != cudaSuccess) return e;
+            e = timed(h, FD_KERNEL_DERIV2, [&] { return fd::launch_bl_d2<T>(g, Wf, D1, D2, st); });
+            if (e != cudaSuccess) return e;
+            return timed(h, FD_KERNEL_FUSED, [&] {
+                return fd::launch_bl_res<T>(g, ph, rk, resid, Qf, Wf, D1, D2, Qin, Qout, h->Qs, st);
+            });
+    }
+}
+
+// One RK stage (s = 0, 1, 2), or the bare residual into `out` when resid:
+// primitives (Fig. 1, evaluate-u_i,p,T), then the family's derivative and
+// residual kernels, the last of which applies the RK update.
+cudaError_t run_stage(fd_handle* h, int s, bool resid, double* out) {
+    const fd::Grid& g = h->grid;
+    const fd::Phys& ph = h->phys;
+    fd::RKStage rk{kRkA[s] * h->dt, kRkB[s] * h->dt, s};
+    const double* Qin = h->Q[h->cur];
+    double* Qout = resid ? out : h->Q[1 - h->cur];
+    cudaError_t e;
+    if (h->dtype == FD_F64) {
+        e = timed(h, FD_KERNEL_PRIMS, [&] { return fd::launch_prims_f64(g, ph, Qin, h->W, h->stream); });
+        if (e != cudaSuccess) return e;
+        return stage_kernels<double>(h, rk, resid, Qin, h->W, h->G, h->P, h->D1, h->D2, Qin, Qout);
+    }
+    e = timed(h, FD_KERNEL_PRIMS, [&] { return fd::launch_prims_f32(g, ph, Qin, h->Wf, h->stream); });
+    if (e != cudaSuccess) return e;
+    const long long n = h->n;
+    return stage_kernels<float>(h, rk, resid, h->Wf, h->Wf + 5 * n, h->Gf, reinterpret_cast<float*>(h->P),
+                                reinterpret_cast<float*>(h->D1), reinterpret_cast<float*>(h->D2), Qin, Qout);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, double Pr, double gamma, double dt,
+              int algorithm, int dtype, const fd_alloc* alloc, void* cuda_stream) {
+    if (!out) return fail_global(FD_EINVAL, "fd_create: out is NULL");
+    *out = nullptr;
+    int rc = check_args(nx, ny, nz, Re, Mach, Pr, gamma, dt, algorithm, dtype);
+    if (rc != FD_OK) return rc;
+    if (alloc && (!alloc->alloc || !alloc->free))
+        return fail_global(FD_EINVAL, "fd_create: allocator needs both alloc and free");
+    fd_handle* h = new (std::nothrow) fd_handle();
+    if (!h) return fail_global(FD_ENOMEM, "fd_create: host allocation failed");
+    h->nx = nx;
+    h->ny = ny;
+    h->nz = nz;
+    h->n = nx * ny * nz;
+    h->Re = Re;
+    h->Mach = Mach;
+    h->Pr = Pr;
+    h->gamma = gamma;
+    h->dt = dt;
+    h->algorithm = algorithm;
+    h->dtype = dtype;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail_global(FD_ECUDA, "fd_create: cudaGetDevice: %s", cudaGetErrorString(e));
+    }
+    Layout L = plan(h->n, algorithm, dtype);
+    h->block_bytes = L.total;
+    if (alloc) {
+        h->alloc = *alloc;
+        h->has_alloc = true;
+        h->block = alloc->alloc(alloc->ctx, L.total, cuda_stream);
+        if (!h->block) {
+            delete h;
+            return fail_global(FD_ENOMEM, "fd_create: allocator returned NULL for %zu bytes", L.total);
+        }
+        if (reinterpret_cast<uintptr_t>(h->block) & 255) {
+            alloc->free(alloc->ctx, h->block, L.total, cuda_stream);
+            delete h;
+            return fail_global(FD_EINVAL, "fd_create: allocator returned a pointer not aligned to 256 bytes");
+        }
+    } else {
+        e = cudaMalloc(&h->block, L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return fail_global(FD_ENOMEM, "fd_create: cudaMalloc(%zu): %s", L.total, cudaGetErrorString(e));
+        }
+    }
+    h->Q[0] = at<double>(h->block, L.q0);
+    h->Q[1] = at<double>(h->block, L.q1);
+    h->Qs = at<double>(h->block, L.qs);
+    h->W = at<double>(h->block, L.w);
+    if (dtype == FD_F64) {
+        h->G = at<double>(h->block, L.g);
+        h->P = at<double>(h->block, L.p);
+        h->D1 = at<double>(h->block, L.d1);
+        h->D2 = at<double>(h->block, L.d2);
+    } else {
+        h->Wf = at<float>(h->block, L.wf);
+        h->Gf = at<float>(h->block, L.gf);
+        h->P = at<double>(h->block, L.p);
+        h->D1 = at<double>(h->block, L.d1);
+        h->D2 = at<double>(h->block, L.d2);
+    }
+    h->partial = at<double>(h->block, L.partial);
+    h->diag = at<double>(h->block, L.diag);
+    h->flag = at<int>(h->block, L.flag);
+
+    double hx = 2.0 * kPi / nx, hy = 2.0 * kPi / ny, hz = 2.0 * kPi / nz;
+    fd::Grid& g = h->grid;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.n = h->n;
+    const double hs[3] = {hx, hy, hz};
+    for (int a = 0; a < 3; ++a) {
+        g.inv12h[a] = 1.0 / (12.0 * hs[a]);
+        g.inv12h2[a] = 1.0 / (12.0 * hs[a] * hs[a]);
+        g.inv12hf[a] = (float)g.inv12h[a];
+        g.inv12h2f[a] = (float)g.inv12h2[a];
+    }
+    fd::Phys& ph = h->phys;
+    ph.gamma = gamma;
+    ph.gm1 = gamma - 1.0;
+    ph.gM2 = gamma * Mach * Mach;
+    ph.nu = 1.0 / Re;
+    ph.kappa = 1.0 / ((gamma - 1.0) * Mach * Mach * Pr * Re);
+    ph.p0 = 1.0 / (gamma * Mach * Mach);
+    ph.rhoE0 = ph.p0 / (gamma - 1.0);
+    h->kd = make_coef<double>(g, ph, false);
+    h->kf = make_coef<float>(g, ph, true);
+
+    e = fd::launch_tgv_ic(g, ph, hx, hy, hz, h->Q[0], h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        device_free(h);
+        delete h;
+        return fail_global(FD_ECUDA, "fd_create: initial condition: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return FD_OK;
+}
+
+int fd_step(fd_handle* h, int n) {
+    if (!h) return fail_global(FD_EINVAL, "fd_step: NULL handle");
+    if (n < 0) return h->fail(FD_EINVAL, "fd_step: n = %d < 0", n);
+    for (int it = 0; it < n; ++it)
+        for (int s = 0; s < 3; ++s) {
+            cudaError_t e = run_stage(h, s, false, nullptr);
+            if (e != cudaSuccess) return h->cuda_fail(e, "fd_step: kernel launch");
+            h->cur = 1 - h->cur;
+        }
+    return FD_OK;
+}
+
+int fd_get_state(fd_handle* h, double* dst, size_t n_elems, int dst_is_device) {
+    if (!h) return fail_global(FD_EINVAL, "fd_get_state: NULL handle");
+    if (!dst) return h->fail(FD_EINVAL, "fd_get_state: dst is NULL");
+    if (n_elems != 5 * (size_t)h->n)
+        return h->fail(FD_EINVAL, "fd_get_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h->n);
+    cudaError_t e = cudaMemcpyAsync(dst, h->Q[h->cur], n_elems * sizeof(double),
+                                    dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "fd_get_state");
+    return FD_OK;
+}
+
+int fd_set_state(fd_handle* h, const double* src, size_t n_elems, int src_is_device) {
+    if (!h) return fail_global(FD_EINVAL, "fd_set_state: NULL handle");
+    if (!src) return h->fail(FD_EINVAL, "fd_set_state: src is NULL");
+    if (n_elems != 5 * (size_t)h->n)
+        return h->fail(FD_EINVAL, "fd_set_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h->n);
+    cudaError_t e = cudaMemcpyAsync(h->Q[h->cur], src, n_elems * sizeof(double),
+                                    src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "fd_set_state");
+    return FD_OK;
+}
+
+int fd_diagnostics(fd_handle* h, double* ke, double* enstrophy) {
+    if (!h) return fail_global(FD_EINVAL, "fd_diagnostics: NULL handle");
+    double out[2];
+    // W is scratch between stages: every stage recomputes it from Q first.
+    cudaError_t e = fd::launch_diagnostics_f64(h->grid, h->Q[h->cur], h->W, h->partial, h->diag, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->diag, sizeof out, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "fd_diagnostics");
+    if (ke) *ke = out[0];
+    if (enstrophy) *enstrophy = out[1];
+    return FD_OK;
+}
+
+int fd_residual(fd_handle* h, double* R, size_t n_elems, int dst_is_device) {
+    if (!h) return fail_global(FD_EINVAL, "fd_residual: NULL handle");
+    if (!R) return h->fail(FD_EINVAL, "fd_residual: R is NULL");
+    if (n_elems != 5 * (size_t)h->n)
+        return h->fail(FD_EINVAL, "fd_residual: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h->n);
+    // Between steps the saved register Qs is dead (stage 0 rewrites it), so it
+    // serves as the device buffer for R.
+    double* out = dst_is_device ? R : h->Qs;
+    cudaError_t e = run_stage(h, 0, true, out);
+    if (e == cudaSuccess && !dst_is_device)
+        e = cudaMemcpyAsync(R, h->Qs, n_elems * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "fd_residual");
+    return FD_OK;
+}
+
+int fd_check_finite(fd_handle* h) {
+    if (!h) return fail_global(FD_EINVAL, "fd_check_finite: NULL handle");
+    int flag = 0;
+    cudaError_t e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = fd::launch_check_finite(h->Q[h->cur], 5LL * h->n, h->flag, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "fd_check_finite");
+    if (flag) return h->fail(FD_EUNSTABLE, "state holds NaN or infinity");
+    return FD_OK;
+}
+
+size_t fd_device_bytes(const fd_handle* h) { return h ? h->block_bytes : 0; }
+
+int fd_profile(fd_handle* h, int enable) {
+    if (!h) return fail_global(FD_EINVAL, "fd_profile: NULL handle");
+    Profiler& P = h->prof;
+    if (enable && P.ev.empty()) {
+        P.ev.resize(2 * Profiler::kCap);
+        P.cls.resize(Profiler::kCap);
+        for (auto& e : P.ev) {
+            cudaError_t rc = cudaEventCreate(&e);
+            if (rc != cudaSuccess) {
+                e = nullptr;
+                return h->cuda_fail(rc, "fd_profile: cudaEventCreate");
+            }
+        }
+    }
+    cudaError_t e = prof_fold(h);
+    if (e != cudaSuccess) return h->cuda_fail(e, "fd_profile");
+    for (int c = 0; c < FD_KERNEL_CLASSES; ++c) {
+        P.total_ms[c] = 0.0;
+        P.count[c] = 0;
+    }
+    P.on = enable != 0;
+    return FD_OK;
+}
+
+int fd_profile_read(fd_handle* h, int kernel_class, double* total_ms, long long* launches) {
+    if (!h) return fail_global(FD_EINVAL, "fd_profile_read: NULL handle");
+    if (kernel_class < 0 || kernel_class >= FD_KERNEL_CLASSES)
+        return h->fail(FD_EINVAL, "fd_profile_read: kernel class %d out of range", kernel_class);
+    cudaError_t e = prof_fold(h);
+    if (e != cudaSuccess) return h->cuda_fail(e, "fd_profile_read");
+    if (total_ms) *total_ms = h->prof.total_ms[kernel_class];
+    if (launches) *launches = h->prof.count[kernel_class];
+    return FD_OK;
+}
+
+int fd_destroy(fd_handle* h) {
+    if (!h) return FD_OK;
+    cudaStreamSynchronize(h->stream);
+    for (auto e : h->prof.ev)
+        if (e) cudaEventDestroy(e);
+    device_free(h);
+    delete h;
+    return FD_OK;
+}
+
+const char* fd_last_error(const fd_handle* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,51 @@
+// fd_internal.h -- launchers shared between the kernel translation units and
+// the C-ABI implementation (not part of the public interface).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fd_core.cuh"
+
+namespace fd {
+
+// Fixed launch shape of the reductions: the partial-sum order, and hence the
+// rounding of the diagnostics, depends only on the grid size.
+constexpr int kDiagBlocks = 608;   // 4 per SM on a 152-SM GB300
+constexpr int kDiagThreads = 256;
+
+cudaError_t launch_tgv_ic(const Grid& g, const Phys& ph, double hx, double hy, double hz, double* Q,
+                          cudaStream_t st);
+// Primitive variables: binary64 W = (u, v, w, p, T), or the ten binary32
+// perturbation fields F = (rho-1, rho u, rho v, rho w, rhoE-rhoE0, u, v, w, p-p0, T-1).
+cudaError_t launch_prims_f64(const Grid& g, const Phys& ph, const double* Q, double* W, cudaStream_t st);
+cudaError_t launch_prims_f32(const Grid& g, const Phys& ph, const double* Q, float* F, cudaStream_t st);
+
+// Kernels of one stage in precision T (double or float), one launch each.
+// Qf / Wf are the five conserved-like and five primitive-like working
+// fields, Q64 the binary64 state the stage starts from, out the next state
+// (or R when resid), Qs the saved register.
+//   RA: launch_ra
+//   SS: launch_ss_grad, launch_ss
+//   BL: launch_bl_prod, launch_bl_d1, launch_bl_d2, launch_bl_res
+template <class T>
+cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
+                      const double* Q64, double* out, double* Qs, cudaStream_t st);
+template <class T>
+cudaError_t launch_ss_grad(const Grid& g, const Coef<T>& k, const T* Wf, T* Gw, cudaStream_t st);
+template <class T>
+cudaError_t launch_ss(const Grid& g, const Coef<T>& k, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
+                      const T* Gw, const double* Q64, double* out, double* Qs, cudaStream_t st);
+template <class T>
+cudaError_t launch_bl_prod(const Grid& g, const T* Qf, const T* Wf, T* P, cudaStream_t st);
+template <class T>
+cudaError_t launch_bl_d1(const Grid& g, const T* Qf, const T* Wf, const T* P, T* D1, cudaStream_t st);
+template <class T>
+cudaError_t launch_bl_d2(const Grid& g, const T* Wf, const T* D1, T* D2, cudaStream_t st);
+template <class T>
+cudaError_t launch_bl_res(const Grid& g, const Phys& ph, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
+                          const T* D1, const T* D2, const double* Q64, double* out, double* Qs, cudaStream_t st);
+cudaError_t launch_diagnostics_f64(const Grid& g, const double* Q, double* Wv, double* partial, double* out,
+                                   cudaStream_t st);
+cudaError_t launch_check_finite(const double* x, long long m, int* flag, cudaStream_t st);
+
+}  // namespace fd

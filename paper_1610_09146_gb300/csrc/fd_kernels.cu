@@ -1,0 +1,677 @@
+// fd_kernels.cu -- kernels of one Runge-Kutta stage for the three algorithm
+// families of Section 2 (BL store-all, SS store-some, RA recompute-all), the
+// Taylor-Green initial condition and the kinetic-energy / enstrophy
+// reduction (Section 3).
+//
+// Layout: every field is a grid-sized array [z][y][x] (x fastest).  The
+// conserved state Q (rho, rho u, rho v, rho w, rho E) and the saved RK
+// register Qs are always binary64.  The stencils read ten "working" fields:
+//   Qf = five conserved-like fields, Wf = five primitive-like fields.
+//   binary64 mode (T = double): Qf = Q itself, Wf = (u, v, w, p, T).
+//   binary32 mode (T = float) : Qf = (rho-1, rho u, rho v, rho w, rho E - rhoE0),
+//                               Wf = (u, v, w, p - p0, T - 1),
+// the shifted (perturbation) fields avoid the loss of digits that the large
+// mean pressure and energy (p0 = 1/(gamma M^2)) would cause in binary32
+// differences.  One thread evaluates one grid point; periodic boundaries
+// (Section 3) are the wrapped neighbour offsets of fd::Nbr.
+//
+// On GB300 binary64 issues at 1/64 of the binary32 rate, so the binary64
+// kernels are bound by FP64 instructions per point, not by memory traffic;
+// stencil taps are read through the read-only data cache.
+#include "fd_core.cuh"
+#include "fd_internal.h"
+
+namespace fd {
+
+namespace {
+
+template <class T>
+__device__ __forceinline__ T ld(const T* __restrict__ p, int i) {
+    return __ldg(p + i);
+}
+
+__device__ __forceinline__ int grid_index() { return blockIdx.x * blockDim.x + threadIdx.x; }
+
+template <class T>
+__device__ __forceinline__ T s1(const Grid& g, int a);
+template <>
+__device__ __forceinline__ double s1<double>(const Grid& g, int a) {
+    return g.inv12h[a];
+}
+template <>
+__device__ __forceinline__ float s1<float>(const Grid& g, int a) {
+    return g.inv12hf[a];
+}
+template <class T>
+__device__ __forceinline__ T s2(const Grid& g, int a);
+template <>
+__device__ __forceinline__ double s2<double>(const Grid& g, int a) {
+    return g.inv12h2[a];
+}
+template <>
+__device__ __forceinline__ float s2<float>(const Grid& g, int a) {
+    return g.inv12h2f[a];
+}
+
+// Constants that restore the mean-field terms removed by the shift (see
+// fd::assemble): zero in binary64 mode.
+template <class T>
+struct Shift {
+    T c_rho, c_E;
+};
+template <class T>
+__device__ __forceinline__ Shift<T> shift_of(const Phys& ph);
+template <>
+__device__ __forceinline__ Shift<double> shift_of<double>(const Phys&) {
+    return {0.0, 0.0};
+}
+template <>
+__device__ __forceinline__ Shift<float> shift_of<float>(const Phys& ph) {
+    return {1.0f, (float)(ph.rhoE0 + ph.p0)};
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- Section 3
+// Taylor-Green vortex (DeBonis 2013, cited in Section 3).
+__global__ void k_tgv_ic(Grid g, Phys ph, double hx, double hy, double hz, double* __restrict__ Q) {
+    int idx = grid_index();
+    if (idx >= g.n) return;
+    int i = idx % g.nx, t = idx / g.nx, j = t % g.ny, k = t / g.ny;
+    double sx, cx, sy, cy, sz, cz, s2x, c2x, s2y, c2y, s2z, c2z;
+    sincos(i * hx, &sx, &cx);
+    sincos(j * hy, &sy, &cy);
+    sincos(k * hz, &sz, &cz);
+    sincos(2.0 * (i * hx), &s2x, &c2x);
+    sincos(2.0 * (j * hy), &s2y, &c2y);
+    sincos(2.0 * (k * hz), &s2z, &c2z);
+    double u = sx * cy * cz;
+    double v = -cx * sy * cz;
+    double p = ph.p0 + (c2x + c2y) * (c2z + 2.0) * (1.0 / 16.0);
+    double rho = ph.gM2 * p;
+    int n = g.n;
+    Q[idx] = rho;
+    Q[n + idx] = rho * u;
+    Q[2 * n + idx] = rho * v;
+    Q[3 * n + idx] = 0.0;
+    Q[4 * n + idx] = p / ph.gm1 + 0.5 * rho * (u * u + v * v);
+}
+
+// ------------------------------------------------------- Section 2, Eqs. 6-7
+// binary64: u_i = rho u_i / rho, p = (gamma-1)(rho E - rho u_i u_i / 2),
+// T = gamma M^2 p / rho, written to W = (u, v, w, p, T).
+__global__ void __launch_bounds__(256) k_prims_f64(Grid g, Phys ph, const double* __restrict__ Q,
+                                                   double* __restrict__ W) {
+    int idx = grid_index();
+    if (idx >= g.n) return;
+    int n = g.n;
+    double rho = Q[idx];
+    double inv = 1.0 / rho;
+    double m0 = Q[n + idx], m1 = Q[2 * n + idx], m2 = Q[3 * n + idx];
+    double u = m0 * inv, v = m1 * inv, w = m2 * inv;
+    double p = ph.gm1 * fmx(-0.5, fmx(m0, u, fmx(m1, v, m2 * w)), Q[4 * n + idx]);
+    W[idx] = u;
+    W[n + idx] = v;
+    W[2 * n + idx] = w;
+    W[3 * n + idx] = p;
+    W[4 * n + idx] = ph.gM2 * p * inv;
+}
+
+// binary32 perturbation fields from the binary64 state.  With
+// p0 = (gamma-1) rhoE0 and gamma M^2 p0 = 1, Eqs. 6-7 become
+//   p - p0 = (gamma-1)(E' - rho u_i u_i / 2),  T - 1 = (gamma M^2 (p-p0) - rho') / rho.
+// Only the two shifts rho-1 and rhoE-rhoE0 are taken in binary64.
+__global__ void __launch_bounds__(256) k_prims_f32(Grid g, Phys ph, const double* __restrict__ Q,
+                                                   float* __restrict__ F) {
+    int idx = grid_index();
+    if (idx >= g.n) return;
+    int n = g.n;
+    double rho = Q[idx];
+    float rp = (float)(rho - 1.0);
+    float Ep = (float)(Q[4 * n + idx] - ph.rhoE0);
+    float m0 = (float)Q[n + idx], m1 = (float)Q[2 * n + idx], m2 = (float)Q[3 * n + idx];
+    float inv = 1.0f / (float)rho;
+    float u = m0 * inv, v = m1 * inv, w = m2 * inv;
+    float pp = (float)ph.gm1 * fmx(-0.5f, fmx(m0, u, fmx(m1, v, m2 * w)), Ep);
+    float Tp = fmx((float)ph.gM2, pp, -rp) * inv;
+    F[idx] = rp;
+    F[n + idx] = m0;
+    F[2 * n + idx] = m1;
+    F[3 * n + idx] = m2;
+    F[4 * n + idx] = Ep;
+    F[5 * n + idx] = u;
+    F[6 * n + idx] = v;
+    F[7 * n + idx] = w;
+    F[8 * n + idx] = pp;
+    F[9 * n + idx] = Tp;
+}
+
+// Final write of a stage: the residual itself (fd_residual), or the
+// two-register RK update (Fig. 1, advance-solution-in-time) in binary64:
+//   Q_out = Qs + a dt R,  Qs <- Qs + b dt R,  with Qs = Q_in at stage 0 (save-state).
+template <class T, bool RESID>
+__device__ __forceinline__ void stage_write(const RKStage& rk, int n, int c, const double* __restrict__ Q64,
+                                            const T R[5], double* __restrict__ out, double* __restrict__ Qs) {
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+        double r = (double)R[f];
+        if (RESID) {
+            out[f * n + c] = r;
+        } else {
+            double qs = rk.stage == 0 ? Q64[f * n + c] : Qs[f * n + c];
+            out[f * n + c] = fmx(rk.adt, r, qs);
+            if (rk.stage < 2) Qs[f * n + c] = fmx(rk.bdt, r, qs);
+        }
+    }
+}
+
+// Load the four taps (-2, -1, +1, +2) of field f around c along one axis.
+template <class T>
+__device__ __forceinline__ void taps(const T* __restrict__ f, int c, const int* o, T t[4]) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) t[a] = ld(f, c + o[a]);
+}
+
+// Residual at one point for the fused families, evaluated into registers
+// (the "thread-local variables" of Section 2, paragraphs SN / SS):
+//   R_f = -1/2 sum_j [ D_j(Q_f u_j) + u_j D_j Q_f ] - 1/2 Q_f div u         (Eq. skewscalar)
+//   R_rho u_i += -D_i p + v_i,   v_i = nu [ sum_j D2_j u_i + 1/3 sum_k D_ik u_k ]   (Eqs. 2, 4)
+//   R_rho E   += -sum_j D_j(p u_j) + kappa sum_j D2_j T + sum_i u_i v_i
+//                + nu [ 2 sum_i G_ii^2 + sum_{i<j} (G_ij + G_ji)^2 - 2/3 div^2 ]  (Eqs. 3-5)
+// with G_ij = D_j u_i.  The convective pair of each direction is one
+// difference of the product Q_f (u_j + u_j(centre)) formed at the taps, equal
+// to D_j(Q_f u_j) + u_j D_j Q_f by linearity of the stencil.  STORED_G: SS
+// reads G from the nine gradient arrays and differences G_jj + G_kk for the
+// mixed derivatives; otherwise (RA) G and D_i(D_k u_k) come from u taps.
+template <class T, bool STORED_G>
+__device__ __forceinline__ void fused_residual(const Nbr& s, int n, const T* __restrict__ Qf,
+                                               const T* __restrict__ Wf, const T* __restrict__ Gw,
+                                               const Coef<T>& k, T R[5]) {
+    const int c = s.c;
+    const T* __restrict__ pf = Wf + 3 * n;
+    const T* __restrict__ Tf = Wf + 4 * n;
+    T uc[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) uc[i] = ld(Wf + i * n, c);
+
+    T G[3][3];
+    if (STORED_G) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) G[i][j] = ld(Gw + (3 * i + j) * n, c);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                T t[4];
+                taps(Wf + i * n, c, s.o[j], t);
+                G[i][j] = k.s1[j] * delta1_taps(t);
+            }
+    }
+    const T div = G[0][0] + G[1][1] + G[2][2];
+    const T hd = T(-0.5) * div;
+#pragma unroll
+    for (int f = 0; f < 5; ++f) R[f] = ld(Qf + f * n, c) * hd;
+
+    // convective sums, pressure gradient and pressure work, direction by direction
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        T ut[4], st[4], pt[4];
+        taps(Wf + j * n, c, s.o[j], ut);
+        taps(pf, c, s.o[j], pt);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) st[a] = ut[a] + uc[j];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+            T qt[4];
+            taps(Qf + f * n, c, s.o[j], qt);
+            R[f] = fmx(k.c1[j], delta1_prod(qt, st), R[f]);
+        }
+        R[1 + j] = fmx(k.cp[j], delta1_taps(pt), R[1 + j]);
+        R[4] = fmx(k.cp[j], delta1_prod(pt, ut), R[4]);
+    }
+
+    // heat flux
+    {
+        const T T0 = ld(Tf, c);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T t[4];
+            taps(Tf, c, s.o[j], t);
+            R[4] = fmx(k.ks2[j], delta2_taps(t, T0), R[4]);
+        }
+    }
+
+    // viscous stress divergence and its work
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        T vi = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T t[4];
+            taps(Wf + i * n, c, s.o[j], t);
+            vi = fmx(k.vs2[i][j], delta2_taps(t, uc[i]), vi);
+        }
+        const int j1 = i == 0 ? 1 : 0, j2 = i == 2 ? 1 : 2;  // the two axes other than i
+        if (STORED_G) {
+            const T* __restrict__ ga = Gw + (3 * j1 + j1) * n;
+            const T* __restrict__ gb = Gw + (3 * j2 + j2) * n;
+            T t[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) t[a] = ld(ga, c + s.o[i][a]) + ld(gb, c + s.o[i][a]);
+            vi = fmx(k.vmix1[i], delta1_taps(t), vi);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int kk = q == 0 ? j1 : j2;
+                const T* __restrict__ uk = Wf + kk * n;
+                T t[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    T u4[4];
+                    taps(uk, c + s.o[i][a], s.o[kk], u4);
+                    t[a] = delta1_taps(u4);
+                }
+                vi = fmx(k.vmix[i][kk], delta1_taps(t), vi);
+            }
+        }
+        R[1 + i] += vi;
+        R[4] = fmx(uc[i], vi, R[4]);
+    }
+
+    // viscous dissipation tau_ij D_j u_i
+    {
+        T d = G[0][0] * G[0][0];
+        d = fmx(G[1][1], G[1][1], d);
+        d = fmx(G[2][2], G[2][2], d);
+        T s01 = G[0][1] + G[1][0], s02 = G[0][2] + G[2][0], s12 = G[1][2] + G[2][1];
+        T o = s01 * s01;
+        o = fmx(s02, s02, o);
+        o = fmx(s12, s12, o);
+        T diss = fmx(T(2), d, o);
+        diss = fmx(T(-2.0 / 3.0) * div, div, diss);
+        R[4] = fmx(k.nu, diss, R[4]);
+    }
+    if (k.c_rho != T(0)) {
+        R[0] = fmx(k.c_rho, div, R[0]);
+        R[4] = fmx(k.c_E, div, R[4]);
+    }
+}
+
+// ------------------------------------------------------------------ RA
+// Recompute-all (Section 2, paragraph RA): every derivative, including the
+// products inside a derivative and the 4x4-tap mixed derivatives, is
+// evaluated from its finite-difference formula at the point of use.
+template <class T, bool RESID>
+__global__ void __launch_bounds__(128) k_ra(Grid g, Coef<T> k, RKStage rk, const T* __restrict__ Qf,
+                                            const T* __restrict__ Wf, const double* __restrict__ Q64,
+                                            double* __restrict__ out, double* __restrict__ Qs) {
+    int idx = grid_index();
+    if (idx >= g.n) return;
+    const Nbr s = make_nbr(g, idx);
+    T R[5];
+    fused_residual<T, false>(s, g.n, Qf, Wf, nullptr, k, R);
+    stage_write<T, RESID>(rk, g.n, s.c, Q64, R, out, Qs);
+}
+
+// ------------------------------------------------------------------ SS
+// Store-some (Section 2, paragraph SS): the nine velocity gradients
+// du_i/dx_j go to global work arrays; every other derivative is evaluated
+// into thread-local registers in the fused kernel.  The mixed derivatives
+// D_i(D_k u_k) difference the stored gradients.
+template <class T>
+__global__ void __launch_bounds__(256) k_ss_grad(Grid g, Coef<T> k, const T* __restrict__ Wf, T* __restrict__ Gw) {
+    int idx = grid_index();
+    if (idx >= g.n) return;
+    const int n = g.n;
+    const Nbr s = make_nbr(g, idx);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T t[4];
+            taps(Wf + i * n, s.c, s.o[j], t);
+            Gw[(3 * i + j) * n + s.c] = k.s1[j] * delta1_taps(t);
+        }
+}
+
+template <class T, bool RESID>
+__global__ void __launch_bounds__(128) k_ss(Grid g, Coef<T> k, RKStage rk, const T* __restrict__ Qf,
+                                            const T* __restrict__ Wf, const T* __restrict__ Gw,
+                                            const double* __restrict__ Q64, double* __restrict__ out,
+                                            double* __restrict__ Qs) {
+    int idx = grid_index();
+    if (idx >= g.n) return;
+    const Nbr s = make_nbr(g, idx);
+    T R[5];
+    fused_residual<T, true>(s, g.n, Qf, Wf, Gw, k, R);
+    stage_write<T, RESID>(rk, g.n, s.c, Q64, R, out, Qs);
+}
+
+// ------------------------------------------------------------------ BL
+// Store-all (Section 2, paragraph BL): every product inside a derivative is
+// first written to a product work array, every derivative to its own
+// derivative work array; the residual is then a pointwise loop.
+// Work-array indices (each a grid-sized array):
+//   P : Qf_f u_j at 3f+j (f = 0..4, j = 0..2), p u_j at 15+j
+//   D1: D_j Qf_f at 3f+j, D_j u_i at 15+3i+j, D_i p at 24+i,
+//       D_j(Qf_f u_j) at 27+3f+j, D_j(p u_j) at 42+j
+//   D2: D2_j u_i at 3i+j, D2_j T at 9+j, D_i(D_k u_k) (k != i) at 12+2i+(k>i ? k-1 : k)
+template <class T>
+__global__ void __launch_bounds__(256) k_bl_prod(Grid g, const T* __restrict__ Qf, const T* __restrict__ Wf,
+                                                 T* __restrict__ P) {
+    int idx = grid_index();
+    if (idx >= g.n) return;
+    const int n = g.n;
+    T u[3] = {Wf[idx], Wf[n + idx], Wf[2 * n + idx]};
+    T p = Wf[3 * n + idx];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+        T qf = Qf[f * n + idx];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) P[(3 * f + j) * n + idx] = qf * u[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) P[(15 + j) * n + idx] = p * u[j];
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_bl_d1(Grid g, const T* __restrict__ Qf, const T* __restrict__ Wf,
+                                               const T* __restrict__ P, T* __restrict__ D1) {
+    int idx = grid_index();
+    if (idx >= g.n) return;
+    const int n = g.n;
+    const Nbr s = make_nbr(g, idx);
+    const int c = s.c;
+#pragma unroll
+    for (int f = 0; f < 5; ++f)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            D1[(3 * f + j) * n + c] = s1<T>(g, j) * delta1<T>([&](int k) { return ld(Qf + f * n, k); }, c, s.o[j]);
+            D1[(27 + 3 * f + j) * n + c] =
+                s1<T>(g, j) * delta1<T>([&](int k) { return ld(P + (3 * f + j) * n, k); }, c, s.o[j]);
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            D1[(15 + 3 * i + j) * n + c] = s1<T>(g, j) * delta1<T>([&](int k) { return ld(Wf + i * n, k); }, c, s.o[j]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        D1[(24 + j) * n + c] = s1<T>(g, j) * delta1<T>([&](int k) { return ld(Wf + 3 * n, k); }, c, s.o[j]);
+        D1[(42 + j) * n + c] = s1<T>(g, j) * delta1<T>([&](int k) { return ld(P + (15 + j) * n, k); }, c, s.o[j]);
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_bl_d2(Grid g, const T* __restrict__ Wf, const T* __restrict__ D1,
+                                               T* __restrict__ D2) {
+    int idx = grid_index();
+    if (idx >= g.n) return;
+    const int n = g.n;
+    const Nbr s = make_nbr(g, idx);
+    const int c = s.c;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        T u0 = ld(Wf + i * n, c);
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            D2[(3 * i + j) * n + c] = s2<T>(g, j) * delta2<T>([&](int k) { return ld(Wf + i * n, k); }, c, s.o[j], u0);
+    }
+    T T0 = ld(Wf + 4 * n, c);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        D2[(9 + j) * n + c] = s2<T>(g, j) * delta2<T>([&](int k) { return ld(Wf + 4 * n, k); }, c, s.o[j], T0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (k == i) continue;
+            const T* __restrict__ gkk = D1 + (15 + 3 * k + k) * n;
+            D2[(12 + 2 * i + (k > i ? k - 1 : k)) * n + c] =
+                s1<T>(g, i) * delta1<T>([&](int r) { return ld(gkk, r); }, c, s.o[i]);
+        }
+}
+
+template <class T, bool RESID>
+__global__ void __launch_bounds__(256) k_bl_res(Grid g, Phys ph, RKStage rk, const T* __restrict__ Qf,
+                                                const T* __restrict__ Wf, const T* __restrict__ D1,
+                                                const T* __restrict__ D2, const double* __restrict__ Q64,
+                                                double* __restrict__ out, double* __restrict__ Qs) {
+    int idx = grid_index();
+    if (idx >= g.n) return;
+    const int n = g.n;
+    const int c = idx;
+    Terms<T> t;
+    T uc[3], q[5];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) uc[i] = Wf[i * n + c];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) q[f] = Qf[f * n + c];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) t.G[i][j] = D1[(15 + 3 * i + j) * n + c];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+        T acc = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) acc += fmx(uc[j], D1[(3 * f + j) * n + c], D1[(27 + 3 * f + j) * n + c]);
+        t.conv[f] = acc;
+    }
+    T dpu = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        t.dp[j] = D1[(24 + j) * n + c];
+        dpu += D1[(42 + j) * n + c];
+    }
+    t.dpu = dpu;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        t.lap[i] = D2[(3 * i) * n + c] + D2[(3 * i + 1) * n + c] + D2[(3 * i + 2) * n + c];
+        T gd = D2[(3 * i + i) * n + c];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (k == i) continue;
+            gd += D2[(12 + 2 * i + (k > i ? k - 1 : k)) * n + c];
+        }
+        t.gd[i] = gd;
+    }
+    t.lapT = D2[9 * n + c] + D2[10 * n + c] + D2[11 * n + c];
+    const Shift<T> sh = shift_of<T>(ph);
+    T R[5];
+    assemble<T>(t, q, uc, (T)ph.nu, (T)ph.kappa, sh.c_rho, sh.c_E, R);
+    stage_write<T, RESID>(rk, n, c, Q64, R, out, Qs);
+}
+
+// ---------------------------------------------------------------- Section 3
+// Kinetic energy and enstrophy, always in binary64.  Pass 1 writes
+// u = rho u / rho into Wv; pass 2 forms rho|u|^2/2 and rho|omega|^2/2 per
+// point, sums them over a fixed grid-stride assignment and a fixed shuffle
+// tree into one partial per block; pass 3 sums the partials in index order.
+// The rounding therefore depends only on the grid size, never on scheduling.
+__global__ void __launch_bounds__(256) k_velocity_f64(Grid g, const double* __restrict__ Q, double* __restrict__ Wv) {
+    int idx = grid_index();
+    if (idx >= g.n) return;
+    const int n = g.n;
+    double inv = 1.0 / Q[idx];
+    Wv[idx] = Q[n + idx] * inv;
+    Wv[n + idx] = Q[2 * n + idx] * inv;
+    Wv[2 * n + idx] = Q[3 * n + idx] * inv;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__global__ void __launch_bounds__(kDiagThreads) k_diag_partial_f64(Grid g, const double* __restrict__ Q,
+                                                                    const double* __restrict__ Wv,
+                                                                    double* __restrict__ partial) {
+    const int n = g.n;
+    double ke = 0.0, en = 0.0;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const Nbr s = make_nbr(g, idx);
+        const int c = s.c;
+        double G[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                G[i][j] = g.inv12h[j] * delta1<double>([&](int k) { return ld(Wv + i * n, k); }, c, s.o[j]);
+        double rho = Q[c];
+        double u = Wv[c], v = Wv[n + c], w = Wv[2 * n + c];
+        double ox = G[2][1] - G[1][2];
+        double oy = G[0][2] - G[2][0];
+        double oz = G[1][0] - G[0][1];
+        ke = fmx(0.5 * rho, fmx(u, u, fmx(v, v, w * w)), ke);
+        en = fmx(0.5 * rho, fmx(ox, ox, fmx(oy, oy, oz * oz)), en);
+    }
+    __shared__ double sk[kDiagThreads / 32], se[kDiagThreads / 32];
+    ke = warp_sum(ke);
+    en = warp_sum(en);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sk[wid] = ke;
+        se[wid] = en;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < kDiagThreads / 32; ++i) {
+            a += sk[i];
+            b += se[i];
+        }
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void k_diag_final_f64(const double* __restrict__ partial, int nblocks, double inv_n,
+                                 double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < nblocks; ++i) {
+            a += partial[2 * i];
+            b += partial[2 * i + 1];
+        }
+        out[0] = a * inv_n;
+        out[1] = b * inv_n;
+    }
+}
+
+// Non-finite scan of m values; sets *flag to 1 if any is NaN or infinite.
+__global__ void k_check_finite(const double* __restrict__ x, long long m, int* __restrict__ flag) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(x[i])) {
+            *flag = 1;
+            return;
+        }
+}
+
+// ---------------------------------------------------------------- launchers
+
+static inline int blocks_for(int n, int threads) { return (n + threads - 1) / threads; }
+
+cudaError_t launch_tgv_ic(const Grid& g, const Phys& ph, double hx, double hy, double hz, double* Q,
+                          cudaStream_t st) {
+    k_tgv_ic<<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, hx, hy, hz, Q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prims_f64(const Grid& g, const Phys& ph, const double* Q, double* W, cudaStream_t st) {
+    k_prims_f64<<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, Q, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prims_f32(const Grid& g, const Phys& ph, const double* Q, float* F, cudaStream_t st) {
+    k_prims_f32<<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, Q, F);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
+                      const double* Q64, double* out, double* Qs, cudaStream_t st) {
+    if (resid)
+        k_ra<T, true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, rk, Qf, Wf, Q64, out, Qs);
+    else
+        k_ra<T, false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, rk, Qf, Wf, Q64, out, Qs);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_ss_grad(const Grid& g, const Coef<T>& k, const T* Wf, T* Gw, cudaStream_t st) {
+    k_ss_grad<T><<<blocks_for(g.n, 256), 256, 0, st>>>(g, k, Wf, Gw);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_ss(const Grid& g, const Coef<T>& k, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
+                      const T* Gw, const double* Q64, double* out, double* Qs, cudaStream_t st) {
+    if (resid)
+        k_ss<T, true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, rk, Qf, Wf, Gw, Q64, out, Qs);
+    else
+        k_ss<T, false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, rk, Qf, Wf, Gw, Q64, out, Qs);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_bl_prod(const Grid& g, const T* Qf, const T* Wf, T* P, cudaStream_t st) {
+    k_bl_prod<T><<<blocks_for(g.n, 256), 256, 0, st>>>(g, Qf, Wf, P);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_bl_d1(const Grid& g, const T* Qf, const T* Wf, const T* P, T* D1, cudaStream_t st) {
+    k_bl_d1<T><<<blocks_for(g.n, 256), 256, 0, st>>>(g, Qf, Wf, P, D1);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_bl_d2(const Grid& g, const T* Wf, const T* D1, T* D2, cudaStream_t st) {
+    k_bl_d2<T><<<blocks_for(g.n, 256), 256, 0, st>>>(g, Wf, D1, D2);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_bl_res(const Grid& g, const Phys& ph, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
+                          const T* D1, const T* D2, const double* Q64, double* out, double* Qs, cudaStream_t st) {
+    if (resid)
+        k_bl_res<T, true><<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, rk, Qf, Wf, D1, D2, Q64, out, Qs);
+    else
+        k_bl_res<T, false><<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, rk, Qf, Wf, D1, D2, Q64, out, Qs);
+    return cudaGetLastError();
+}
+
+#define FD_INSTANTIATE(T)                                                                                        \
+    template cudaError_t launch_ra<T>(const Grid&, const Coef<T>&, const RKStage&, bool, const T*, const T*,     \
+                                      const double*, double*, double*, cudaStream_t);                           \
+    template cudaError_t launch_ss_grad<T>(const Grid&, const Coef<T>&, const T*, T*, cudaStream_t);            \
+    template cudaError_t launch_ss<T>(const Grid&, const Coef<T>&, const RKStage&, bool, const T*, const T*,     \
+                                      const T*, const double*, double*, double*, cudaStream_t);                 \
+    template cudaError_t launch_bl_prod<T>(const Grid&, const T*, const T*, T*, cudaStream_t);                  \
+    template cudaError_t launch_bl_d1<T>(const Grid&, const T*, const T*, const T*, T*, cudaStream_t);          \
+    template cudaError_t launch_bl_d2<T>(const Grid&, const T*, const T*, T*, cudaStream_t);                    \
+    template cudaError_t launch_bl_res<T>(const Grid&, const Phys&, const RKStage&, bool, const T*, const T*,    \
+                                          const T*, const T*, const double*, double*, double*, cudaStream_t);
+FD_INSTANTIATE(double)
+FD_INSTANTIATE(float)
+#undef FD_INSTANTIATE
+
+cudaError_t launch_diagnostics_f64(const Grid& g, const double* Q, double* Wv, double* partial, double* out,
+                                   cudaStream_t st) {
+    k_velocity_f64<<<blocks_for(g.n, 256), 256, 0, st>>>(g, Q, Wv);
+    k_diag_partial_f64<<<kDiagBlocks, kDiagThreads, 0, st>>>(g, Q, Wv, partial);
+    k_diag_final_f64<<<1, 32, 0, st>>>(partial, kDiagBlocks, 1.0 / (double)g.n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const double* x, long long m, int* flag, cudaStream_t st) {
+    k_check_finite<<<kDiagBlocks, 256, 0, st>>>(x, m, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace fd

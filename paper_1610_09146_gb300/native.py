@@ -1,0 +1,186 @@
+"""ctypes binding of the C ABI in ``include/fdgb300.h`` (argument marshalling only).
+
+Every function keeps the C name and argument order; pointers are passed as
+integers (device addresses, e.g. ``tensor.data_ptr()``) or numpy arrays (host).
+Loading fails loudly when ``libfdgb300.so`` has not been built: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+FD_OK = 0
+FD_EINVAL = -1
+FD_ENOMEM = -2
+FD_ECUDA = -3
+FD_EUNSTABLE = -4
+FD_EBUSY = -5
+
+FD_STORE_ALL = 0
+FD_STORE_SOME = 1
+FD_RECOMPUTE_ALL = 2
+
+FD_F64 = 0
+FD_F32_ACC64 = 1
+
+FD_KERNEL_PRIMS = 0
+FD_KERNEL_GRAD = 1
+FD_KERNEL_FUSED = 2
+FD_KERNEL_PRODUCTS = 3
+FD_KERNEL_DERIV1 = 4
+FD_KERNEL_DERIV2 = 5
+FD_KERNEL_CLASSES = 6
+KERNEL_CLASS_NAMES = ["prims", "grad", "fused", "products", "deriv1", "deriv2"]
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class FdAlloc(ctypes.Structure):
+    """``fd_alloc``: device allocator callbacks."""
+
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class FdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "fd_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                 ctypes.c_int, ctypes.POINTER(FdAlloc), _vp]),
+    "fd_step": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "fd_get_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int]),
+    "fd_set_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int]),
+    "fd_diagnostics": (ctypes.c_int, [_vp, _dp, _dp]),
+    "fd_residual": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int]),
+    "fd_check_finite": (ctypes.c_int, [_vp]),
+    "fd_device_bytes": (ctypes.c_size_t, [_vp]),
+    "fd_profile": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "fd_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "fd_destroy": (ctypes.c_int, [_vp]),
+    "fd_last_error": (ctypes.c_char_p, [_vp]),
+}
+
+
+def exported_symbols():
+    """Names of the entry points this binding expects the library to export."""
+    return list(_SIGS)
+
+
+def lib_path() -> str:
+    return LIB
+
+
+def load():
+    """Load the native library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with paper_1610_09146_gb300.build.build() "
+                               "(the CUDA path has no fallback)")
+        L = ctypes.CDLL(LIB)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, h=None):
+    if rc != FD_OK:
+        msg = load().fd_last_error(h).decode()
+        raise FdError(rc, msg)
+    return rc
+
+
+def _hostptr(a: np.ndarray):
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise TypeError("host buffers must be C-contiguous float64 numpy arrays")
+    return a.ctypes.data
+
+
+# ---- thin wrappers with the C names ------------------------------------------
+
+
+def fd_create(nx, ny, nz, Re, Mach, Pr, gamma, dt, algorithm, dtype, alloc=None, stream=0):
+    """Returns the handle (an opaque integer).  `alloc` is an FdAlloc or None,
+    `stream` a cudaStream_t as an integer (0 = default stream)."""
+    h = _vp()
+    ap = ctypes.byref(alloc) if alloc is not None else None
+    rc = load().fd_create(ctypes.byref(h), nx, ny, nz, Re, Mach, Pr, gamma, dt, algorithm, dtype, ap,
+                          _vp(stream or None))
+    _check(rc, None)
+    return h.value
+
+
+def fd_step(h, n):
+    return _check(load().fd_step(h, n), h)
+
+
+def fd_get_state(h, dst, n_elems=None, dst_is_device=None):
+    """dst: numpy float64 array (host) or an int device address (then give n_elems)."""
+    if isinstance(dst, np.ndarray):
+        return _check(load().fd_get_state(h, _hostptr(dst), dst.size, 0), h)
+    return _check(load().fd_get_state(h, dst, n_elems, 1 if dst_is_device is None else dst_is_device), h)
+
+
+def fd_set_state(h, src, n_elems=None, src_is_device=None):
+    if isinstance(src, np.ndarray):
+        return _check(load().fd_set_state(h, _hostptr(src), src.size, 0), h)
+    return _check(load().fd_set_state(h, src, n_elems, 1 if src_is_device is None else src_is_device), h)
+
+
+def fd_diagnostics(h):
+    ke = ctypes.c_double()
+    en = ctypes.c_double()
+    _check(load().fd_diagnostics(h, ctypes.byref(ke), ctypes.byref(en)), h)
+    return ke.value, en.value
+
+
+def fd_residual(h, dst, n_elems=None, dst_is_device=None):
+    if isinstance(dst, np.ndarray):
+        return _check(load().fd_residual(h, _hostptr(dst), dst.size, 0), h)
+    return _check(load().fd_residual(h, dst, n_elems, 1 if dst_is_device is None else dst_is_device), h)
+
+
+def fd_check_finite(h):
+    return load().fd_check_finite(h)
+
+
+def fd_device_bytes(h):
+    return load().fd_device_bytes(h)
+
+
+def fd_profile(h, enable):
+    return _check(load().fd_profile(h, 1 if enable else 0), h)
+
+
+def fd_profile_read(h, kernel_class):
+    """(total milliseconds, launches) of one kernel class since the last fd_profile."""
+    ms = ctypes.c_double()
+    cnt = ctypes.c_longlong()
+    _check(load().fd_profile_read(h, kernel_class, ctypes.byref(ms), ctypes.byref(cnt)), h)
+    return ms.value, cnt.value
+
+
+def fd_destroy(h):
+    return _check(load().fd_destroy(h), None)
+
+
+def fd_last_error(h=None):
+    return load().fd_last_error(h).decode()

@@ -1,0 +1,259 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle.
+
+Tolerances (binary64 path): relative L-inf <= 1e-12 per conserved variable,
+normalised by max|oracle| of that variable, after 10 steps; the residual
+itself to the same bound.  Variants agree with one another to the same bound
+(Section 3: all algorithms match BL "up to machine precision"; they round in
+different orders, e.g. a product formed at each tap vs a stored product, and
+the smallest variable, rho w, starts at zero).
+Inputs are the oracle's own Taylor-Green state or seeded random fields from
+tests/inputs.py; no oracle input or expected value comes from the GPU.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.inputs import rough_state, smooth_state
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1610_09146_gb300 as fd  # noqa: E402
+
+VARIANTS = ["store_all", "store_some", "recompute_all"]
+GAMMA, MACH, RE, PR = 1.4, 0.1, 1600.0, 0.71
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    fd.build()
+
+
+def rel_linf(a, b):
+    return max(np.abs(a[v] - b[v]).max() / max(np.abs(b[v]).max(), 1e-300) for v in range(5))
+
+
+def solver(shape, alg, dtype="f64", dt=1e-3, **kw):
+    nz, ny, nx = shape
+    return fd.Solver((nx, ny, nz), Re=kw.get("Re", RE), Mach=kw.get("Mach", MACH), Pr=PR, gamma=GAMMA, dt=dt,
+                     algorithm=alg, dtype=dtype)
+
+
+# ------------------------------------------------------------ initial condition
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (20, 24, 28), (5, 5, 5)])
+def test_initial_condition_matches_oracle(shape):
+    nz, ny, nx = shape
+    ref = O.tgv_ic(nx, ny, nz, GAMMA, MACH)
+    with solver(shape, "store_some") as s:
+        Q = s.state()
+    assert np.abs(Q - ref).max() < 1e-13
+
+
+# -------------------------------------------------------------------- residual
+
+
+@pytest.mark.parametrize("alg", VARIANTS)
+@pytest.mark.parametrize("shape,kind", [((23, 19, 21), "rough"), ((32, 32, 32), "smooth"), ((5, 6, 7), "rough")])
+def test_residual_matches_oracle(alg, shape, kind):
+    Q0 = rough_state(shape, seed=5) if kind == "rough" else smooth_state(shape, seed=6)
+    ref = O.residual(Q0, Re=RE, Mach=MACH, Pr=PR, gamma=GAMMA)
+    with solver(shape, alg) as s:
+        s.set_state(Q0)
+        R = s.residual()
+    assert rel_linf(R, ref) <= 1e-12
+
+
+# --------------------------------------------------------------- 10 RK3 steps
+
+
+@pytest.mark.parametrize("alg", VARIANTS)
+def test_ten_steps_tgv_32_matches_oracle(alg):
+    n = 32
+    ref = O.run(O.tgv_ic(n, n, n, GAMMA, MACH), 10, dt=1e-3)
+    with solver((n, n, n), alg) as s:
+        s.step(10)
+        Q = s.state()
+    assert rel_linf(Q, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("alg", VARIANTS)
+def test_ten_steps_random_ragged_grid_matches_oracle(alg):
+    shape = (18, 24, 20)  # nz, ny, nx: no axis a multiple of the block size
+    Q0 = smooth_state(shape, seed=21)
+    ref = O.run(Q0, 10, dt=1e-3)
+    with solver(shape, alg) as s:
+        s.set_state(Q0)
+        s.step(10)
+        Q = s.state()
+    assert rel_linf(Q, ref) <= 1e-12
+
+
+def test_variants_agree_to_machine_precision():
+    n = 32
+    out = {}
+    for alg in VARIANTS:
+        with solver((n, n, n), alg) as s:
+            s.step(10)
+            out[alg] = s.state()
+    assert rel_linf(out["store_some"], out["store_all"]) <= 1e-12
+    assert rel_linf(out["recompute_all"], out["store_all"]) <= 1e-12
+
+
+# ----------------------------------------------------------------- diagnostics
+
+
+@pytest.mark.parametrize("steps", [0, 10])
+def test_diagnostics_match_oracle(steps):
+    n = 32
+    Q = O.tgv_ic(n, n, n, GAMMA, MACH)
+    Q = O.run(Q, steps, dt=1e-3) if steps else Q
+    ke_ref, en_ref = O.diagnostics(Q)
+    with solver((n, n, n), "store_some") as s:
+        s.set_state(Q)
+        ke, en = s.diagnostics()
+        ke2, en2 = s.diagnostics()
+    assert abs(ke - ke_ref) <= 1e-13 * ke_ref
+    assert abs(en - en_ref) <= 1e-13 * en_ref
+    assert (ke, en) == (ke2, en2)  # fixed reduction order: bitwise repeatable
+
+
+def test_initial_kinetic_energy_closed_form_on_gpu():
+    with solver((64, 64, 64), "recompute_all") as s:
+        ke, en = s.diagnostics()
+    h = 2 * np.pi / 64
+    k1 = (8 * np.sin(h) - np.sin(2 * h)) / (6 * h)
+    assert abs(ke - 0.125) < 1e-14
+    assert abs(en - k1**2 * (3 / 8 - 5 * GAMMA * MACH**2 / 128)) < 1e-14
+
+
+# ------------------------------------------------- full size, sampled points
+
+
+def _block(Q, z, y, x, r):
+    nz, ny, nx = Q.shape[1:]
+    iz = (np.arange(z - r, z + r + 1)) % nz
+    iy = (np.arange(y - r, y + r + 1)) % ny
+    ix = (np.arange(x - r, x + r + 1)) % nx
+    return np.ascontiguousarray(Q[:, iz][:, :, iy][:, :, :, ix])
+
+
+def oracle_one_step_at(Q0, pts, dt, h):
+    """The oracle's one-step result at sample points, each computed on a periodic
+    17^3 block cut around the point with the parent grid spacing.  The scheme's
+    dependency radius is 2 points per stage (6 per step), so the centre of the
+    block is unaffected by the block's own wrap-around."""
+    r = 8
+    out = []
+    for (z, y, x) in pts:
+        B = _block(Q0, z, y, x, r)
+        B1 = O.run(B, 1, dt=dt, h=h)
+        out.append(B1[:, r, r, r])
+    return np.array(out)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("alg", VARIANTS)
+def test_full_size_256_one_step_sampled(alg):
+    n = 256
+    dt = fd.dt_for_grid(n)
+    Q0 = O.tgv_ic(n, n, n, GAMMA, MACH)
+    rng = np.random.default_rng(256)
+    pts = [tuple(rng.integers(0, n, 3)) for _ in range(24)] + [(0, 0, 0), (n - 1, n - 1, n - 1), (1, n - 2, 0)]
+    h = (2 * np.pi / n,) * 3
+    ref = oracle_one_step_at(Q0, pts, dt, h)
+    scale = np.abs(Q0).reshape(5, -1).max(axis=1)
+    scale[3] = np.abs(ref[:, 3]).max()
+    with solver((n, n, n), alg, dt=dt) as s:
+        Qi = s.state()
+        assert np.abs(Qi - Q0).max() < 1e-13  # initial condition, every point
+        s.step(1)
+        Q = s.state()
+        # conservation of mass and momentum at full size
+        for v in range(3):
+            assert abs(Q[v].sum() - Q0[v].sum()) <= 1e-12 * np.abs(Q0[v]).sum() + 1e-9
+    got = np.array([Q[:, z, y, x] for (z, y, x) in pts])
+    for v in range(5):
+        assert np.abs(got[:, v] - ref[:, v]).max() <= 1e-12 * scale[v], v
+
+
+# ------------------------------------------------------------------ edge cases
+
+
+@pytest.mark.parametrize("alg", VARIANTS)
+def test_smallest_grid_and_zero_steps(alg):
+    shape = (5, 5, 5)
+    Q0 = smooth_state(shape, seed=2)
+    ref = O.run(Q0, 3, dt=1e-3)
+    with solver(shape, alg) as s:
+        s.set_state(Q0)
+        s.step(0)
+        assert np.array_equal(s.state(), Q0)
+        s.step(3)
+        assert rel_linf(s.state(), ref) <= 1e-12
+
+
+def test_checkpoint_resume_is_bitwise():
+    n = 24
+    with solver((n, n, n), "store_some") as a:
+        a.step(6)
+        full = a.state()
+    with solver((n, n, n), "store_some") as b:
+        b.step(3)
+        mid = b.state()
+    with solver((n, n, n), "store_some") as c:
+        c.set_state(mid)
+        c.step(3)
+        resumed = c.state()
+    assert np.array_equal(full, resumed)
+
+
+def test_device_buffers_and_streams():
+    n = 16
+    st = torch.cuda.Stream()
+    ref = O.run(O.tgv_ic(n, n, n, GAMMA, MACH), 2, dt=1e-3)
+    with torch.cuda.stream(st):
+        with solver((n, n, n), "recompute_all") as s:
+            s.step(2)
+            out = torch.empty((5, n, n, n), dtype=torch.float64, device="cuda")
+            s.state(out)
+            R = torch.empty_like(out)
+            s.residual(R)
+    st.synchronize()
+    assert rel_linf(out.cpu().numpy(), ref) <= 1e-12
+    assert torch.isfinite(R).all()
+
+
+def test_cuda_malloc_path_matches_torch_allocator():
+    n = 16
+    a = fd.Solver(n, dt=1e-3, algorithm="store_all", use_torch_allocator=True)
+    b = fd.Solver(n, dt=1e-3, algorithm="store_all", use_torch_allocator=False)
+    a.step(2)
+    b.step(2)
+    assert np.array_equal(a.state(), b.state())
+    assert a.device_bytes() == b.device_bytes() > 0
+    a.close()
+    b.close()
+
+
+def test_non_finite_state_is_reported():
+    n = 8
+    with solver((n, n, n), "store_some") as s:
+        assert s.check_finite()
+        Q = s.state()
+        Q[4, 3, 2, 1] = np.nan
+        s.set_state(Q)
+        assert fd.fd_check_finite(s.h) == fd.FD_EUNSTABLE
+
+
+def test_bad_sizes_are_rejected():
+    n = 8
+    with solver((n, n, n), "store_some") as s:
+        with pytest.raises(fd.FdError) as e:
+            fd.fd_get_state(s.h, np.empty(10))
+        assert e.value.code == fd.FD_EINVAL
+        with pytest.raises(fd.FdError):
+            fd.fd_step(s.h, -1)
