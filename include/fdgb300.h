@@ -165,6 +165,40 @@ int fd_profile(fd_handle* h, int enable);
  * output may be NULL.  Errors: FD_EINVAL (class out of range), FD_ECUDA. */
 int fd_profile_read(fd_handle* h, int kernel_class, double* total_ms, long long* launches);
 
+/* ---- residual without any allocation -------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory when they need a residual, for example
+ * an external time integrator that owns its state and calls R(Q) while a
+ * stream capture is in progress, inside a real-time loop with a fixed memory
+ * budget, or in a process whose device memory is held by another framework's
+ * pool.  fd_residual needs a handle and fd_create allocates; this call needs
+ * neither and calls no allocating routine.
+ *
+ * Q (input) and R (output) are caller-owned device arrays of 5*nx*ny*nz
+ * doubles in the state layout above, on the current device, not overlapping.
+ * R receives the residual of Eqs. 1-5 (Section 2, Eq. skewscalar) evaluated
+ * with the store-some family in binary64; it equals what fd_residual returns
+ * for a FD_STORE_SOME / FD_F64 handle holding Q.  The work is enqueued on
+ * cuda_stream (NULL = default stream) and the call returns without waiting.
+ *
+ * Scratch: a fixed device array inside the library holds the primitives and
+ * the nine velocity gradients of at most FD_NOALLOC_MAX_POINTS grid points
+ * (29.4 MB, kept by every GPU that loads the library until the process
+ * exits).  All calls share it and it keeps the last call's contents, which
+ * no call reads before overwriting; two calls whose work overlaps on the GPU
+ * (different streams, or host threads racing on one device) race on it and
+ * must be ordered by the caller.  The first call on each device looks up the
+ * scratch address with cudaGetSymbolAddress; make that first call before any
+ * stream capture begins.
+ *
+ * Errors: FD_EINVAL for a NULL pointer, an axis below 5 points, more than
+ * FD_NOALLOC_MAX_POINTS points, or Re, Mach, Pr <= 0 or gamma <= 1 (nothing is
+ * launched); FD_ECUDA if the set-up lookup or a launch fails.  This function
+ * does not set fd_last_error's message. */
+#define FD_NOALLOC_MAX_POINTS 262144 /* 64^3 */
+int fd_residual_noalloc(const double* Q, double* R, int nx, int ny, int nz, double Re, double Mach,
+                        double Pr, double gamma, void* cuda_stream);
+
 /* Free every device buffer of the handle and the handle itself.  NULL is a
  * no-op.  Synchronises the handle's stream first. */
 int fd_destroy(fd_handle* h);

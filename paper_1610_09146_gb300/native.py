@@ -35,6 +35,8 @@ FD_KERNEL_PRODUCTS = 3
 FD_KERNEL_DERIV1 = 4
 FD_KERNEL_DERIV2 = 5
 FD_KERNEL_CLASSES = 6
+
+FD_NOALLOC_MAX_POINTS = 262144
 KERNEL_CLASS_NAMES = ["prims", "grad", "fused", "products", "deriv1", "deriv2"]
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -71,6 +73,8 @@ _SIGS = {
     "fd_device_bytes": (ctypes.c_size_t, [_vp]),
     "fd_profile": (ctypes.c_int, [_vp, ctypes.c_int]),
     "fd_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "fd_residual_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp]),
     "fd_destroy": (ctypes.c_int, [_vp]),
     "fd_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -176,6 +180,12 @@ def fd_profile_read(h, kernel_class):
     cnt = ctypes.c_longlong()
     _check(load().fd_profile_read(h, kernel_class, ctypes.byref(ms), ctypes.byref(cnt)), h)
     return ms.value, cnt.value
+
+
+def fd_residual_noalloc(Q, R, nx, ny, nz, Re, Mach, Pr, gamma, stream=0):
+    """Q, R: device addresses (ints) of caller-owned float64 arrays.  Returns the status
+    code as is (no message is set by this entry point)."""
+    return load().fd_residual_noalloc(Q, R, nx, ny, nz, Re, Mach, Pr, gamma, _vp(stream or None))
 
 
 def fd_destroy(h):
