@@ -53,20 +53,21 @@ HBM_FALLBACK_GBS = 6800.0
 # Algorithmic cost per grid point of one launch, by (dtype, family, kernel class):
 # (flops with FMA = 2, HBM bytes at ideal reuse, FP64 pipe instructions), each averaged
 # over the three stages.  Counted from the kernel source (see the kernel table of the
-# design notes); the SS fused count agrees with ncu's executed DADD/DMUL/DFMA (257/pt).
+# design notes); the fused kernels include the primitives of the next stage, which they
+# write with the update (so "prims" runs only after a state is set).
 COST = {
-    ("f64", "store_some", "fused"): (395.7, 245.3, 253.7),
+    ("f64", "store_some", "fused"): (409.7, 285.3, 273.7),
     ("f64", "store_some", "grad"): (45, 96, 36),
-    ("f64", "recompute_all", "fused"): (542.7, 173.3, 357.7),
-    ("f64", "store_all", "fused"): (163, 661.3, 120),
+    ("f64", "recompute_all", "fused"): (556.7, 213.3, 377.7),
+    ("f64", "store_all", "fused"): (177, 701.3, 140),
     ("f64", "store_all", "deriv1"): (225, 576, 180),
     ("f64", "store_all", "deriv2"): (114, 200, 84),
     ("f64", "store_all", "products"): (18, 216, 18),
     ("f64", "*", "prims"): (14, 80, 20),
-    ("f32", "store_some", "fused"): (399.7, 182.7, 0),
+    ("f32", "store_some", "fused"): (415.7, 222.7, 10.3),
     ("f32", "store_some", "grad"): (45, 48, 0),
-    ("f32", "recompute_all", "fused"): (546.7, 146.7, 0),
-    ("f32", "store_all", "fused"): (167, 390.7, 0),
+    ("f32", "recompute_all", "fused"): (562.7, 186.7, 10.3),
+    ("f32", "store_all", "fused"): (183, 430.7, 10.3),
     ("f32", "store_all", "deriv1"): (225, 288, 0),
     ("f32", "store_all", "deriv2"): (114, 100, 0),
     ("f32", "store_all", "products"): (18, 108, 0),
@@ -205,7 +206,7 @@ def roofline_of(dtype, alg, kern, n, hbm_peak, hbm_src):
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of a 256^3 launch, from one ncu
 # capture of the current kernel on a 160^3 grid (two launches, 249 B per point) scaled by
 # the point count; None where no capture of the current kernel version exists.
-TRAFFIC = {("f64", "store_some", "fused"): 4.18e9}
+TRAFFIC = {}
 
 
 def e2e_run(fd, torch, s, n, steps, stream):

@@ -55,7 +55,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not os.path.exists(nvcc):
         nvcc = shutil.which("nvcc") or "nvcc"
     os.makedirs(BUILD_DIR, exist_ok=True)
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
+    # -fmad=false: every multiply-add the kernels intend is written as an explicit fma, so the
+    # compiler may not contract others; the same per-point code then rounds identically in
+    # every kernel that inlines it (a batched instance matches the same instance run alone).
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
                      "-I", os.path.join(os.path.dirname(HERE), "include")]
     if verbose:
         common += ["-Xptxas", "-v"]

@@ -6,10 +6,14 @@
 //         a value a neighbour still reads (the race Section 2 avoids by
 //         splitting loops in BL);
 //   Qs    the saved RK register (Fig. 1, save-state), updated pointwise;
-//   W     primitives u, v, w, p, T (stored in every family, Section 2);
+//   W[2]  primitives u, v, w, p, T (stored in every family, Section 2),
+//         ping-pong: the last kernel of a stage writes the primitives of the
+//         new state into W[1-wcur] while the stage reads W[wcur];
 //   work  SS: 9 velocity-gradient arrays; BL: 18 product + 45 first- and 18
 //         second-derivative arrays;
-//   mixed-precision arrays (FD_F32_ACC64) and the reduction scratch.
+//   Wf[2] binary32 mode: the ten perturbation fields, ping-pong likewise
+//         (W[0] then only serves as scratch of the diagnostics);
+//   and the reduction scratch.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -21,13 +25,13 @@
 #include <vector>
 
 #include "../../include/fdgb300.h"
+#include "fd_host.h"
 #include "fd_internal.h"
 
 namespace {
 
-constexpr double kPi = 3.14159265358979323846;
-constexpr double kRkA[3] = {2.0 / 3.0, 5.0 / 12.0, 3.0 / 5.0};
-constexpr double kRkB[3] = {1.0 / 4.0, 3.0 / 20.0, 0.0};
+using fd::kRkA;
+using fd::kRkB;
 
 thread_local std::string g_err;
 
@@ -70,13 +74,15 @@ struct fd_handle {
     double* Q[2] = {nullptr, nullptr};
     int cur = 0;
     double* Qs = nullptr;
-    double* W = nullptr;
+    double* W[2] = {nullptr, nullptr};
+    float* Wf[2] = {nullptr, nullptr};  // binary32 mode: perturbation fields (10 arrays each)
+    int wcur = 0;                       // W[wcur] / Wf[wcur] hold the primitives of Q[cur] ...
+    bool wvalid = false;                // ... when wvalid
     double* G = nullptr;   // SS
     double* P = nullptr;   // BL
     double* D1 = nullptr;  // BL
     double* D2 = nullptr;  // BL
-    float* Wf = nullptr;   // mixed: perturbation fields (10 arrays)
-    float* Gf = nullptr;   // mixed SS: 9 gradients
+    float* Gf = nullptr;   // binary32 SS: 9 gradients
     double* partial = nullptr;
     double* diag = nullptr;
     int* flag = nullptr;
@@ -115,39 +121,10 @@ const fd::Coef<float>& fd_handle::coef<float>() const {
 
 namespace {
 
-// Host-side constants of the fused residual (see fd::Coef).
-template <class T>
-fd::Coef<T> make_coef(const fd::Grid& g, const fd::Phys& ph, bool shifted) {
-    fd::Coef<T> k{};
-    for (int j = 0; j < 3; ++j) {
-        double s1 = g.inv12h[j], s2 = g.inv12h2[j];
-        k.s1[j] = (T)s1;
-        k.c1[j] = (T)(-0.5 * s1);
-        k.cp[j] = (T)(-s1);
-        k.ks2[j] = (T)(ph.kappa * s2);
-        k.vmix1[j] = (T)(ph.nu / 3.0 * s1);
-    }
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            k.vs2[i][j] = (T)(ph.nu * g.inv12h2[j] * (i == j ? 4.0 / 3.0 : 1.0));
-            k.vmix[i][j] = (T)(ph.nu / 3.0 * g.inv12h[i] * g.inv12h[j]);
-        }
-    k.nu = (T)ph.nu;
-    k.c_rho = shifted ? (T)-1.0 : (T)0.0;
-    k.c_E = shifted ? (T)(-(ph.rhoE0 + ph.p0)) : (T)0.0;
-    return k;
-}
-
 int check_args(int nx, int ny, int nz, double Re, double Mach, double Pr, double gamma, double dt, int algorithm,
                int dtype) {
-    if (nx < 5 || ny < 5 || nz < 5)
-        return fail_global(FD_EINVAL, "grid %dx%dx%d: every axis needs at least 5 points", nx, ny, nz);
-    if ((long long)nx * ny * nz >= (1LL << 31))
-        return fail_global(FD_EINVAL, "grid %dx%dx%d: nx*ny*nz must be below 2^31", nx, ny, nz);
-    if (!(Re > 0) || !(Mach > 0) || !(Pr > 0) || !(dt > 0) || !std::isfinite(Re) || !std::isfinite(Mach) ||
-        !std::isfinite(Pr) || !std::isfinite(dt))
-        return fail_global(FD_EINVAL, "Re, Mach, Pr and dt must be positive and finite");
-    if (!(gamma > 1) || !std::isfinite(gamma)) return fail_global(FD_EINVAL, "gamma must be > 1");
+    if (const char* why = fd::check_instance(nx, ny, nz, Re, Mach, Pr, gamma, dt))
+        return fail_global(FD_EINVAL, "fd_create: grid %dx%dx%d: %s", nx, ny, nz, why);
     if (algorithm != FD_STORE_ALL && algorithm != FD_STORE_SOME && algorithm != FD_RECOMPUTE_ALL)
         return fail_global(FD_EINVAL, "unknown algorithm %d", algorithm);
     if (dtype != FD_F64 && dtype != FD_F32_ACC64) return fail_global(FD_EINVAL, "unknown dtype %d", dtype);
@@ -156,7 +133,7 @@ int check_args(int nx, int ny, int nz, double Re, double Mach, double Pr, double
 
 // Byte layout of a handle's single device allocation.
 struct Layout {
-    size_t q0, q1, qs, w, g, p, d1, d2, wf, gf, partial, diag, flag, total;
+    size_t q0, q1, qs, w0, w1, g, p, d1, d2, wf0, wf1, gf, partial, diag, flag, total;
 };
 
 Layout plan(long long n, int algorithm, int dtype) {
@@ -171,9 +148,10 @@ Layout plan(long long n, int algorithm, int dtype) {
     L.q0 = take(f5);
     L.q1 = take(f5);
     L.qs = take(f5);
-    L.w = take(f5);
-    L.g = L.p = L.d1 = L.d2 = L.wf = L.gf = (size_t)-1;
+    L.w0 = take(f5);
+    L.w1 = L.g = L.p = L.d1 = L.d2 = L.wf0 = L.wf1 = L.gf = (size_t)-1;
     if (dtype == FD_F64) {
+        L.w1 = take(f5);
         if (algorithm == FD_STORE_SOME) L.g = take(9 * n * sizeof(double));
         if (algorithm == FD_STORE_ALL) {
             L.p = take(18 * n * sizeof(double));
@@ -181,7 +159,8 @@ Layout plan(long long n, int algorithm, int dtype) {
             L.d2 = take(18 * n * sizeof(double));
         }
     } else {
-        L.wf = take(10 * n * sizeof(float));
+        L.wf0 = take(10 * n * sizeof(float));
+        L.wf1 = take(10 * n * sizeof(float));
         if (algorithm == FD_STORE_SOME) L.gf = take(9 * n * sizeof(float));
         if (algorithm == FD_STORE_ALL) {
             L.p = take(18 * n * sizeof(float));
@@ -250,7 +229,7 @@ cudaError_t timed(fd_handle* h, int cls, F launch) {
 // Kernels of one stage of family `alg` in precision T.
 template <class T>
 cudaError_t stage_kernels(fd_handle* h, const fd::RKStage& rk, bool resid, const T* Qf, const T* Wf, T* G, T* P,
-                          T* D1, T* D2, const double* Qin, double* Qout) {
+                          T* D1, T* D2, const double* Qin, double* Qout, T* Wnext) {
     const fd::Grid& g = h->grid;
     const fd::Phys& ph = h->phys;
     const fd::Coef<T>& k = h->coef<T>();
@@ -258,13 +237,15 @@ cudaError_t stage_kernels(fd_handle* h, const fd::RKStage& rk, bool resid, const
     cudaError_t e;
     switch (h->algorithm) {
         case FD_RECOMPUTE_ALL:
-            return timed(h, FD_KERNEL_FUSED,
-                         [&] { return fd::launch_ra<T>(g, k, rk, resid, Qf, Wf, Qin, Qout, h->Qs, st); });
+            return timed(h, FD_KERNEL_FUSED, [&] {
+                return fd::launch_ra<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, h->Qs, Wnext, st);
+            });
         case FD_STORE_SOME:
             e = timed(h, FD_KERNEL_GRAD, [&] { return fd::launch_ss_grad<T>(g, k, Wf, G, st); });
             if (e != cudaSuccess) return e;
-            return timed(h, FD_KERNEL_FUSED,
-                         [&] { return fd::launch_ss<T>(g, k, rk, resid, Qf, Wf, G, Qin, Qout, h->Qs, st); });
+            return timed(h, FD_KERNEL_FUSED, [&] {
+                return fd::launch_ss<T>(g, k, ph, rk, resid, Qf, Wf, G, Qin, Qout, h->Qs, Wnext, st);
+            });
         default:
             e = timed(h, FD_KERNEL_PRODUCTS, [&] { return fd::launch_bl_prod<T>(g, Qf, Wf, P, st); });
             if (e != cudaSuccess) return e;
@@ -273,31 +254,41 @@ cudaError_t stage_kernels(fd_handle* h, const fd::RKStage& rk, bool resid, const
             e = timed(h, FD_KERNEL_DERIV2, [&] { return fd::launch_bl_d2<T>(g, Wf, D1, D2, st); });
             if (e != cudaSuccess) return e;
             return timed(h, FD_KERNEL_FUSED, [&] {
-                return fd::launch_bl_res<T>(g, ph, rk, resid, Qf, Wf, D1, D2, Qin, Qout, h->Qs, st);
+                return fd::launch_bl_res<T>(g, ph, rk, resid, Qf, Wf, D1, D2, Qin, Qout, h->Qs, Wnext, st);
             });
     }
 }
 
-// One RK stage (s = 0, 1, 2), or the bare residual into `out` when resid:
-// primitives (Fig. 1, evaluate-u_i,p,T), then the family's derivative and
-// residual kernels, the last of which applies the RK update.
+// One RK stage (s = 0, 1, 2), or the bare residual into `out` when resid.
+// The primitives of Q[cur] (Fig. 1, evaluate-u_i,p,T) come from the previous
+// stage, which wrote them with its update; only after creation or
+// fd_set_state is a separate primitives pass needed.
 cudaError_t run_stage(fd_handle* h, int s, bool resid, double* out) {
     const fd::Grid& g = h->grid;
     const fd::Phys& ph = h->phys;
     fd::RKStage rk{kRkA[s] * h->dt, kRkB[s] * h->dt, s};
     const double* Qin = h->Q[h->cur];
     double* Qout = resid ? out : h->Q[1 - h->cur];
+    const int wc = h->wcur;
     cudaError_t e;
     if (h->dtype == FD_F64) {
-        e = timed(h, FD_KERNEL_PRIMS, [&] { return fd::launch_prims_f64(g, ph, Qin, h->W, h->stream); });
-        if (e != cudaSuccess) return e;
-        return stage_kernels<double>(h, rk, resid, Qin, h->W, h->G, h->P, h->D1, h->D2, Qin, Qout);
+        if (!h->wvalid) {
+            e = timed(h, FD_KERNEL_PRIMS, [&] { return fd::launch_prims_f64(g, ph, Qin, h->W[wc], h->stream); });
+            if (e != cudaSuccess) return e;
+            h->wvalid = true;
+        }
+        return stage_kernels<double>(h, rk, resid, Qin, h->W[wc], h->G, h->P, h->D1, h->D2, Qin, Qout,
+                                     resid ? nullptr : h->W[1 - wc]);
     }
-    e = timed(h, FD_KERNEL_PRIMS, [&] { return fd::launch_prims_f32(g, ph, Qin, h->Wf, h->stream); });
-    if (e != cudaSuccess) return e;
+    if (!h->wvalid) {
+        e = timed(h, FD_KERNEL_PRIMS, [&] { return fd::launch_prims_f32(g, ph, Qin, h->Wf[wc], h->stream); });
+        if (e != cudaSuccess) return e;
+        h->wvalid = true;
+    }
     const long long n = h->n;
-    return stage_kernels<float>(h, rk, resid, h->Wf, h->Wf + 5 * n, h->Gf, reinterpret_cast<float*>(h->P),
-                                reinterpret_cast<float*>(h->D1), reinterpret_cast<float*>(h->D2), Qin, Qout);
+    return stage_kernels<float>(h, rk, resid, h->Wf[wc], h->Wf[wc] + 5 * n, h->Gf, reinterpret_cast<float*>(h->P),
+                                reinterpret_cast<float*>(h->D1), reinterpret_cast<float*>(h->D2), Qin, Qout,
+                                resid ? nullptr : h->Wf[1 - wc]);
 }
 
 }  // namespace
@@ -357,14 +348,16 @@ int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, d
     h->Q[0] = at<double>(h->block, L.q0);
     h->Q[1] = at<double>(h->block, L.q1);
     h->Qs = at<double>(h->block, L.qs);
-    h->W = at<double>(h->block, L.w);
+    h->W[0] = at<double>(h->block, L.w0);
+    h->W[1] = at<double>(h->block, L.w1);
     if (dtype == FD_F64) {
         h->G = at<double>(h->block, L.g);
         h->P = at<double>(h->block, L.p);
         h->D1 = at<double>(h->block, L.d1);
         h->D2 = at<double>(h->block, L.d2);
     } else {
-        h->Wf = at<float>(h->block, L.wf);
+        h->Wf[0] = at<float>(h->block, L.wf0);
+        h->Wf[1] = at<float>(h->block, L.wf1);
         h->Gf = at<float>(h->block, L.gf);
         h->P = at<double>(h->block, L.p);
         h->D1 = at<double>(h->block, L.d1);
@@ -374,29 +367,13 @@ int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, d
     h->diag = at<double>(h->block, L.diag);
     h->flag = at<int>(h->block, L.flag);
 
-    double hx = 2.0 * kPi / nx, hy = 2.0 * kPi / ny, hz = 2.0 * kPi / nz;
-    fd::Grid& g = h->grid;
-    g.nx = nx;
-    g.ny = ny;
-    g.nz = nz;
-    g.n = h->n;
-    const double hs[3] = {hx, hy, hz};
-    for (int a = 0; a < 3; ++a) {
-        g.inv12h[a] = 1.0 / (12.0 * hs[a]);
-        g.inv12h2[a] = 1.0 / (12.0 * hs[a] * hs[a]);
-        g.inv12hf[a] = (float)g.inv12h[a];
-        g.inv12h2f[a] = (float)g.inv12h2[a];
-    }
-    fd::Phys& ph = h->phys;
-    ph.gamma = gamma;
-    ph.gm1 = gamma - 1.0;
-    ph.gM2 = gamma * Mach * Mach;
-    ph.nu = 1.0 / Re;
-    ph.kappa = 1.0 / ((gamma - 1.0) * Mach * Mach * Pr * Re);
-    ph.p0 = 1.0 / (gamma * Mach * Mach);
-    ph.rhoE0 = ph.p0 / (gamma - 1.0);
-    h->kd = make_coef<double>(g, ph, false);
-    h->kf = make_coef<float>(g, ph, true);
+    const double hx = 2.0 * fd::kPi / nx, hy = 2.0 * fd::kPi / ny, hz = 2.0 * fd::kPi / nz;
+    h->grid = fd::make_grid(nx, ny, nz);
+    h->phys = fd::make_phys(Re, Mach, Pr, gamma);
+    const fd::Grid& g = h->grid;
+    const fd::Phys& ph = h->phys;
+    h->kd = fd::make_coef<double>(g, ph, false);
+    h->kf = fd::make_coef<float>(g, ph, true);
 
     e = fd::launch_tgv_ic(g, ph, hx, hy, hz, h->Q[0], h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -415,8 +392,12 @@ int fd_step(fd_handle* h, int n) {
     for (int it = 0; it < n; ++it)
         for (int s = 0; s < 3; ++s) {
             cudaError_t e = run_stage(h, s, false, nullptr);
-            if (e != cudaSuccess) return h->cuda_fail(e, "fd_step: kernel launch");
+            if (e != cudaSuccess) {
+                h->wvalid = false;
+                return h->cuda_fail(e, "fd_step: kernel launch");
+            }
             h->cur = 1 - h->cur;
+            h->wcur = 1 - h->wcur;
         }
     return FD_OK;
 }
@@ -438,6 +419,7 @@ int fd_set_state(fd_handle* h, const double* src, size_t n_elems, int src_is_dev
     if (!src) return h->fail(FD_EINVAL, "fd_set_state: src is NULL");
     if (n_elems != 5 * (size_t)h->n)
         return h->fail(FD_EINVAL, "fd_set_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h->n);
+    h->wvalid = false;
     cudaError_t e = cudaMemcpyAsync(h->Q[h->cur], src, n_elems * sizeof(double),
                                     src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -448,8 +430,10 @@ int fd_set_state(fd_handle* h, const double* src, size_t n_elems, int src_is_dev
 int fd_diagnostics(fd_handle* h, double* ke, double* enstrophy) {
     if (!h) return fail_global(FD_EINVAL, "fd_diagnostics: NULL handle");
     double out[2];
-    // W is scratch between stages: every stage recomputes it from Q first.
-    cudaError_t e = fd::launch_diagnostics_f64(h->grid, h->Q[h->cur], h->W, h->partial, h->diag, h->stream);
+    // Scratch for the velocities: the W buffer the next stage will overwrite
+    // (binary64), or W[0], unused by the binary32 stages.
+    double* Wv = h->dtype == FD_F64 ? h->W[1 - h->wcur] : h->W[0];
+    cudaError_t e = fd::launch_diagnostics_f64(h->grid, h->Q[h->cur], Wv, h->partial, h->diag, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->diag, sizeof out, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "fd_diagnostics");

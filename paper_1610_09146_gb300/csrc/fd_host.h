@@ -1,0 +1,85 @@
+// fd_host.h -- host-side set-up shared by the single-instance and batched
+// paths: grid spacings, flow constants with their negative powers (Section 2:
+// rationals and inverse constants are evaluated once at start-up), the fused
+// residual's coefficients, and the Runge-Kutta coefficients.
+#pragma once
+
+#include <cmath>
+
+#include "fd_core.cuh"
+
+namespace fd {
+
+constexpr double kPi = 3.14159265358979323846;
+// Two-register low-storage RK3 (read of Section 2 / Fig. 1): a, b per stage.
+constexpr double kRkA[3] = {2.0 / 3.0, 5.0 / 12.0, 3.0 / 5.0};
+constexpr double kRkB[3] = {1.0 / 4.0, 3.0 / 20.0, 0.0};
+
+// Periodic grid x_i = i * 2 pi / n per axis (Section 3).
+inline Grid make_grid(int nx, int ny, int nz) {
+    Grid g{};
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.n = nx * ny * nz;
+    const int ns[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) {
+        double h = 2.0 * kPi / ns[a];
+        g.inv12h[a] = 1.0 / (12.0 * h);
+        g.inv12h2[a] = 1.0 / (12.0 * h * h);
+        g.inv12hf[a] = (float)g.inv12h[a];
+        g.inv12h2f[a] = (float)g.inv12h2[a];
+    }
+    return g;
+}
+
+inline Phys make_phys(double Re, double Mach, double Pr, double gamma) {
+    Phys ph{};
+    ph.gamma = gamma;
+    ph.gm1 = gamma - 1.0;
+    ph.gM2 = gamma * Mach * Mach;
+    ph.nu = 1.0 / Re;
+    ph.kappa = 1.0 / ((gamma - 1.0) * Mach * Mach * Pr * Re);
+    ph.p0 = 1.0 / (gamma * Mach * Mach);
+    ph.rhoE0 = ph.p0 / (gamma - 1.0);
+    return ph;
+}
+
+// Constants of the fused residual (see fd::Coef); `shifted` selects the
+// binary32 perturbation form.
+template <class T>
+Coef<T> make_coef(const Grid& g, const Phys& ph, bool shifted) {
+    Coef<T> k{};
+    for (int j = 0; j < 3; ++j) {
+        double s1 = g.inv12h[j], s2 = g.inv12h2[j];
+        k.s1[j] = (T)s1;
+        k.c1[j] = (T)(-0.5 * s1);
+        k.cp[j] = (T)(-s1);
+        k.ks2[j] = (T)(ph.kappa * s2);
+        k.vmix1[j] = (T)(ph.nu / 3.0 * s1);
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            k.vs2[i][j] = (T)(ph.nu * g.inv12h2[j] * (i == j ? 4.0 / 3.0 : 1.0));
+            k.vmix[i][j] = (T)(ph.nu / 3.0 * g.inv12h[i] * g.inv12h[j]);
+        }
+    k.nu = (T)ph.nu;
+    k.c_rho = shifted ? (T)-1.0 : (T)0.0;
+    k.c_E = shifted ? (T)(-(ph.rhoE0 + ph.p0)) : (T)0.0;
+    return k;
+}
+
+// Argument checks shared by fd_create and the batch / server calls; returns
+// nullptr when valid, else a static description of the first problem.
+inline const char* check_instance(int nx, int ny, int nz, double Re, double Mach, double Pr, double gamma,
+                                  double dt) {
+    if (nx < 5 || ny < 5 || nz < 5) return "every axis needs at least 5 points";
+    if ((long long)nx * ny * nz >= (1LL << 31)) return "nx*ny*nz must be below 2^31";
+    if (!(Re > 0) || !(Mach > 0) || !(Pr > 0) || !(dt > 0) || !std::isfinite(Re) || !std::isfinite(Mach) ||
+        !std::isfinite(Pr) || !std::isfinite(dt))
+        return "Re, Mach, Pr and dt must be positive and finite";
+    if (!(gamma > 1) || !std::isfinite(gamma)) return "gamma must be > 1";
+    return nullptr;
+}
+
+}  // namespace fd

@@ -23,18 +23,20 @@ cudaError_t launch_prims_f32(const Grid& g, const Phys& ph, const double* Q, flo
 // Kernels of one stage in precision T (double or float), one launch each.
 // Qf / Wf are the five conserved-like and five primitive-like working
 // fields, Q64 the binary64 state the stage starts from, out the next state
-// (or R when resid), Qs the saved register.
+// (or R when resid), Qs the saved register, Wnext the working fields of `out`
+// for the next stage (written by the last kernel of a stage unless resid).
 //   RA: launch_ra
 //   SS: launch_ss_grad, launch_ss
 //   BL: launch_bl_prod, launch_bl_d1, launch_bl_d2, launch_bl_res
 template <class T>
-cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
-                      const double* Q64, double* out, double* Qs, cudaStream_t st);
+cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid, const T* Qf,
+                      const T* Wf, const double* Q64, double* out, double* Qs, T* Wnext, cudaStream_t st);
 template <class T>
 cudaError_t launch_ss_grad(const Grid& g, const Coef<T>& k, const T* Wf, T* Gw, cudaStream_t st);
 template <class T>
-cudaError_t launch_ss(const Grid& g, const Coef<T>& k, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
-                      const T* Gw, const double* Q64, double* out, double* Qs, cudaStream_t st);
+cudaError_t launch_ss(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid, const T* Qf,
+                      const T* Wf, const T* Gw, const double* Q64, double* out, double* Qs, T* Wnext,
+                      cudaStream_t st);
 template <class T>
 cudaError_t launch_bl_prod(const Grid& g, const T* Qf, const T* Wf, T* P, cudaStream_t st);
 template <class T>
@@ -43,7 +45,39 @@ template <class T>
 cudaError_t launch_bl_d2(const Grid& g, const T* Wf, const T* D1, T* D2, cudaStream_t st);
 template <class T>
 cudaError_t launch_bl_res(const Grid& g, const Phys& ph, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
-                          const T* D1, const T* D2, const double* Q64, double* out, double* Qs, cudaStream_t st);
+                          const T* D1, const T* D2, const double* Q64, double* out, double* Qs, T* Wnext,
+                          cudaStream_t st);
+// ---- batched path ----------------------------------------------------------
+// One instance of a batch as the kernels see it (device memory, read per tile).
+template <class T>
+struct BatchInst {
+    Grid g;
+    Coef<T> k;
+    Phys ph;
+    double* Q[2];  // ping-pong state
+    double* Qs;    // saved RK register
+    T* W[2];       // working fields of Q[0] / Q[1] (binary64: 5 primitives; binary32: 10 perturbation fields)
+    T* G;          // SS: nine velocity gradients (else null)
+    double adt[3], bdt[3];  // a_s dt, b_s dt per stage
+};
+
+// A contiguous run of points [start, start + count) of one instance.
+struct BatchTile {
+    int inst, start, count;
+};
+
+template <class T>
+int batch_blocks_per_sm(bool fused, bool stored_g);
+template <class T>
+cudaError_t launch_batch_prims(const BatchInst<T>* insts, const BatchTile* tiles, int ntiles, int parity, int grid,
+                               cudaStream_t st);
+template <class T>
+cudaError_t launch_batch_grad(const BatchInst<T>* insts, const BatchTile* tiles, int ntiles, int parity, int grid,
+                              cudaStream_t st);
+template <class T>
+cudaError_t launch_batch_fused(const BatchInst<T>* insts, const BatchTile* tiles, int ntiles, bool stored_g,
+                               int stage, int parity, int grid, cudaStream_t st);
+
 cudaError_t launch_diagnostics_f64(const Grid& g, const double* Q, double* Wv, double* partial, double* out,
                                    cudaStream_t st);
 cudaError_t launch_check_finite(const double* x, long long m, int* flag, cudaStream_t st);

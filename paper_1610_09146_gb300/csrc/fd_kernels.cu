@@ -99,59 +99,69 @@ __global__ void k_tgv_ic(Grid g, Phys ph, double hx, double hy, double hz, doubl
 
 // ------------------------------------------------------- Section 2, Eqs. 6-7
 // binary64: u_i = rho u_i / rho, p = (gamma-1)(rho E - rho u_i u_i / 2),
-// T = gamma M^2 p / rho, written to W = (u, v, w, p, T).
-__global__ void __launch_bounds__(256) k_prims_f64(Grid g, Phys ph, const double* __restrict__ Q,
-                                                   double* __restrict__ W) {
-    int idx = grid_index();
-    if (idx >= g.n) return;
-    int n = g.n;
-    double rho = Q[idx];
-    double inv = 1.0 / rho;
-    double m0 = Q[n + idx], m1 = Q[2 * n + idx], m2 = Q[3 * n + idx];
-    double u = m0 * inv, v = m1 * inv, w = m2 * inv;
-    double p = ph.gm1 * fmx(-0.5, fmx(m0, u, fmx(m1, v, m2 * w)), Q[4 * n + idx]);
-    W[idx] = u;
-    W[n + idx] = v;
-    W[2 * n + idx] = w;
-    W[3 * n + idx] = p;
-    W[4 * n + idx] = ph.gM2 * p * inv;
+// T = gamma M^2 p / rho, written to W = (u, v, w, p, T) at point c.
+__device__ __forceinline__ void prims_point(const Phys& ph, const double q[5], double* __restrict__ W, int n,
+                                            int c) {
+    double inv = 1.0 / q[0];
+    double u = q[1] * inv, v = q[2] * inv, w = q[3] * inv;
+    double p = ph.gm1 * fmx(-0.5, fmx(q[1], u, fmx(q[2], v, q[3] * w)), q[4]);
+    W[c] = u;
+    W[n + c] = v;
+    W[2 * n + c] = w;
+    W[3 * n + c] = p;
+    W[4 * n + c] = ph.gM2 * p * inv;
 }
 
-// binary32 perturbation fields from the binary64 state.  With
-// p0 = (gamma-1) rhoE0 and gamma M^2 p0 = 1, Eqs. 6-7 become
+// binary32 perturbation fields F = (rho-1, rho u, rho v, rho w, rhoE-rhoE0,
+// u, v, w, p-p0, T-1) from the binary64 state.  With p0 = (gamma-1) rhoE0
+// and gamma M^2 p0 = 1, Eqs. 6-7 become
 //   p - p0 = (gamma-1)(E' - rho u_i u_i / 2),  T - 1 = (gamma M^2 (p-p0) - rho') / rho.
 // Only the two shifts rho-1 and rhoE-rhoE0 are taken in binary64.
-__global__ void __launch_bounds__(256) k_prims_f32(Grid g, Phys ph, const double* __restrict__ Q,
-                                                   float* __restrict__ F) {
-    int idx = grid_index();
-    if (idx >= g.n) return;
-    int n = g.n;
-    double rho = Q[idx];
-    float rp = (float)(rho - 1.0);
-    float Ep = (float)(Q[4 * n + idx] - ph.rhoE0);
-    float m0 = (float)Q[n + idx], m1 = (float)Q[2 * n + idx], m2 = (float)Q[3 * n + idx];
-    float inv = 1.0f / (float)rho;
+__device__ __forceinline__ void prims_point(const Phys& ph, const double q[5], float* __restrict__ F, int n,
+                                            int c) {
+    float rp = (float)(q[0] - 1.0);
+    float Ep = (float)(q[4] - ph.rhoE0);
+    float m0 = (float)q[1], m1 = (float)q[2], m2 = (float)q[3];
+    float inv = 1.0f / (float)q[0];
     float u = m0 * inv, v = m1 * inv, w = m2 * inv;
     float pp = (float)ph.gm1 * fmx(-0.5f, fmx(m0, u, fmx(m1, v, m2 * w)), Ep);
     float Tp = fmx((float)ph.gM2, pp, -rp) * inv;
-    F[idx] = rp;
-    F[n + idx] = m0;
-    F[2 * n + idx] = m1;
-    F[3 * n + idx] = m2;
-    F[4 * n + idx] = Ep;
-    F[5 * n + idx] = u;
-    F[6 * n + idx] = v;
-    F[7 * n + idx] = w;
-    F[8 * n + idx] = pp;
-    F[9 * n + idx] = Tp;
+    F[c] = rp;
+    F[n + c] = m0;
+    F[2 * n + c] = m1;
+    F[3 * n + c] = m2;
+    F[4 * n + c] = Ep;
+    F[5 * n + c] = u;
+    F[6 * n + c] = v;
+    F[7 * n + c] = w;
+    F[8 * n + c] = pp;
+    F[9 * n + c] = Tp;
+}
+
+// Primitives of the whole state (at creation, after fd_set_state, or when
+// no stage has produced them yet).
+template <class T>
+__global__ void __launch_bounds__(256) k_prims(Grid g, Phys ph, const double* __restrict__ Q, T* __restrict__ W) {
+    int idx = grid_index();
+    if (idx >= g.n) return;
+    const int n = g.n;
+    double q[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) q[f] = Q[f * n + idx];
+    prims_point(ph, q, W, n, idx);
 }
 
 // Final write of a stage: the residual itself (fd_residual), or the
-// two-register RK update (Fig. 1, advance-solution-in-time) in binary64:
-//   Q_out = Qs + a dt R,  Qs <- Qs + b dt R,  with Qs = Q_in at stage 0 (save-state).
+// two-register RK update (Fig. 1, advance-solution-in-time) in binary64,
+//   Q_out = Qs + a dt R,  Qs <- Qs + b dt R,  with Qs = Q_in at stage 0 (save-state),
+// followed by the primitives of Q_out for the next stage (evaluate-u_i,p,T of
+// Fig. 1 moved to the end of the previous stage: it is pointwise, so the point
+// that produces Q_out can produce them without another pass over memory).
 template <class T, bool RESID>
-__device__ __forceinline__ void stage_write(const RKStage& rk, int n, int c, const double* __restrict__ Q64,
-                                            const T R[5], double* __restrict__ out, double* __restrict__ Qs) {
+__device__ __forceinline__ void stage_write(const RKStage& rk, const Phys& ph, int n, int c,
+                                            const double* __restrict__ Q64, const T R[5], double* __restrict__ out,
+                                            double* __restrict__ Qs, T* __restrict__ Wnext) {
+    double qn[5];
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
         double r = (double)R[f];
@@ -159,10 +169,12 @@ __device__ __forceinline__ void stage_write(const RKStage& rk, int n, int c, con
             out[f * n + c] = r;
         } else {
             double qs = rk.stage == 0 ? Q64[f * n + c] : Qs[f * n + c];
-            out[f * n + c] = fmx(rk.adt, r, qs);
+            qn[f] = fmx(rk.adt, r, qs);
+            out[f * n + c] = qn[f];
             if (rk.stage < 2) Qs[f * n + c] = fmx(rk.bdt, r, qs);
         }
     }
+    if (!RESID) prims_point(ph, qn, Wnext, n, c);
 }
 
 // Load the four taps (-2, -1, +1, +2) of field f around c along one axis.
@@ -305,15 +317,16 @@ __device__ __forceinline__ void fused_residual(const Nbr& s, int n, const T* __r
 // products inside a derivative and the 4x4-tap mixed derivatives, is
 // evaluated from its finite-difference formula at the point of use.
 template <class T, bool RESID>
-__global__ void __launch_bounds__(128) k_ra(Grid g, Coef<T> k, RKStage rk, const T* __restrict__ Qf,
+__global__ void __launch_bounds__(128) k_ra(Grid g, Coef<T> k, Phys ph, RKStage rk, const T* __restrict__ Qf,
                                             const T* __restrict__ Wf, const double* __restrict__ Q64,
-                                            double* __restrict__ out, double* __restrict__ Qs) {
+                                            double* __restrict__ out, double* __restrict__ Qs,
+                                            T* __restrict__ Wnext) {
     int idx = grid_index();
     if (idx >= g.n) return;
     const Nbr s = make_nbr(g, idx);
     T R[5];
     fused_residual<T, false>(s, g.n, Qf, Wf, nullptr, k, R);
-    stage_write<T, RESID>(rk, g.n, s.c, Q64, R, out, Qs);
+    stage_write<T, RESID>(rk, ph, g.n, s.c, Q64, R, out, Qs, Wnext);
 }
 
 // ------------------------------------------------------------------ SS
@@ -338,16 +351,16 @@ __global__ void __launch_bounds__(256) k_ss_grad(Grid g, Coef<T> k, const T* __r
 }
 
 template <class T, bool RESID>
-__global__ void __launch_bounds__(128) k_ss(Grid g, Coef<T> k, RKStage rk, const T* __restrict__ Qf,
+__global__ void __launch_bounds__(128) k_ss(Grid g, Coef<T> k, Phys ph, RKStage rk, const T* __restrict__ Qf,
                                             const T* __restrict__ Wf, const T* __restrict__ Gw,
                                             const double* __restrict__ Q64, double* __restrict__ out,
-                                            double* __restrict__ Qs) {
+                                            double* __restrict__ Qs, T* __restrict__ Wnext) {
     int idx = grid_index();
     if (idx >= g.n) return;
     const Nbr s = make_nbr(g, idx);
     T R[5];
     fused_residual<T, true>(s, g.n, Qf, Wf, Gw, k, R);
-    stage_write<T, RESID>(rk, g.n, s.c, Q64, R, out, Qs);
+    stage_write<T, RESID>(rk, ph, g.n, s.c, Q64, R, out, Qs, Wnext);
 }
 
 // ------------------------------------------------------------------ BL
@@ -439,7 +452,8 @@ template <class T, bool RESID>
 __global__ void __launch_bounds__(256) k_bl_res(Grid g, Phys ph, RKStage rk, const T* __restrict__ Qf,
                                                 const T* __restrict__ Wf, const T* __restrict__ D1,
                                                 const T* __restrict__ D2, const double* __restrict__ Q64,
-                                                double* __restrict__ out, double* __restrict__ Qs) {
+                                                double* __restrict__ out, double* __restrict__ Qs,
+                                                T* __restrict__ Wnext) {
     int idx = grid_index();
     if (idx >= g.n) return;
     const int n = g.n;
@@ -483,8 +497,138 @@ __global__ void __launch_bounds__(256) k_bl_res(Grid g, Phys ph, RKStage rk, con
     const Shift<T> sh = shift_of<T>(ph);
     T R[5];
     assemble<T>(t, q, uc, (T)ph.nu, (T)ph.kappa, sh.c_rho, sh.c_E, R);
-    stage_write<T, RESID>(rk, n, c, Q64, R, out, Qs);
+    stage_write<T, RESID>(rk, ph, n, c, Q64, R, out, Qs, Wnext);
 }
+
+// ------------------------------------------------------------- batched path
+// Many instances of different grids in one launch per kernel: a persistent
+// grid walks a work list of tiles (instance, first point, count) with a grid
+// stride; each block stages its tile's instance record in shared memory and
+// runs the same per-point code as the single-instance kernels, so a batched
+// instance evolves bitwise as it would alone.  `parity` selects Q[parity] /
+// W[parity] as the stage's input (all instances of a batch flip together).
+template <class T, bool STORED_G>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_batch_fused(const BatchInst<T>* __restrict__ insts,
+                                                     const BatchTile* __restrict__ tiles, int ntiles, int stage,
+                                                     int parity) {
+    __shared__ BatchInst<T> I;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        __syncthreads();
+        if (threadIdx.x == 0) I = insts[tl.inst];
+        __syncthreads();
+        const int n = I.g.n;
+        const double* Qin = I.Q[parity];
+        double* Qout = I.Q[1 - parity];
+        const T* Wc = I.W[parity];
+        const T* Qf = sizeof(T) == sizeof(double) ? reinterpret_cast<const T*>(Qin) : Wc;
+        const T* Wf = sizeof(T) == sizeof(double) ? Wc : Wc + 5 * (size_t)n;
+        const RKStage rk{I.adt[stage], I.bdt[stage], stage};
+        for (int p = threadIdx.x; p < tl.count; p += blockDim.x) {
+            const Nbr s = make_nbr(I.g, tl.start + p);
+            T R[5];
+            fused_residual<T, STORED_G>(s, n, Qf, Wf, I.G, I.k, R);
+            stage_write<T, false>(rk, I.ph, n, s.c, Qin, R, Qout, I.Qs, I.W[1 - parity]);
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_batch_grad(const BatchInst<T>* __restrict__ insts,
+                                                    const BatchTile* __restrict__ tiles, int ntiles, int parity) {
+    __shared__ BatchInst<T> I;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        __syncthreads();
+        if (threadIdx.x == 0) I = insts[tl.inst];
+        __syncthreads();
+        const int n = I.g.n;
+        const T* Wc = I.W[parity];
+        const T* Wf = sizeof(T) == sizeof(double) ? Wc : Wc + 5 * (size_t)n;
+        for (int p = threadIdx.x; p < tl.count; p += blockDim.x) {
+            const Nbr s = make_nbr(I.g, tl.start + p);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    T tp[4];
+                    taps(Wf + i * n, s.c, s.o[j], tp);
+                    I.G[(3 * i + j) * n + s.c] = I.k.s1[j] * delta1_taps(tp);
+                }
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_batch_prims(const BatchInst<T>* __restrict__ insts,
+                                                     const BatchTile* __restrict__ tiles, int ntiles, int parity) {
+    __shared__ BatchInst<T> I;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        __syncthreads();
+        if (threadIdx.x == 0) I = insts[tl.inst];
+        __syncthreads();
+        const int n = I.g.n;
+        for (int p = threadIdx.x; p < tl.count; p += blockDim.x) {
+            const int c = tl.start + p;
+            double q[5];
+#pragma unroll
+            for (int f = 0; f < 5; ++f) q[f] = I.Q[parity][f * n + c];
+            prims_point(I.ph, q, I.W[parity], n, c);
+        }
+    }
+}
+
+template <class T>
+int batch_blocks_per_sm(bool fused, bool stored_g) {
+    int b = 0;
+    cudaError_t e;
+    if (!fused)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_grad<T>, 256, 0);
+    else if (stored_g)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_fused<T, true>, 256, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_fused<T, false>, 256, 0);
+    return e == cudaSuccess && b > 0 ? b : 1;
+}
+
+template <class T>
+cudaError_t launch_batch_prims(const BatchInst<T>* insts, const BatchTile* tiles, int ntiles, int parity, int grid,
+                               cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    k_batch_prims<T><<<grid, 256, 0, st>>>(insts, tiles, ntiles, parity);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_batch_grad(const BatchInst<T>* insts, const BatchTile* tiles, int ntiles, int parity, int grid,
+                              cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    k_batch_grad<T><<<grid, 256, 0, st>>>(insts, tiles, ntiles, parity);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_batch_fused(const BatchInst<T>* insts, const BatchTile* tiles, int ntiles, bool stored_g,
+                               int stage, int parity, int grid, cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    if (stored_g)
+        k_batch_fused<T, true><<<grid, 256, 0, st>>>(insts, tiles, ntiles, stage, parity);
+    else
+        k_batch_fused<T, false><<<grid, 256, 0, st>>>(insts, tiles, ntiles, stage, parity);
+    return cudaGetLastError();
+}
+
+#define FD_INSTANTIATE_BATCH(T)                                                                                  \
+    template int batch_blocks_per_sm<T>(bool, bool);                                                            \
+    template cudaError_t launch_batch_prims<T>(const BatchInst<T>*, const BatchTile*, int, int, int,            \
+                                               cudaStream_t);                                                   \
+    template cudaError_t launch_batch_grad<T>(const BatchInst<T>*, const BatchTile*, int, int, int, cudaStream_t); \
+    template cudaError_t launch_batch_fused<T>(const BatchInst<T>*, const BatchTile*, int, bool, int, int, int,  \
+                                               cudaStream_t);
+FD_INSTANTIATE_BATCH(double)
+FD_INSTANTIATE_BATCH(float)
+#undef FD_INSTANTIATE_BATCH
 
 // ---------------------------------------------------------------- Section 3
 // Kinetic energy and enstrophy, always in binary64.  Pass 1 writes
@@ -583,22 +727,22 @@ cudaError_t launch_tgv_ic(const Grid& g, const Phys& ph, double hx, double hy, d
 }
 
 cudaError_t launch_prims_f64(const Grid& g, const Phys& ph, const double* Q, double* W, cudaStream_t st) {
-    k_prims_f64<<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, Q, W);
+    k_prims<double><<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, Q, W);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prims_f32(const Grid& g, const Phys& ph, const double* Q, float* F, cudaStream_t st) {
-    k_prims_f32<<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, Q, F);
+    k_prims<float><<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, Q, F);
     return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
-                      const double* Q64, double* out, double* Qs, cudaStream_t st) {
+cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid, const T* Qf,
+                      const T* Wf, const double* Q64, double* out, double* Qs, T* Wnext, cudaStream_t st) {
     if (resid)
-        k_ra<T, true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, rk, Qf, Wf, Q64, out, Qs);
+        k_ra<T, true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Qf, Wf, Q64, out, Qs, Wnext);
     else
-        k_ra<T, false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, rk, Qf, Wf, Q64, out, Qs);
+        k_ra<T, false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Qf, Wf, Q64, out, Qs, Wnext);
     return cudaGetLastError();
 }
 
@@ -609,12 +753,13 @@ cudaError_t launch_ss_grad(const Grid& g, const Coef<T>& k, const T* Wf, T* Gw, 
 }
 
 template <class T>
-cudaError_t launch_ss(const Grid& g, const Coef<T>& k, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
-                      const T* Gw, const double* Q64, double* out, double* Qs, cudaStream_t st) {
+cudaError_t launch_ss(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid, const T* Qf,
+                      const T* Wf, const T* Gw, const double* Q64, double* out, double* Qs, T* Wnext,
+                      cudaStream_t st) {
     if (resid)
-        k_ss<T, true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, rk, Qf, Wf, Gw, Q64, out, Qs);
+        k_ss<T, true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
     else
-        k_ss<T, false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, rk, Qf, Wf, Gw, Q64, out, Qs);
+        k_ss<T, false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
     return cudaGetLastError();
 }
 
@@ -638,25 +783,26 @@ cudaError_t launch_bl_d2(const Grid& g, const T* Wf, const T* D1, T* D2, cudaStr
 
 template <class T>
 cudaError_t launch_bl_res(const Grid& g, const Phys& ph, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
-                          const T* D1, const T* D2, const double* Q64, double* out, double* Qs, cudaStream_t st) {
+                          const T* D1, const T* D2, const double* Q64, double* out, double* Qs, T* Wnext,
+                          cudaStream_t st) {
     if (resid)
-        k_bl_res<T, true><<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, rk, Qf, Wf, D1, D2, Q64, out, Qs);
+        k_bl_res<T, true><<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, rk, Qf, Wf, D1, D2, Q64, out, Qs, Wnext);
     else
-        k_bl_res<T, false><<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, rk, Qf, Wf, D1, D2, Q64, out, Qs);
+        k_bl_res<T, false><<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, rk, Qf, Wf, D1, D2, Q64, out, Qs, Wnext);
     return cudaGetLastError();
 }
 
 #define FD_INSTANTIATE(T)                                                                                        \
-    template cudaError_t launch_ra<T>(const Grid&, const Coef<T>&, const RKStage&, bool, const T*, const T*,     \
-                                      const double*, double*, double*, cudaStream_t);                           \
+    template cudaError_t launch_ra<T>(const Grid&, const Coef<T>&, const Phys&, const RKStage&, bool, const T*,  \
+                                      const T*, const double*, double*, double*, T*, cudaStream_t);             \
     template cudaError_t launch_ss_grad<T>(const Grid&, const Coef<T>&, const T*, T*, cudaStream_t);            \
-    template cudaError_t launch_ss<T>(const Grid&, const Coef<T>&, const RKStage&, bool, const T*, const T*,     \
-                                      const T*, const double*, double*, double*, cudaStream_t);                 \
+    template cudaError_t launch_ss<T>(const Grid&, const Coef<T>&, const Phys&, const RKStage&, bool, const T*,  \
+                                      const T*, const T*, const double*, double*, double*, T*, cudaStream_t);   \
     template cudaError_t launch_bl_prod<T>(const Grid&, const T*, const T*, T*, cudaStream_t);                  \
     template cudaError_t launch_bl_d1<T>(const Grid&, const T*, const T*, const T*, T*, cudaStream_t);          \
     template cudaError_t launch_bl_d2<T>(const Grid&, const T*, const T*, T*, cudaStream_t);                    \
     template cudaError_t launch_bl_res<T>(const Grid&, const Phys&, const RKStage&, bool, const T*, const T*,    \
-                                          const T*, const T*, const double*, double*, double*, cudaStream_t);
+                                          const T*, const T*, const double*, double*, double*, T*, cudaStream_t);
 FD_INSTANTIATE(double)
 FD_INSTANTIATE(float)
 #undef FD_INSTANTIATE

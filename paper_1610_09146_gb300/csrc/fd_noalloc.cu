@@ -108,6 +108,7 @@ extern "C" int fd_residual_noalloc(const double* Q, double* R, int nx, int ny, i
     const fd::RKStage rk{0.0, 0.0, 0};
     if (fd::launch_prims_f64(g, ph, Q, W, st) != cudaSuccess) return FD_ECUDA;
     if (fd::launch_ss_grad<double>(g, k, W, G, st) != cudaSuccess) return FD_ECUDA;
-    if (fd::launch_ss<double>(g, k, rk, true, Q, W, G, Q, R, nullptr, st) != cudaSuccess) return FD_ECUDA;
+    if (fd::launch_ss<double>(g, k, ph, rk, true, Q, W, G, Q, R, nullptr, nullptr, st) != cudaSuccess)
+        return FD_ECUDA;
     return FD_OK;
 }
