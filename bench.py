@@ -325,6 +325,150 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------ batched ensemble
+
+
+def run_batched(args):
+    """64 uneven Taylor-Green solves (grids from {32,48,64,96,128}^3, Re in [400,3200],
+    Mach in [0.1,0.4], 100 RK3 steps): binary32-stencil batch in one persistent launch per
+    family and stage (family and tile size per grid from the autotuner) against the plain
+    binary64 per-solve loop on the same GPU.  A solve = create + steps + diagnostics."""
+    import numpy as np
+    import torch
+
+    import paper_1610_09146_gb300 as fd
+    from paper_1610_09146_gb300 import autotune, native, workloads
+    torch.cuda.set_device(0)
+    fd.build()
+    specs = workloads.ensemble(count=args.instances, steps=args.solve_steps)
+    steps = args.solve_steps
+    tuned, choice = autotune.choose(specs, "f32")
+    pts = sum(s["n"] ** 3 for s in specs)
+
+    def batched(dtype, sp):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with fd.Batch(sp, dtype=dtype) as b:
+            b.step(steps)
+            ke, en = b.diagnostics()
+            states = None
+        t1 = time.perf_counter()
+        return t1 - t0, ke, en
+
+    def loop64():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ke = []
+        for s in specs:
+            with fd.Solver(s["n"], Re=s["Re"], Mach=s["Mach"], dt=s["dt"], algorithm="store_some",
+                           dtype="f64") as sol:
+                sol.step(steps)
+                ke.append(sol.diagnostics()[0])
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, np.array(ke)
+
+    batched("f32", tuned[:4])  # warm-up: module load, allocator pools
+    tb, ke32, _ = batched("f32", tuned)
+    tb2, _, _ = batched("f32", tuned)
+    tb = min(tb, tb2)
+    tl, ke64 = loop64()
+    # binary64 batch of the same solves (store-some everywhere): bitwise the loop's results
+    t64b, ke64b, _ = batched("f64", [dict(s, algorithm="store_some", tile_points=1024) for s in specs])
+    kerr = np.abs(ke32 - ke64) / ke64
+    line = {
+        "workload": f"batched ensemble: {len(specs)} Taylor-Green solves, grids {{32,48,64,96,128}}^3, "
+                    f"Re U[400,3200], Mach U[0.1,0.4], {steps} RK3 steps, seed 1610",
+        "metric": "solves/s", "value": len(specs) / tb, "unit": "solves/s", "higher_is_better": True,
+        "dtype": "f32 stencils / f64 accumulation",
+        "seconds": tb, "point_updates_per_s": pts * steps / tb,
+        "fp64_loop": {"solves_per_s": len(specs) / tl, "seconds": tl, "family": "store_some"},
+        "fp64_batched": {"solves_per_s": len(specs) / t64b, "seconds": t64b,
+                         "ke_bitwise_equal_to_loop": bool(np.array_equal(ke64b, ke64))},
+        "speedup_vs_fp64_loop": tl / tb,
+        "ke_rel_err_vs_fp64": {"max": float(kerr.max()), "median": float(np.median(kerr))},
+        "autotune": {str(n): {"family": f, "tile_points": t, "ms_per_instance_step": round(m, 4)}
+                     for n, (f, t, m) in choice.items()},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ serving
+
+
+def run_serve(args):
+    """Poisson stream (mean 20 requests/s, seeded) of Taylor-Green solves, grids the multiples
+    of 16 in [48, 192], 50-500 steps, Re in [400, 3200], Mach in [0.1, 0.4], binary32 or
+    binary64 with equal odds, served by the continuous-batching server: requests are
+    submitted when their arrival time passes on the wall clock, admitted by device
+    footprint, advanced together one RK3 step per tick.  Latency = completion - arrival."""
+    import numpy as np
+    import torch
+
+    import paper_1610_09146_gb300 as fd
+    from paper_1610_09146_gb300 import autotune, workloads
+    torch.cuda.set_device(0)
+    fd.build()
+    reqs = workloads.requests(count=args.requests, rate=args.rate)
+    # family and tile per (grid, dtype) from the autotuner (cached between runs)
+    best = {}
+    for r in reqs:
+        k = (r["n"], r["dtype"])
+        if k not in best:
+            fam, tile, ms = autotune.tune(r["n"], r["dtype"])
+            best[k] = (fam, tile, ms)
+        r["algorithm"], r["tile_points"] = best[k][0], best[k][1]
+        r["tag"] = r["id"]
+    work = sum(r["n"] ** 3 * r["steps"] for r in reqs)
+    with fd.Server(args.arena_gb * (1 << 30), max_active=args.max_active) as srv:
+        # warm-up outside the measurement: one tiny solve of each dtype
+        for dt_ in ("f32", "f64"):
+            srv.submit(dict(n=16, steps=2, dtype=dt_, tag=-1))
+        while srv.stats()["completed"] < 2:
+            srv.tick()
+        srv.poll()
+        t0 = time.perf_counter()
+        nxt, done, active_hist = 0, {}, []
+        busy = 0.0
+        while len(done) < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and reqs[nxt]["t"] <= now:
+                srv.submit(reqs[nxt])
+                nxt += 1
+            st = srv.stats()
+            if st["active"] == 0 and st["queued"] == 0:
+                if nxt < len(reqs):
+                    time.sleep(max(0.0, min(0.002, reqs[nxt]["t"] - now)))
+                continue
+            ta = time.perf_counter()
+            active_hist.append(srv.tick())
+            tb = time.perf_counter()
+            busy += tb - ta
+            for res in srv.poll():
+                done[res["tag"]] = (tb - t0, res)
+        t_end = max(v[0] for v in done.values())
+        stats = srv.stats()
+    lat = np.array([done[r["id"]][0] - r["t"] for r in reqs])
+    ok = sum(1 for v in done.values() if v[1]["status"] == fd.FD_OK)
+    span = t_end - reqs[0]["t"]
+    offered = args.rate * work / len(reqs)
+    line = {
+        "workload": f"serving: {len(reqs)} Poisson requests (mean {args.rate}/s, seed 9146), grids 48^3-192^3, "
+                    "50-500 RK3 steps, Re U[400,3200], Mach U[0.1,0.4], f32 or f64 per request",
+        "metric": "solves/s", "value": len(reqs) / span, "unit": "solves/s", "higher_is_better": True,
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "mean": float(lat.mean()), "max": float(lat.max())},
+        "completed_ok": ok, "span_s": span,
+        "point_updates_per_s": work / span,
+        "capacity_point_updates_per_busy_s": work / busy,
+        "offered_point_updates_per_s": offered,
+        "offered_over_capacity": offered / (work / busy),
+        "mean_active_per_tick": float(np.mean(active_hist)), "ticks": stats["ticks"],
+        "arena_gb": args.arena_gb, "max_active": args.max_active,
+        "autotune": {f"{n}|{d}": {"family": f, "tile_points": t} for (n, d), (f, t, _) in sorted(best.items())},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------ reference arm
 
 
@@ -373,11 +517,23 @@ def main():
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     ap.add_argument("--variants", nargs="+", default=VARIANTS, choices=VARIANTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["single", "batched", "serve"], default="single",
+                    help="single: the 256^3 line (default); batched / serve: the ensemble and serving runs")
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--solve-steps", type=int, default=100)
+    ap.add_argument("--requests", type=int, default=120)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--arena-gb", type=int, default=64)
+    ap.add_argument("--max-active", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -165,6 +165,127 @@ int fd_profile(fd_handle* h, int enable);
  * output may be NULL.  Errors: FD_EINVAL (class out of range), FD_ECUDA. */
 int fd_profile_read(fd_handle* h, int kernel_class, double* total_ms, long long* launches);
 
+/* ---- batched instances ----------------------------------------------------
+ * The paper has no counterpart: a batch advances many independent
+ * Taylor-Green instances (different grids, Re, Mach, ...) together.  Each
+ * stage is one persistent launch per family present (SS adds its gradient
+ * kernel): a fixed grid of blocks walks a work list of tiles (instance, first
+ * point, point count).  The per-point arithmetic is the single-instance
+ * arithmetic, so every instance evolves bitwise as it would alone with the
+ * same family and dtype.  Steps are replayed from CUDA graphs captured on the
+ * first fd_batch_step. */
+typedef struct fd_instance_desc {
+    int nx, ny, nz;                     /* grid, each axis >= 5, nx*ny*nz < 2^31 */
+    double Re, Mach, Pr, gamma, dt;     /* as for fd_create */
+    int algorithm;                      /* FD_STORE_SOME or FD_RECOMPUTE_ALL */
+    int tile_points;                    /* points per work item, >= 32; 0 = 1024 */
+} fd_instance_desc;
+
+typedef struct fd_batch fd_batch;
+
+/* Create `count` >= 1 instances described by desc[0..count-1], all in one
+ * dtype (FD_F64 or FD_F32_ACC64), each set to its Taylor-Green initial state.
+ * One device allocation holds every instance (through alloc, else
+ * cudaMalloc).  Errors: FD_EINVAL (a bad descriptor; FD_STORE_ALL is not
+ * batched), FD_ENOMEM, FD_ECUDA; the message is in fd_batch_last_error(NULL). */
+int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int dtype, const fd_alloc* alloc,
+                    void* cuda_stream);
+
+/* Enqueue n >= 0 RK3 steps of every instance (asynchronous). */
+int fd_batch_step(fd_batch* b, int n);
+
+/* State of instance i (same layout and rules as fd_get_state / fd_set_state). */
+int fd_batch_get_state(fd_batch* b, int i, double* dst, size_t n_elems, int dst_is_device);
+int fd_batch_set_state(fd_batch* b, int i, const double* src, size_t n_elems, int src_is_device);
+
+/* Kinetic energy and enstrophy of every instance into ke[count], ens[count]
+ * (host arrays; either may be NULL), as fd_diagnostics.  Synchronises. */
+int fd_batch_diagnostics(fd_batch* b, double* ke, double* enstrophy);
+
+/* Number of instances, device bytes held, and per-kernel timing (same kernel
+ * classes and rules as fd_profile / fd_profile_read; the batched fused and
+ * gradient kernels count as FD_KERNEL_FUSED / FD_KERNEL_GRAD; while timing is
+ * on, steps launch kernels directly instead of replaying graphs). */
+int fd_batch_count(const fd_batch* b);
+size_t fd_batch_device_bytes(const fd_batch* b);
+int fd_batch_profile(fd_batch* b, int enable);
+int fd_batch_profile_read(fd_batch* b, int kernel_class, double* total_ms, long long* launches);
+
+/* Free the batch (NULL is a no-op).  Synchronises its stream first. */
+int fd_batch_destroy(fd_batch* b);
+
+/* Message of the last failed call on b, or of the last failed batch call
+ * without a batch (b == NULL) on this thread; "" when there was none. */
+const char* fd_batch_last_error(const fd_batch* b);
+
+/* ---- continuous-batching server -------------------------------------------
+ * The paper has no counterpart.  A server owns one device arena of a fixed
+ * size and runs every admitted Taylor-Green solve through the batched kernels
+ * above: requests queue in submission order; each fd_server_tick admits the
+ * queued requests whose device footprint fits the free arena space (first
+ * fit, later requests may pass one that does not fit yet) up to max_active
+ * solves, advances every active solve by one RK3 step (all of them in the
+ * same launches, grouped by dtype and family), and retires the solves that
+ * reached their step count: their kinetic energy and enstrophy become results
+ * for fd_server_poll and their memory returns to the arena.  Results are
+ * those of the same solve run alone (same per-point arithmetic and
+ * reduction order). */
+typedef struct fd_request {
+    int nx, ny, nz;                  /* grid, as for fd_create */
+    double Re, Mach, Pr, gamma, dt;  /* as for fd_create */
+    int steps;                       /* RK3 steps to run, >= 1 */
+    int dtype;                       /* FD_F64 or FD_F32_ACC64 */
+    int algorithm;                   /* FD_STORE_SOME or FD_RECOMPUTE_ALL */
+    int tile_points;                 /* as in fd_instance_desc */
+    long long tag;                   /* caller's identifier, returned with the result */
+} fd_request;
+
+typedef struct fd_result {
+    long long tag;
+    int status;              /* FD_OK, FD_EUNSTABLE (non-finite diagnostics) or FD_EBUSY (cancelled) */
+    int steps_done;
+    double ke, enstrophy;    /* of the final state (fd_diagnostics) */
+} fd_result;
+
+typedef struct fd_server_stats {
+    int queued, active;
+    long long submitted, completed, ticks;
+    size_t arena_bytes, arena_used;
+} fd_server_stats;
+
+typedef struct fd_server fd_server;
+
+/* A server with a device arena of arena_bytes (allocated once, through alloc
+ * if given) and at most max_active concurrent solves.  Errors: FD_EINVAL,
+ * FD_ENOMEM, FD_ECUDA (message in fd_server_last_error(NULL)). */
+int fd_server_create(fd_server** out, size_t arena_bytes, int max_active, const fd_alloc* alloc, void* cuda_stream);
+
+/* Queue a request (copied).  Errors: FD_EINVAL (bad request), FD_EBUSY (its
+ * footprint exceeds the whole arena, so it could never be admitted). */
+int fd_server_submit(fd_server* s, const fd_request* req);
+
+/* Device bytes a request would occupy while active (0 for a bad request). */
+size_t fd_server_footprint(const fd_request* req);
+
+/* Cancel a queued or active request by tag: it is retired at the next tick
+ * with status FD_EBUSY.  Errors: FD_EINVAL if no such request is pending. */
+int fd_server_cancel(fd_server* s, long long tag);
+
+/* Admit, advance every active solve one RK3 step, retire finished solves.
+ * Synchronises the server's stream.  *active_out (may be NULL) receives the
+ * number of solves active during this tick.  Errors: FD_ECUDA. */
+int fd_server_tick(fd_server* s, int* active_out);
+
+/* Move up to max finished results into out[]; *n_out receives the count. */
+int fd_server_poll(fd_server* s, fd_result* out, int max, int* n_out);
+
+int fd_server_get_stats(const fd_server* s, fd_server_stats* out);
+
+/* Free the server, dropping queued and active requests.  NULL is a no-op. */
+int fd_server_destroy(fd_server* s);
+
+const char* fd_server_last_error(const fd_server* s);
+
 /* ---- residual without any allocation -------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory when they need a residual, for example

@@ -29,15 +29,10 @@ ALGORITHMS = {"store_all": FD_STORE_ALL, "store_some": FD_STORE_SOME, "recompute
               "BL": FD_STORE_ALL, "SS": FD_STORE_SOME, "RA": FD_RECOMPUTE_ALL}
 DTYPES = {"f64": FD_F64, "f32": FD_F32_ACC64, "f32_acc64": FD_F32_ACC64}
 
+from .workloads import dt_for_grid  # noqa: E402  (Section 3 time-step rule)
+
 # Section 3: time step 3.385e-3 on 64^3, halved for each doubling of the grid.
 DT_64 = 3.385e-3
-
-
-def dt_for_grid(n: int) -> float:
-    """Time step of the paper's validation runs for an n^3 grid (n >= 64), following the
-    rule of Section 3 (dt = 3.385e-3 at 64^3, halved per doubling of n); smaller grids
-    keep the 64^3 value."""
-    return DT_64 * 64.0 / max(int(n), 64)
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -65,6 +60,144 @@ def torch_allocator() -> FdAlloc:
     a = FdAlloc(native.ALLOC_FN(_alloc), native.FREE_FN(_free), None)
     _torch_alloc_keep.append(a)  # the callbacks must outlive every handle using them
     return a
+
+
+class Batch:
+    """Many Taylor-Green instances advanced together (see fd_batch_* in include/fdgb300.h).
+
+    instances: sequence of dicts with keys n (int or (nx, ny, nz)), Re, Mach, Pr, gamma, dt,
+    algorithm ("store_some" | "recompute_all"), tile_points; missing keys take the defaults
+    of Solver.  dtype: "f64" | "f32" for the whole batch."""
+
+    def __init__(self, instances, dtype="f32", stream=None, use_torch_allocator=True):
+        import torch
+        self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        self.shapes = []
+        descs = []
+        for spec in instances:
+            n = spec.get("n", 32)
+            nx, ny, nz = (n, n, n) if isinstance(n, int) else tuple(n)
+            alg = spec.get("algorithm", "recompute_all")
+            alg = ALGORITHMS[alg] if isinstance(alg, str) else int(alg)
+            dt = spec.get("dt")
+            dt = dt_for_grid(max(nx, ny, nz)) if dt is None else float(dt)
+            descs.append(native.FdInstanceDesc(nx, ny, nz, spec.get("Re", 1600.0), spec.get("Mach", 0.1),
+                                               spec.get("Pr", 0.71), spec.get("gamma", 1.4), dt, alg,
+                                               int(spec.get("tile_points", 0))))
+            self.shapes.append((nz, ny, nx))
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.stream = int(stream)
+        self._alloc = torch_allocator() if use_torch_allocator else None
+        self.b = native.fd_batch_create(descs, self.dtype, self._alloc, self.stream)
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def step(self, n: int = 1):
+        native.fd_batch_step(self.b, n)
+
+    def state(self, i):
+        out = np.empty((5,) + self.shapes[i])
+        native.fd_batch_get_state(self.b, i, out)
+        return out
+
+    def set_state(self, i, src):
+        native.fd_batch_set_state(self.b, i, np.ascontiguousarray(src, dtype=np.float64))
+
+    def diagnostics(self):
+        return native.fd_batch_diagnostics(self.b)
+
+    def device_bytes(self):
+        return native.fd_batch_device_bytes(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            native.fd_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """Continuous-batching server (fd_server_* in include/fdgb300.h).
+
+    submit(dict) queues a solve (keys: n, steps, Re, Mach, Pr, gamma, dt, dtype, algorithm,
+    tile_points, tag); tick() admits what fits, advances every active solve one RK3 step and
+    retires finished ones; poll() returns finished results as dicts."""
+
+    def __init__(self, arena_bytes, max_active=256, stream=None, use_torch_allocator=True):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.stream = int(stream)
+        self._alloc = torch_allocator() if use_torch_allocator else None
+        self.s = native.fd_server_create(int(arena_bytes), int(max_active), self._alloc, self.stream)
+
+    @staticmethod
+    def request(spec) -> "native.FdRequest":
+        n = spec["n"]
+        nx, ny, nz = (n, n, n) if isinstance(n, int) else tuple(n)
+        alg = spec.get("algorithm", "recompute_all")
+        alg = ALGORITHMS[alg] if isinstance(alg, str) else int(alg)
+        dt = spec.get("dt")
+        dt = dt_for_grid(max(nx, ny, nz)) if dt is None else float(dt)
+        dtype = spec.get("dtype", "f32")
+        dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        return native.FdRequest(nx, ny, nz, spec.get("Re", 1600.0), spec.get("Mach", 0.1), spec.get("Pr", 0.71),
+                                spec.get("gamma", 1.4), dt, int(spec["steps"]), dtype, alg,
+                                int(spec.get("tile_points", 0)), int(spec.get("tag", 0)))
+
+    def submit(self, spec):
+        native.fd_server_submit(self.s, self.request(spec))
+
+    def footprint(self, spec) -> int:
+        return native.fd_server_footprint(self.request(spec))
+
+    def cancel(self, tag):
+        native.fd_server_cancel(self.s, tag)
+
+    def tick(self) -> int:
+        return native.fd_server_tick(self.s)
+
+    def poll(self):
+        return [dict(tag=r.tag, status=r.status, steps=r.steps_done, ke=r.ke, enstrophy=r.enstrophy)
+                for r in native.fd_server_poll(self.s)]
+
+    def stats(self):
+        st = native.fd_server_get_stats(self.s)
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "s", None):
+            native.fd_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Solver:

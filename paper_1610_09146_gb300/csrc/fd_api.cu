@@ -49,18 +49,6 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 }  // namespace
 
-// Per-kernel timing: CUDA events recorded around each launch on the
-// handle's own stream, folded into totals when the ring fills or on read.
-struct Profiler {
-    static constexpr int kCap = 2048;
-    bool on = false;
-    std::vector<cudaEvent_t> ev;  // 2 * kCap events, created on first enable
-    std::vector<int> cls;         // kernel class of each pending pair
-    int used = 0;
-    double total_ms[FD_KERNEL_CLASSES] = {};
-    long long count[FD_KERNEL_CLASSES] = {};
-};
-
 struct fd_handle {
     int nx = 0, ny = 0, nz = 0, n = 0;
     double Re = 0, Mach = 0, Pr = 0, gamma = 0, dt = 0;
@@ -90,7 +78,7 @@ struct fd_handle {
     fd::Phys phys{};
     fd::Coef<double> kd{};  // fused-residual coefficients, binary64 mode
     fd::Coef<float> kf{};   // and binary32 perturbation mode
-    Profiler prof;
+    fd::Profiler prof;
 
     template <class T>
     const fd::Coef<T>& coef() const;
@@ -189,41 +177,9 @@ void device_free(fd_handle* h) {
     h->block = nullptr;
 }
 
-cudaError_t prof_fold(fd_handle* h) {
-    Profiler& P = h->prof;
-    if (P.used == 0) return cudaSuccess;
-    cudaError_t e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return e;
-    for (int i = 0; i < P.used; ++i) {
-        float ms = 0.f;
-        e = cudaEventElapsedTime(&ms, P.ev[2 * i], P.ev[2 * i + 1]);
-        if (e != cudaSuccess) return e;
-        P.total_ms[P.cls[i]] += ms;
-        P.count[P.cls[i]] += 1;
-    }
-    P.used = 0;
-    return cudaSuccess;
-}
-
-// Launch one kernel (the callable returns its launch status), bracketed by a
-// pair of events when profiling is on.
 template <class F>
 cudaError_t timed(fd_handle* h, int cls, F launch) {
-    Profiler& P = h->prof;
-    if (!P.on) return launch();
-    if (P.used == Profiler::kCap) {
-        cudaError_t e = prof_fold(h);
-        if (e != cudaSuccess) return e;
-    }
-    cudaEvent_t a = P.ev[2 * P.used], b = P.ev[2 * P.used + 1];
-    cudaError_t e = cudaEventRecord(a, h->stream);
-    if (e != cudaSuccess) return e;
-    e = launch();
-    if (e != cudaSuccess) return e;
-    e = cudaEventRecord(b, h->stream);
-    if (e != cudaSuccess) return e;
-    P.cls[P.used++] = cls;
-    return cudaSuccess;
+    return h->prof.timed(h->stream, cls, launch);
 }
 
 // Kernels of one stage of family `alg` in precision T.
@@ -474,25 +430,8 @@ size_t fd_device_bytes(const fd_handle* h) { return h ? h->block_bytes : 0; }
 
 int fd_profile(fd_handle* h, int enable) {
     if (!h) return fail_global(FD_EINVAL, "fd_profile: NULL handle");
-    Profiler& P = h->prof;
-    if (enable && P.ev.empty()) {
-        P.ev.resize(2 * Profiler::kCap);
-        P.cls.resize(Profiler::kCap);
-        for (auto& e : P.ev) {
-            cudaError_t rc = cudaEventCreate(&e);
-            if (rc != cudaSuccess) {
-                e = nullptr;
-                return h->cuda_fail(rc, "fd_profile: cudaEventCreate");
-            }
-        }
-    }
-    cudaError_t e = prof_fold(h);
+    cudaError_t e = h->prof.enable(enable != 0, h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "fd_profile");
-    for (int c = 0; c < FD_KERNEL_CLASSES; ++c) {
-        P.total_ms[c] = 0.0;
-        P.count[c] = 0;
-    }
-    P.on = enable != 0;
     return FD_OK;
 }
 
@@ -500,7 +439,7 @@ int fd_profile_read(fd_handle* h, int kernel_class, double* total_ms, long long*
     if (!h) return fail_global(FD_EINVAL, "fd_profile_read: NULL handle");
     if (kernel_class < 0 || kernel_class >= FD_KERNEL_CLASSES)
         return h->fail(FD_EINVAL, "fd_profile_read: kernel class %d out of range", kernel_class);
-    cudaError_t e = prof_fold(h);
+    cudaError_t e = h->prof.fold(h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "fd_profile_read");
     if (total_ms) *total_ms = h->prof.total_ms[kernel_class];
     if (launches) *launches = h->prof.count[kernel_class];
@@ -510,8 +449,7 @@ int fd_profile_read(fd_handle* h, int kernel_class, double* total_ms, long long*
 int fd_destroy(fd_handle* h) {
     if (!h) return FD_OK;
     cudaStreamSynchronize(h->stream);
-    for (auto e : h->prof.ev)
-        if (e) cudaEventDestroy(e);
+    h->prof.destroy();
     device_free(h);
     delete h;
     return FD_OK;

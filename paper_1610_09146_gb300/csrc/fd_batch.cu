@@ -1,0 +1,482 @@
+// fd_batch.cu -- many independent Taylor-Green instances advanced together
+// (the batched path of include/fdgb300.h).
+//
+// Device memory (one allocation, 256-byte-aligned pieces):
+//   instance table  BatchInst<T>[count]   grid, coefficients, buffer pointers
+//   tile lists      BatchTile[...]        one list per family (SS, RA) and one
+//                                         over all instances (primitives pass)
+//   per instance    Q[2], Qs (binary64), W[2] working fields, G (SS)
+//   diagnostics     partial sums and 2 x count results
+// A step is three stages; each stage launches, per family present, the
+// persistent kernels of fd_kernels.cu (SS: gradients then fused; RA: fused).
+// The two families touch disjoint instances, so the captured step graph runs
+// them on two branches (fork/join) and their tails overlap.  All instances
+// flip their ping-pong parity together, so two graphs exist: one for a step
+// that starts at parity 0 and one for parity 1.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fdgb300.h"
+#include "fd_host.h"
+#include "fd_internal.h"
+
+namespace {
+
+thread_local std::string g_batch_err;
+
+int fail_global(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_batch_err = buf;
+    return code;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+constexpr int kThreads = 256;
+constexpr int kDefaultTile = 1024;
+
+struct InstHost {
+    fd_instance_desc d;
+    int n;
+    size_t q0, q1, qs, w0, w1, g;  // byte offsets in the allocation
+};
+
+}  // namespace
+
+struct fd_batch {
+    int count = 0, dtype = 0, device = 0;
+    cudaStream_t stream = nullptr;
+    fd_alloc alloc{};
+    bool has_alloc = false;
+    void* block = nullptr;
+    size_t block_bytes = 0;
+    std::vector<InstHost> inst;
+    void* d_inst = nullptr;                       // BatchInst<T>[count]
+    fd::BatchTile *d_ss = nullptr, *d_ra = nullptr, *d_all = nullptr;
+    int n_ss = 0, n_ra = 0, n_all = 0;
+    int grid_ss_fused = 0, grid_ra_fused = 0, grid_grad = 0, grid_prims = 0;
+    double* partial = nullptr;
+    double* diag = nullptr;
+    int parity = 0;
+    bool wvalid = false;
+    cudaStream_t cap[2] = {nullptr, nullptr};      // capture streams
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    fd::Profiler prof;
+    std::string err;
+
+    int fail(int code, const char* fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        err = buf;
+        return code;
+    }
+    int cuda_fail(cudaError_t e, const char* what) { return fail(FD_ECUDA, "%s: %s", what, cudaGetErrorString(e)); }
+    char* base() const { return static_cast<char*>(block); }
+};
+
+namespace {
+
+template <class T>
+void fill_inst(const fd_batch* b, std::vector<fd::BatchInst<T>>& out) {
+    out.resize(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        const InstHost& h = b->inst[i];
+        fd::BatchInst<T>& I = out[i];
+        std::memset(&I, 0, sizeof I);
+        I.g = fd::make_grid(h.d.nx, h.d.ny, h.d.nz);
+        I.ph = fd::make_phys(h.d.Re, h.d.Mach, h.d.Pr, h.d.gamma);
+        I.k = fd::make_coef<T>(I.g, I.ph, sizeof(T) == sizeof(float));
+        I.Q[0] = reinterpret_cast<double*>(b->base() + h.q0);
+        I.Q[1] = reinterpret_cast<double*>(b->base() + h.q1);
+        I.Qs = reinterpret_cast<double*>(b->base() + h.qs);
+        I.W[0] = reinterpret_cast<T*>(b->base() + h.w0);
+        I.W[1] = reinterpret_cast<T*>(b->base() + h.w1);
+        I.G = h.g == (size_t)-1 ? nullptr : reinterpret_cast<T*>(b->base() + h.g);
+        for (int s = 0; s < 3; ++s) {
+            I.adt[s] = fd::kRkA[s] * h.d.dt;
+            I.bdt[s] = fd::kRkB[s] * h.d.dt;
+        }
+    }
+}
+
+void make_tiles(const fd_batch* b, int family, std::vector<fd::BatchTile>& out) {
+    for (int i = 0; i < b->count; ++i) {
+        const InstHost& h = b->inst[i];
+        if (family >= 0 && h.d.algorithm != family) continue;
+        int tp = h.d.tile_points > 0 ? h.d.tile_points : kDefaultTile;
+        for (int s = 0; s < h.n; s += tp) out.push_back({i, s, std::min(tp, h.n - s)});
+    }
+}
+
+// Kernels of stage s at parity p for the instances of one family.
+template <class T>
+cudaError_t enqueue_family(fd_batch* b, bool ss, int s, int p, cudaStream_t st) {
+    auto* I = static_cast<const fd::BatchInst<T>*>(b->d_inst);
+    if (ss) {
+        if (!b->n_ss) return cudaSuccess;
+        cudaError_t e = b->prof.timed(st, FD_KERNEL_GRAD, [&] {
+            return fd::launch_batch_grad<T>(I, b->d_ss, b->n_ss, p, b->grid_grad, st);
+        });
+        if (e != cudaSuccess) return e;
+        return b->prof.timed(st, FD_KERNEL_FUSED, [&] {
+            return fd::launch_batch_fused<T>(I, b->d_ss, b->n_ss, true, s, p, b->grid_ss_fused, st);
+        });
+    }
+    if (!b->n_ra) return cudaSuccess;
+    return b->prof.timed(st, FD_KERNEL_FUSED, [&] {
+        return fd::launch_batch_fused<T>(I, b->d_ra, b->n_ra, false, s, p, b->grid_ra_fused, st);
+    });
+}
+
+// One RK3 step starting at parity p.  With two streams the SS family runs on
+// st0 and RA on st1 between a fork and a join; with one stream in sequence.
+template <class T>
+cudaError_t enqueue_step(fd_batch* b, int p, cudaStream_t st0, cudaStream_t st1) {
+    cudaError_t e;
+    bool two = st1 != nullptr && b->n_ss && b->n_ra;
+    if (two) {
+        if ((e = cudaEventRecord(b->fork, st0)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st1, b->fork, 0)) != cudaSuccess) return e;
+    }
+    for (int s = 0, q = p; s < 3; ++s, q ^= 1) {
+        if ((e = enqueue_family<T>(b, true, s, q, st0)) != cudaSuccess) return e;
+        if ((e = enqueue_family<T>(b, false, s, q, two ? st1 : st0)) != cudaSuccess) return e;
+    }
+    if (two) {
+        if ((e = cudaEventRecord(b->join, st1)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st0, b->join, 0)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t step_direct(fd_batch* b, int p) {
+    return b->dtype == FD_F64 ? enqueue_step<double>(b, p, b->stream, nullptr)
+                              : enqueue_step<float>(b, p, b->stream, nullptr);
+}
+
+cudaError_t build_graphs(fd_batch* b) {
+    cudaError_t e;
+    if (!b->cap[0]) {
+        for (auto& c : b->cap)
+            if ((e = cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    for (int p = 0; p < 2; ++p) {
+        cudaGraph_t g = nullptr;
+        if ((e = cudaStreamBeginCapture(b->cap[0], cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+        cudaError_t le = b->dtype == FD_F64 ? enqueue_step<double>(b, p, b->cap[0], b->cap[1])
+                                            : enqueue_step<float>(b, p, b->cap[0], b->cap[1]);
+        e = cudaStreamEndCapture(b->cap[0], &g);
+        if (le != cudaSuccess) return le;
+        if (e != cudaSuccess) return e;
+        e = cudaGraphInstantiate(&b->exec[p], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void release(fd_batch* b) {
+    if (b->stream || b->block) cudaStreamSynchronize(b->stream);
+    for (auto& x : b->exec)
+        if (x) cudaGraphExecDestroy(x);
+    for (auto& c : b->cap)
+        if (c) cudaStreamDestroy(c);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
+    b->prof.destroy();
+    if (b->block) {
+        if (b->has_alloc)
+            b->alloc.free(b->alloc.ctx, b->block, b->block_bytes, b->stream);
+        else
+            cudaFree(b->block);
+    }
+    b->block = nullptr;
+}
+
+int ensure_prims(fd_batch* b) {
+    if (b->wvalid) return FD_OK;
+    cudaError_t e = b->prof.timed(b->stream, FD_KERNEL_PRIMS, [&] {
+        if (b->dtype == FD_F64)
+            return fd::launch_batch_prims<double>(static_cast<const fd::BatchInst<double>*>(b->d_inst), b->d_all,
+                                                  b->n_all, b->parity, b->grid_prims, b->stream);
+        return fd::launch_batch_prims<float>(static_cast<const fd::BatchInst<float>*>(b->d_inst), b->d_all,
+                                             b->n_all, b->parity, b->grid_prims, b->stream);
+    });
+    if (e != cudaSuccess) return b->cuda_fail(e, "fd_batch: primitives");
+    b->wvalid = true;
+    return FD_OK;
+}
+
+template <class T>
+int grid_for(int sms, bool fused, bool stored_g) {
+    return sms * fd::batch_blocks_per_sm<T>(fused, stored_g);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int dtype, const fd_alloc* alloc,
+                    void* cuda_stream) {
+    if (!out) return fail_global(FD_EINVAL, "fd_batch_create: out is NULL");
+    *out = nullptr;
+    if (!desc || count < 1) return fail_global(FD_EINVAL, "fd_batch_create: need count >= 1 descriptors");
+    if (dtype != FD_F64 && dtype != FD_F32_ACC64) return fail_global(FD_EINVAL, "fd_batch_create: dtype %d", dtype);
+    if (alloc && (!alloc->alloc || !alloc->free))
+        return fail_global(FD_EINVAL, "fd_batch_create: allocator needs both alloc and free");
+    for (int i = 0; i < count; ++i) {
+        const fd_instance_desc& d = desc[i];
+        if (const char* why = fd::check_instance(d.nx, d.ny, d.nz, d.Re, d.Mach, d.Pr, d.gamma, d.dt))
+            return fail_global(FD_EINVAL, "fd_batch_create: instance %d: %s", i, why);
+        if (d.algorithm != FD_STORE_SOME && d.algorithm != FD_RECOMPUTE_ALL)
+            return fail_global(FD_EINVAL, "fd_batch_create: instance %d: algorithm %d is not batched", i, d.algorithm);
+        if (d.tile_points != 0 && d.tile_points < 32)
+            return fail_global(FD_EINVAL, "fd_batch_create: instance %d: tile_points %d < 32", i, d.tile_points);
+    }
+    fd_batch* b = new (std::nothrow) fd_batch();
+    if (!b) return fail_global(FD_ENOMEM, "fd_batch_create: host allocation failed");
+    b->count = count;
+    b->dtype = dtype;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e != cudaSuccess) {
+        delete b;
+        return fail_global(FD_ECUDA, "fd_batch_create: cudaGetDevice: %s", cudaGetErrorString(e));
+    }
+    const size_t tsize = dtype == FD_F64 ? sizeof(double) : sizeof(float);
+    const size_t wfields = dtype == FD_F64 ? 5 : 10;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off += align256(bytes);
+        return at;
+    };
+    const size_t inst_bytes = dtype == FD_F64 ? sizeof(fd::BatchInst<double>) : sizeof(fd::BatchInst<float>);
+    size_t o_inst = take(inst_bytes * count);
+    b->inst.resize(count);
+    for (int i = 0; i < count; ++i) {
+        InstHost& h = b->inst[i];
+        h.d = desc[i];
+        h.n = desc[i].nx * desc[i].ny * desc[i].nz;
+        size_t f5 = 5 * (size_t)h.n * sizeof(double);
+        h.q0 = take(f5);
+        h.q1 = take(f5);
+        h.qs = take(f5);
+        h.w0 = take(wfields * h.n * tsize);
+        h.w1 = take(wfields * h.n * tsize);
+        h.g = desc[i].algorithm == FD_STORE_SOME ? take(9 * (size_t)h.n * tsize) : (size_t)-1;
+    }
+    std::vector<fd::BatchTile> t_ss, t_ra, t_all;
+    make_tiles(b, FD_STORE_SOME, t_ss);
+    make_tiles(b, FD_RECOMPUTE_ALL, t_ra);
+    make_tiles(b, -1, t_all);
+    size_t o_ss = take(std::max<size_t>(1, t_ss.size()) * sizeof(fd::BatchTile));
+    size_t o_ra = take(std::max<size_t>(1, t_ra.size()) * sizeof(fd::BatchTile));
+    size_t o_all = take(t_all.size() * sizeof(fd::BatchTile));
+    size_t o_part = take(2 * fd::kDiagBlocks * sizeof(double));
+    size_t o_diag = take(2 * (size_t)count * sizeof(double));
+    b->block_bytes = off;
+    if (alloc) {
+        b->alloc = *alloc;
+        b->has_alloc = true;
+        b->block = alloc->alloc(alloc->ctx, off, cuda_stream);
+        if (!b->block) {
+            delete b;
+            return fail_global(FD_ENOMEM, "fd_batch_create: allocator returned NULL for %zu bytes", off);
+        }
+    } else if ((e = cudaMalloc(&b->block, off)) != cudaSuccess) {
+        cudaGetLastError();
+        b->block = nullptr;
+        delete b;
+        return fail_global(FD_ENOMEM, "fd_batch_create: cudaMalloc(%zu): %s", off, cudaGetErrorString(e));
+    }
+    b->d_inst = b->base() + o_inst;
+    b->d_ss = reinterpret_cast<fd::BatchTile*>(b->base() + o_ss);
+    b->d_ra = reinterpret_cast<fd::BatchTile*>(b->base() + o_ra);
+    b->d_all = reinterpret_cast<fd::BatchTile*>(b->base() + o_all);
+    b->n_ss = (int)t_ss.size();
+    b->n_ra = (int)t_ra.size();
+    b->n_all = (int)t_all.size();
+    b->partial = reinterpret_cast<double*>(b->base() + o_part);
+    b->diag = reinterpret_cast<double*>(b->base() + o_diag);
+
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (sms <= 0) sms = 152;
+    if (dtype == FD_F64) {
+        b->grid_ss_fused = grid_for<double>(sms, true, true);
+        b->grid_ra_fused = grid_for<double>(sms, true, false);
+        b->grid_grad = grid_for<double>(sms, false, false);
+    } else {
+        b->grid_ss_fused = grid_for<float>(sms, true, true);
+        b->grid_ra_fused = grid_for<float>(sms, true, false);
+        b->grid_grad = grid_for<float>(sms, false, false);
+    }
+    b->grid_prims = b->grid_grad;
+
+    // Instance table and tile lists (host staging is pageable; copies complete
+    // before the synchronisation below).
+    if (dtype == FD_F64) {
+        std::vector<fd::BatchInst<double>> I;
+        fill_inst<double>(b, I);
+        e = cudaMemcpyAsync(b->d_inst, I.data(), I.size() * sizeof I[0], cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    } else {
+        std::vector<fd::BatchInst<float>> I;
+        fill_inst<float>(b, I);
+        e = cudaMemcpyAsync(b->d_inst, I.data(), I.size() * sizeof I[0], cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    }
+    auto up = [&](fd::BatchTile* dst, const std::vector<fd::BatchTile>& v) {
+        if (v.empty() || e != cudaSuccess) return;
+        e = cudaMemcpyAsync(dst, v.data(), v.size() * sizeof v[0], cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    };
+    up(b->d_ss, t_ss);
+    up(b->d_ra, t_ra);
+    up(b->d_all, t_all);
+    // Taylor-Green initial state of every instance (Section 3).
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        const InstHost& h = b->inst[i];
+        fd::Grid g = fd::make_grid(h.d.nx, h.d.ny, h.d.nz);
+        fd::Phys ph = fd::make_phys(h.d.Re, h.d.Mach, h.d.Pr, h.d.gamma);
+        e = fd::launch_tgv_ic(g, ph, 2.0 * fd::kPi / h.d.nx, 2.0 * fd::kPi / h.d.ny, 2.0 * fd::kPi / h.d.nz,
+                              reinterpret_cast<double*>(b->base() + h.q0), b->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        release(b);
+        delete b;
+        return fail_global(FD_ECUDA, "fd_batch_create: set-up: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return FD_OK;
+}
+
+int fd_batch_step(fd_batch* b, int n) {
+    if (!b) return fail_global(FD_EINVAL, "fd_batch_step: NULL batch");
+    if (n < 0) return b->fail(FD_EINVAL, "fd_batch_step: n = %d < 0", n);
+    if (n == 0) return FD_OK;
+    int rc = ensure_prims(b);
+    if (rc != FD_OK) return rc;
+    cudaError_t e;
+    if (b->prof.on) {
+        for (int it = 0; it < n; ++it) {
+            if ((e = step_direct(b, b->parity)) != cudaSuccess) return b->cuda_fail(e, "fd_batch_step");
+            b->parity ^= 1;
+        }
+        return FD_OK;
+    }
+    if (!b->exec[0] && (e = build_graphs(b)) != cudaSuccess) return b->cuda_fail(e, "fd_batch_step: graph capture");
+    for (int it = 0; it < n; ++it) {
+        if ((e = cudaGraphLaunch(b->exec[b->parity], b->stream)) != cudaSuccess)
+            return b->cuda_fail(e, "fd_batch_step: graph launch");
+        b->parity ^= 1;
+    }
+    return FD_OK;
+}
+
+int fd_batch_get_state(fd_batch* b, int i, double* dst, size_t n_elems, int dst_is_device) {
+    if (!b) return fail_global(FD_EINVAL, "fd_batch_get_state: NULL batch");
+    if (i < 0 || i >= b->count) return b->fail(FD_EINVAL, "fd_batch_get_state: instance %d out of range", i);
+    if (!dst) return b->fail(FD_EINVAL, "fd_batch_get_state: dst is NULL");
+    const InstHost& h = b->inst[i];
+    if (n_elems != 5 * (size_t)h.n)
+        return b->fail(FD_EINVAL, "fd_batch_get_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h.n);
+    const char* src = b->base() + (b->parity ? h.q1 : h.q0);
+    cudaError_t e = cudaMemcpyAsync(dst, src, n_elems * sizeof(double),
+                                    dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return b->cuda_fail(e, "fd_batch_get_state");
+    return FD_OK;
+}
+
+int fd_batch_set_state(fd_batch* b, int i, const double* src, size_t n_elems, int src_is_device) {
+    if (!b) return fail_global(FD_EINVAL, "fd_batch_set_state: NULL batch");
+    if (i < 0 || i >= b->count) return b->fail(FD_EINVAL, "fd_batch_set_state: instance %d out of range", i);
+    if (!src) return b->fail(FD_EINVAL, "fd_batch_set_state: src is NULL");
+    const InstHost& h = b->inst[i];
+    if (n_elems != 5 * (size_t)h.n)
+        return b->fail(FD_EINVAL, "fd_batch_set_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h.n);
+    b->wvalid = false;
+    char* dst = b->base() + (b->parity ? h.q1 : h.q0);
+    cudaError_t e = cudaMemcpyAsync(dst, src, n_elems * sizeof(double),
+                                    src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return b->cuda_fail(e, "fd_batch_set_state");
+    return FD_OK;
+}
+
+int fd_batch_diagnostics(fd_batch* b, double* ke, double* enstrophy) {
+    if (!b) return fail_global(FD_EINVAL, "fd_batch_diagnostics: NULL batch");
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < b->count && e == cudaSuccess; ++i) {
+        const InstHost& h = b->inst[i];
+        fd::Grid g = fd::make_grid(h.d.nx, h.d.ny, h.d.nz);
+        const double* Q = reinterpret_cast<const double*>(b->base() + (b->parity ? h.q1 : h.q0));
+        // Scratch for the velocities: the working-field buffer the next stage
+        // overwrites (at least 3 x n doubles in either precision).
+        double* Wv = reinterpret_cast<double*>(b->base() + (b->parity ? h.w0 : h.w1));
+        e = fd::launch_diagnostics_f64(g, Q, Wv, b->partial, b->diag + 2 * i, b->stream);
+    }
+    std::vector<double> out(2 * (size_t)b->count);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out.data(), b->diag, out.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return b->cuda_fail(e, "fd_batch_diagnostics");
+    for (int i = 0; i < b->count; ++i) {
+        if (ke) ke[i] = out[2 * i];
+        if (enstrophy) enstrophy[i] = out[2 * i + 1];
+    }
+    return FD_OK;
+}
+
+int fd_batch_count(const fd_batch* b) { return b ? b->count : 0; }
+
+size_t fd_batch_device_bytes(const fd_batch* b) { return b ? b->block_bytes : 0; }
+
+int fd_batch_profile(fd_batch* b, int enable) {
+    if (!b) return fail_global(FD_EINVAL, "fd_batch_profile: NULL batch");
+    cudaError_t e = b->prof.enable(enable != 0, b->stream);
+    if (e != cudaSuccess) return b->cuda_fail(e, "fd_batch_profile");
+    return FD_OK;
+}
+
+int fd_batch_profile_read(fd_batch* b, int kernel_class, double* total_ms, long long* launches) {
+    if (!b) return fail_global(FD_EINVAL, "fd_batch_profile_read: NULL batch");
+    if (kernel_class < 0 || kernel_class >= FD_KERNEL_CLASSES)
+        return b->fail(FD_EINVAL, "fd_batch_profile_read: kernel class %d out of range", kernel_class);
+    cudaError_t e = b->prof.fold(b->stream);
+    if (e != cudaSuccess) return b->cuda_fail(e, "fd_batch_profile_read");
+    if (total_ms) *total_ms = b->prof.total_ms[kernel_class];
+    if (launches) *launches = b->prof.count[kernel_class];
+    return FD_OK;
+}
+
+int fd_batch_destroy(fd_batch* b) {
+    if (!b) return FD_OK;
+    release(b);
+    delete b;
+    return FD_OK;
+}
+
+const char* fd_batch_last_error(const fd_batch* b) { return b ? b->err.c_str() : g_batch_err.c_str(); }
+
+}  // extern "C"

@@ -4,7 +4,10 @@
 // residual's coefficients, and the Runge-Kutta coefficients.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cmath>
+#include <vector>
 
 #include "fd_core.cuh"
 
@@ -81,5 +84,78 @@ inline const char* check_instance(int nx, int ny, int nz, double Re, double Mach
     if (!(gamma > 1) || !std::isfinite(gamma)) return "gamma must be > 1";
     return nullptr;
 }
+
+// Per-kernel timing: CUDA events recorded around each launch on the caller's
+// stream, folded into per-class totals when the ring fills or on read.
+struct Profiler {
+    static constexpr int kCap = 2048;
+    static constexpr int kClasses = 6;  // FD_KERNEL_CLASSES
+    bool on = false;
+    std::vector<cudaEvent_t> ev;  // 2 * kCap events, created on first enable
+    std::vector<int> cls;         // kernel class of each pending pair
+    int used = 0;
+    double total_ms[kClasses] = {};
+    long long count[kClasses] = {};
+
+    cudaError_t enable(bool en, cudaStream_t st) {
+        if (en && ev.empty()) {
+            ev.assign(2 * kCap, nullptr);
+            cls.assign(kCap, 0);
+            for (auto& e : ev) {
+                cudaError_t rc = cudaEventCreate(&e);
+                if (rc != cudaSuccess) return rc;
+            }
+        }
+        cudaError_t rc = fold(st);
+        if (rc != cudaSuccess) return rc;
+        for (int c = 0; c < kClasses; ++c) {
+            total_ms[c] = 0.0;
+            count[c] = 0;
+        }
+        on = en;
+        return cudaSuccess;
+    }
+
+    cudaError_t fold(cudaStream_t st) {
+        if (used == 0) return cudaSuccess;
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        for (int i = 0; i < used; ++i) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+            if (e != cudaSuccess) return e;
+            total_ms[cls[i]] += ms;
+            count[cls[i]] += 1;
+        }
+        used = 0;
+        return cudaSuccess;
+    }
+
+    // Launch one kernel (the callable returns its launch status), bracketed by
+    // a pair of events when timing is on.
+    template <class F>
+    cudaError_t timed(cudaStream_t st, int c, F launch) {
+        if (!on) return launch();
+        if (used == kCap) {
+            cudaError_t e = fold(st);
+            if (e != cudaSuccess) return e;
+        }
+        cudaEvent_t a = ev[2 * used], b = ev[2 * used + 1];
+        cudaError_t e = cudaEventRecord(a, st);
+        if (e != cudaSuccess) return e;
+        e = launch();
+        if (e != cudaSuccess) return e;
+        e = cudaEventRecord(b, st);
+        if (e != cudaSuccess) return e;
+        cls[used++] = c;
+        return cudaSuccess;
+    }
+
+    void destroy() {
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+        ev.clear();
+    }
+};
 
 }  // namespace fd

@@ -1,0 +1,523 @@
+// fd_server.cu -- continuous-batching server for Taylor-Green solves (the
+// serving path of include/fdgb300.h).
+//
+// Memory: one device arena, sized at creation, split by a first-fit
+// free-list allocator with coalescing; an admitted solve takes one block for
+// its Q[2], Qs, W[2] (and G for store-some), laid out as in a batch.  The
+// instance tables and tile lists live in separate device buffers that grow
+// geometrically.
+//
+// Scheduling: FIFO queue, first-fit admission by footprint and a cap on
+// active solves.  All active solves share one ping-pong parity: a newly
+// admitted solve writes its initial state into Q[parity], so every tick runs
+// one RK3 step of every active solve with the batched kernels, one group per
+// (dtype, family).  A tick ends synchronised; finished solves are retired
+// with their diagnostics and their memory returns to the arena.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fdgb300.h"
+#include "fd_host.h"
+#include "fd_internal.h"
+
+namespace {
+
+thread_local std::string g_server_err;
+
+int fail_global(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_server_err = buf;
+    return code;
+}
+
+constexpr size_t kAlign = 256;
+constexpr int kDefaultTile = 1024;
+size_t align256(size_t b) { return (b + kAlign - 1) & ~(kAlign - 1); }
+
+// First-fit allocator over [0, capacity) with coalescing of free neighbours.
+class Arena {
+   public:
+    explicit Arena(size_t cap = 0) : cap_(cap) {
+        if (cap) free_[0] = cap;
+    }
+    bool alloc(size_t bytes, size_t* off) {
+        bytes = align256(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                size_t rest = it->second - bytes, at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                used_ += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = align256(bytes);
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto next = std::next(it);
+        if (next != free_.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_.erase(next);
+        }
+        if (it != free_.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t used() const { return used_; }
+    size_t capacity() const { return cap_; }
+
+   private:
+    size_t cap_ = 0, used_ = 0;
+    std::map<size_t, size_t> free_;  // offset -> size
+};
+
+struct Layout {
+    size_t q0, q1, qs, w0, w1, g, total;
+};
+
+Layout layout_of(const fd_request& r) {
+    const size_t n = (size_t)r.nx * r.ny * r.nz;
+    const size_t t = r.dtype == FD_F64 ? sizeof(double) : sizeof(float);
+    const size_t wf = r.dtype == FD_F64 ? 5 : 10;
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t at = off;
+        off += align256(b);
+        return at;
+    };
+    L.q0 = take(5 * n * sizeof(double));
+    L.q1 = take(5 * n * sizeof(double));
+    L.qs = take(5 * n * sizeof(double));
+    L.w0 = take(wf * n * t);
+    L.w1 = take(wf * n * t);
+    L.g = r.algorithm == FD_STORE_SOME ? take(9 * n * t) : (size_t)-1;
+    L.total = off;
+    return L;
+}
+
+const char* check_request(const fd_request* r) {
+    if (!r) return "request is NULL";
+    if (const char* why = fd::check_instance(r->nx, r->ny, r->nz, r->Re, r->Mach, r->Pr, r->gamma, r->dt)) return why;
+    if (r->steps < 1) return "steps must be >= 1";
+    if (r->dtype != FD_F64 && r->dtype != FD_F32_ACC64) return "unknown dtype";
+    if (r->algorithm != FD_STORE_SOME && r->algorithm != FD_RECOMPUTE_ALL) return "algorithm must be SS or RA";
+    if (r->tile_points != 0 && r->tile_points < 32) return "tile_points must be 0 or >= 32";
+    return nullptr;
+}
+
+struct Active {
+    fd_request r;
+    Layout L;
+    size_t off;  // arena offset of the block
+    int n;
+    int done = 0;
+    bool fresh = true;  // initial state written this tick, primitives pending
+    bool cancelled = false;
+    int slot = -1;      // index in its dtype's instance table
+};
+
+}  // namespace
+
+struct fd_server {
+    cudaStream_t stream = nullptr;
+    fd_alloc alloc{};
+    bool has_alloc = false;
+    int device = 0, max_active = 0, sms = 152;
+    void* arena_ptr = nullptr;
+    Arena arena;
+    // small fixed buffers: diagnostics partial sums and per-slot results
+    void* fixed = nullptr;
+    size_t fixed_bytes = 0;
+    double* partial = nullptr;
+    double* results = nullptr;  // 2 * max_active
+    // growable buffers for tables and tiles
+    void* tab = nullptr;
+    size_t tab_bytes = 0;
+    std::deque<fd_request> queue;
+    std::vector<Active> active;
+    std::vector<fd_result> done;
+    bool dirty = true;
+    int parity = 0;
+    long long submitted = 0, completed = 0, ticks = 0;
+    // current device views (valid after a rebuild)
+    void* inst[2] = {nullptr, nullptr};  // [0] double table, [1] float table
+    fd::BatchTile* tiles[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [dtype][family: 0 SS, 1 RA]
+    int ntiles[2][2] = {{0, 0}, {0, 0}};
+    fd::BatchTile* fresh_tiles[2] = {nullptr, nullptr};
+    int nfresh[2] = {0, 0};
+    std::string err;
+
+    int fail(int code, const char* fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        err = buf;
+        return code;
+    }
+    int cuda_fail(cudaError_t e, const char* what) { return fail(FD_ECUDA, "%s: %s", what, cudaGetErrorString(e)); }
+    char* base() const { return static_cast<char*>(arena_ptr); }
+
+    void* dev_alloc(size_t bytes) {
+        if (has_alloc) return alloc.alloc(alloc.ctx, bytes, stream);
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    }
+    void dev_free(void* p, size_t bytes) {
+        if (!p) return;
+        if (has_alloc)
+            alloc.free(alloc.ctx, p, bytes, stream);
+        else
+            cudaFree(p);
+    }
+};
+
+namespace {
+
+template <class T>
+fd::BatchInst<T> record(const fd_server* s, const Active& a) {
+    fd::BatchInst<T> I;
+    std::memset(&I, 0, sizeof I);
+    I.g = fd::make_grid(a.r.nx, a.r.ny, a.r.nz);
+    I.ph = fd::make_phys(a.r.Re, a.r.Mach, a.r.Pr, a.r.gamma);
+    I.k = fd::make_coef<T>(I.g, I.ph, sizeof(T) == sizeof(float));
+    char* b = s->base() + a.off;
+    I.Q[0] = reinterpret_cast<double*>(b + a.L.q0);
+    I.Q[1] = reinterpret_cast<double*>(b + a.L.q1);
+    I.Qs = reinterpret_cast<double*>(b + a.L.qs);
+    I.W[0] = reinterpret_cast<T*>(b + a.L.w0);
+    I.W[1] = reinterpret_cast<T*>(b + a.L.w1);
+    I.G = a.L.g == (size_t)-1 ? nullptr : reinterpret_cast<T*>(b + a.L.g);
+    for (int st = 0; st < 3; ++st) {
+        I.adt[st] = fd::kRkA[st] * a.r.dt;
+        I.bdt[st] = fd::kRkB[st] * a.r.dt;
+    }
+    return I;
+}
+
+void append_tiles(const Active& a, std::vector<fd::BatchTile>& v) {
+    int tp = a.r.tile_points > 0 ? a.r.tile_points : kDefaultTile;
+    for (int st = 0; st < a.n; st += tp) v.push_back({a.slot, st, std::min(tp, a.n - st)});
+}
+
+// Rebuild the instance tables and tile lists of the active set and upload
+// them (stream-ordered after every earlier launch that reads them).
+cudaError_t rebuild(fd_server* s) {
+    std::vector<fd::BatchInst<double>> I64;
+    std::vector<fd::BatchInst<float>> I32;
+    std::vector<fd::BatchTile> t[2][2], f[2];
+    for (auto& a : s->active) {
+        const int d = a.r.dtype == FD_F64 ? 0 : 1;
+        if (d == 0) {
+            a.slot = (int)I64.size();
+            I64.push_back(record<double>(s, a));
+        } else {
+            a.slot = (int)I32.size();
+            I32.push_back(record<float>(s, a));
+        }
+        append_tiles(a, t[d][a.r.algorithm == FD_STORE_SOME ? 0 : 1]);
+        if (a.fresh) append_tiles(a, f[d]);
+    }
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t at = off;
+        off += align256(std::max<size_t>(b, 1));
+        return at;
+    };
+    size_t o64 = take(I64.size() * sizeof(fd::BatchInst<double>));
+    size_t o32 = take(I32.size() * sizeof(fd::BatchInst<float>));
+    size_t ot[2][2], of[2];
+    for (int d = 0; d < 2; ++d) {
+        for (int k = 0; k < 2; ++k) ot[d][k] = take(t[d][k].size() * sizeof(fd::BatchTile));
+        of[d] = take(f[d].size() * sizeof(fd::BatchTile));
+    }
+    cudaError_t e;
+    if (off > s->tab_bytes) {
+        if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return e;
+        s->dev_free(s->tab, s->tab_bytes);
+        size_t nb = std::max(off, 2 * s->tab_bytes);
+        s->tab = s->dev_alloc(nb);
+        s->tab_bytes = s->tab ? nb : 0;
+        if (!s->tab) return cudaErrorMemoryAllocation;
+    }
+    char* b = static_cast<char*>(s->tab);
+    auto up = [&](size_t at, const void* src, size_t bytes) {
+        if (!bytes) return cudaSuccess;
+        return cudaMemcpyAsync(b + at, src, bytes, cudaMemcpyHostToDevice, s->stream);
+    };
+    if ((e = up(o64, I64.data(), I64.size() * sizeof I64[0])) != cudaSuccess) return e;
+    if ((e = up(o32, I32.data(), I32.size() * sizeof I32[0])) != cudaSuccess) return e;
+    s->inst[0] = b + o64;
+    s->inst[1] = b + o32;
+    for (int d = 0; d < 2; ++d) {
+        for (int k = 0; k < 2; ++k) {
+            if ((e = up(ot[d][k], t[d][k].data(), t[d][k].size() * sizeof(fd::BatchTile))) != cudaSuccess) return e;
+            s->tiles[d][k] = reinterpret_cast<fd::BatchTile*>(b + ot[d][k]);
+            s->ntiles[d][k] = (int)t[d][k].size();
+        }
+        if ((e = up(of[d], f[d].data(), f[d].size() * sizeof(fd::BatchTile))) != cudaSuccess) return e;
+        s->fresh_tiles[d] = reinterpret_cast<fd::BatchTile*>(b + of[d]);
+        s->nfresh[d] = (int)f[d].size();
+    }
+    // Host vectors are pageable: the copies above have consumed them on return.
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t run_group(fd_server* s, int d) {
+    auto* I = static_cast<const fd::BatchInst<T>*>(s->inst[d]);
+    cudaError_t e;
+    const int gg = s->sms * fd::batch_blocks_per_sm<T>(false, false);
+    if (s->nfresh[d]) {
+        if ((e = fd::launch_batch_prims<T>(I, s->fresh_tiles[d], s->nfresh[d], s->parity, gg, s->stream)) !=
+            cudaSuccess)
+            return e;
+    }
+    const int gs = s->sms * fd::batch_blocks_per_sm<T>(true, true);
+    const int gr = s->sms * fd::batch_blocks_per_sm<T>(true, false);
+    for (int st = 0, p = s->parity; st < 3; ++st, p ^= 1) {
+        if (s->ntiles[d][0]) {
+            if ((e = fd::launch_batch_grad<T>(I, s->tiles[d][0], s->ntiles[d][0], p, gg, s->stream)) != cudaSuccess)
+                return e;
+            if ((e = fd::launch_batch_fused<T>(I, s->tiles[d][0], s->ntiles[d][0], true, st, p, gs, s->stream)) !=
+                cudaSuccess)
+                return e;
+        }
+        if (s->ntiles[d][1]) {
+            if ((e = fd::launch_batch_fused<T>(I, s->tiles[d][1], s->ntiles[d][1], false, st, p, gr, s->stream)) !=
+                cudaSuccess)
+                return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+void release_all(fd_server* s) {
+    if (s->stream || s->arena_ptr) cudaStreamSynchronize(s->stream);
+    s->dev_free(s->tab, s->tab_bytes);
+    s->dev_free(s->fixed, s->fixed_bytes);
+    s->dev_free(s->arena_ptr, s->arena.capacity());
+    s->tab = s->fixed = s->arena_ptr = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t fd_server_footprint(const fd_request* req) { return check_request(req) ? 0 : layout_of(*req).total; }
+
+int fd_server_create(fd_server** out, size_t arena_bytes, int max_active, const fd_alloc* alloc, void* cuda_stream) {
+    if (!out) return fail_global(FD_EINVAL, "fd_server_create: out is NULL");
+    *out = nullptr;
+    if (arena_bytes < kAlign || max_active < 1)
+        return fail_global(FD_EINVAL, "fd_server_create: need arena_bytes >= 256 and max_active >= 1");
+    if (alloc && (!alloc->alloc || !alloc->free))
+        return fail_global(FD_EINVAL, "fd_server_create: allocator needs both alloc and free");
+    fd_server* s = new (std::nothrow) fd_server();
+    if (!s) return fail_global(FD_ENOMEM, "fd_server_create: host allocation failed");
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+    s->max_active = max_active;
+    if (alloc) {
+        s->alloc = *alloc;
+        s->has_alloc = true;
+    }
+    cudaGetDevice(&s->device);
+    cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (s->sms <= 0) s->sms = 152;
+    arena_bytes = arena_bytes & ~(kAlign - 1);
+    s->arena_ptr = s->dev_alloc(arena_bytes);
+    if (!s->arena_ptr) {
+        delete s;
+        return fail_global(FD_ENOMEM, "fd_server_create: arena of %zu bytes could not be allocated", arena_bytes);
+    }
+    s->arena = Arena(arena_bytes);
+    s->fixed_bytes = align256(2 * fd::kDiagBlocks * sizeof(double)) + align256(2 * (size_t)max_active * sizeof(double));
+    s->fixed = s->dev_alloc(s->fixed_bytes);
+    if (!s->fixed) {
+        release_all(s);
+        delete s;
+        return fail_global(FD_ENOMEM, "fd_server_create: diagnostics buffers could not be allocated");
+    }
+    s->partial = static_cast<double*>(s->fixed);
+    s->results = reinterpret_cast<double*>(static_cast<char*>(s->fixed) + align256(2 * fd::kDiagBlocks * sizeof(double)));
+    *out = s;
+    return FD_OK;
+}
+
+int fd_server_submit(fd_server* s, const fd_request* req) {
+    if (!s) return fail_global(FD_EINVAL, "fd_server_submit: NULL server");
+    if (const char* why = check_request(req)) return s->fail(FD_EINVAL, "fd_server_submit: %s", why);
+    size_t need = layout_of(*req).total;
+    if (need > s->arena.capacity())
+        return s->fail(FD_EBUSY, "fd_server_submit: footprint %zu bytes exceeds the arena (%zu)", need,
+                       s->arena.capacity());
+    s->queue.push_back(*req);
+    s->submitted++;
+    return FD_OK;
+}
+
+int fd_server_cancel(fd_server* s, long long tag) {
+    if (!s) return fail_global(FD_EINVAL, "fd_server_cancel: NULL server");
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+        if (it->tag == tag) {
+            s->done.push_back({tag, FD_EBUSY, 0, 0.0, 0.0});
+            s->queue.erase(it);
+            return FD_OK;
+        }
+    for (auto& a : s->active)
+        if (a.r.tag == tag && !a.cancelled) {
+            a.cancelled = true;
+            return FD_OK;
+        }
+    return s->fail(FD_EINVAL, "fd_server_cancel: no pending request with tag %lld", tag);
+}
+
+int fd_server_tick(fd_server* s, int* active_out) {
+    if (!s) return fail_global(FD_EINVAL, "fd_server_tick: NULL server");
+    s->ticks++;
+    cudaError_t e = cudaSuccess;
+    // 1. cancelled active solves leave without diagnostics
+    for (size_t i = 0; i < s->active.size();) {
+        Active& a = s->active[i];
+        if (a.cancelled) {
+            s->done.push_back({a.r.tag, FD_EBUSY, a.done, 0.0, 0.0});
+            s->arena.release(a.off, a.L.total);
+            s->active.erase(s->active.begin() + i);
+            s->dirty = true;
+        } else {
+            ++i;
+        }
+    }
+    // 2. admission: first fit in submission order
+    for (auto it = s->queue.begin(); it != s->queue.end() && (int)s->active.size() < s->max_active;) {
+        Layout L = layout_of(*it);
+        size_t off = 0;
+        if (!s->arena.alloc(L.total, &off)) {
+            ++it;
+            continue;
+        }
+        Active a;
+        a.r = *it;
+        a.L = L;
+        a.off = off;
+        a.n = it->nx * it->ny * it->nz;
+        fd::Grid g = fd::make_grid(a.r.nx, a.r.ny, a.r.nz);
+        fd::Phys ph = fd::make_phys(a.r.Re, a.r.Mach, a.r.Pr, a.r.gamma);
+        double* Q = reinterpret_cast<double*>(s->base() + off + (s->parity ? L.q1 : L.q0));
+        e = fd::launch_tgv_ic(g, ph, 2.0 * fd::kPi / a.r.nx, 2.0 * fd::kPi / a.r.ny, 2.0 * fd::kPi / a.r.nz, Q,
+                              s->stream);
+        if (e != cudaSuccess) {
+            s->arena.release(off, L.total);
+            return s->cuda_fail(e, "fd_server_tick: initial condition");
+        }
+        s->active.push_back(a);
+        it = s->queue.erase(it);
+        s->dirty = true;
+    }
+    if (active_out) *active_out = (int)s->active.size();
+    if (s->active.empty()) return FD_OK;
+    // 3. tables, then one RK3 step of every active solve
+    bool any_fresh = false;
+    for (auto& a : s->active) any_fresh |= a.fresh;
+    if (s->dirty || any_fresh) {
+        if ((e = rebuild(s)) != cudaSuccess) return s->cuda_fail(e, "fd_server_tick: tables");
+        s->dirty = false;
+    }
+    if ((e = run_group<double>(s, 0)) != cudaSuccess) return s->cuda_fail(e, "fd_server_tick: binary64 group");
+    if ((e = run_group<float>(s, 1)) != cudaSuccess) return s->cuda_fail(e, "fd_server_tick: binary32 group");
+    s->parity ^= 1;
+    s->nfresh[0] = s->nfresh[1] = 0;
+    for (auto& a : s->active) {
+        a.fresh = false;
+        a.done++;
+    }
+    // 4. diagnostics of finished solves (scratch: the working fields the next
+    //    stage would overwrite), then synchronise and retire them
+    std::vector<int> fin;
+    for (int i = 0; i < (int)s->active.size(); ++i)
+        if (s->active[i].done >= s->active[i].r.steps) fin.push_back(i);
+    for (size_t k = 0; k < fin.size() && e == cudaSuccess; ++k) {
+        const Active& a = s->active[fin[k]];
+        fd::Grid g = fd::make_grid(a.r.nx, a.r.ny, a.r.nz);
+        char* b = s->base() + a.off;
+        const double* Q = reinterpret_cast<const double*>(b + (s->parity ? a.L.q1 : a.L.q0));
+        double* Wv = reinterpret_cast<double*>(b + (s->parity ? a.L.w0 : a.L.w1));
+        e = fd::launch_diagnostics_f64(g, Q, Wv, s->partial, s->results + 2 * k, s->stream);
+    }
+    std::vector<double> res(2 * fin.size());
+    if (e == cudaSuccess && !fin.empty())
+        e = cudaMemcpyAsync(res.data(), s->results, res.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "fd_server_tick");
+    for (size_t k = fin.size(); k-- > 0;) {
+        Active& a = s->active[fin[k]];
+        double ke = res[2 * k], en = res[2 * k + 1];
+        int st = std::isfinite(ke) && std::isfinite(en) ? FD_OK : FD_EUNSTABLE;
+        s->done.push_back({a.r.tag, st, a.done, ke, en});
+        s->arena.release(a.off, a.L.total);
+        s->active.erase(s->active.begin() + fin[k]);
+        s->completed++;
+        s->dirty = true;
+    }
+    return FD_OK;
+}
+
+int fd_server_poll(fd_server* s, fd_result* out, int max, int* n_out) {
+    if (!s) return fail_global(FD_EINVAL, "fd_server_poll: NULL server");
+    if (max < 0 || (max > 0 && !out)) return s->fail(FD_EINVAL, "fd_server_poll: bad output buffer");
+    int n = std::min<int>(max, (int)s->done.size());
+    for (int i = 0; i < n; ++i) out[i] = s->done[i];
+    s->done.erase(s->done.begin(), s->done.begin() + n);
+    if (n_out) *n_out = n;
+    return FD_OK;
+}
+
+int fd_server_get_stats(const fd_server* s, fd_server_stats* out) {
+    if (!s || !out) return fail_global(FD_EINVAL, "fd_server_get_stats: NULL argument");
+    out->queued = (int)s->queue.size();
+    out->active = (int)s->active.size();
+    out->submitted = s->submitted;
+    out->completed = s->completed;
+    out->ticks = s->ticks;
+    out->arena_bytes = s->arena.capacity();
+    out->arena_used = s->arena.used();
+    return FD_OK;
+}
+
+int fd_server_destroy(fd_server* s) {
+    if (!s) return FD_OK;
+    release_all(s);
+    delete s;
+    return FD_OK;
+}
+
+const char* fd_server_last_error(const fd_server* s) { return s ? s->err.c_str() : g_server_err.c_str(); }
+
+}  // extern "C"

@@ -49,6 +49,36 @@ class FdAlloc(ctypes.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
 
 
+class FdInstanceDesc(ctypes.Structure):
+    """``fd_instance_desc``: one instance of a batch."""
+
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("Re", ctypes.c_double), ("Mach", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("dt", ctypes.c_double),
+                ("algorithm", ctypes.c_int), ("tile_points", ctypes.c_int)]
+
+
+class FdRequest(ctypes.Structure):
+    """``fd_request``: one solve submitted to a server."""
+
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("Re", ctypes.c_double), ("Mach", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("dt", ctypes.c_double), ("steps", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("algorithm", ctypes.c_int), ("tile_points", ctypes.c_int),
+                ("tag", ctypes.c_longlong)]
+
+
+class FdResult(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_longlong), ("status", ctypes.c_int), ("steps_done", ctypes.c_int),
+                ("ke", ctypes.c_double), ("enstrophy", ctypes.c_double)]
+
+
+class FdServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int), ("active", ctypes.c_int), ("submitted", ctypes.c_longlong),
+                ("completed", ctypes.c_longlong), ("ticks", ctypes.c_longlong),
+                ("arena_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t)]
+
+
 class FdError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"[{code}] {msg}")
@@ -77,6 +107,28 @@ _SIGS = {
                                             ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp]),
     "fd_destroy": (ctypes.c_int, [_vp]),
     "fd_last_error": (ctypes.c_char_p, [_vp]),
+    "fd_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(FdInstanceDesc), ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(FdAlloc), _vp]),
+    "fd_batch_step": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "fd_batch_get_state": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int]),
+    "fd_batch_set_state": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int]),
+    "fd_batch_diagnostics": (ctypes.c_int, [_vp, _dp, _dp]),
+    "fd_batch_count": (ctypes.c_int, [_vp]),
+    "fd_batch_device_bytes": (ctypes.c_size_t, [_vp]),
+    "fd_batch_profile": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "fd_batch_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "fd_batch_destroy": (ctypes.c_int, [_vp]),
+    "fd_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "fd_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_int,
+                                        ctypes.POINTER(FdAlloc), _vp]),
+    "fd_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(FdRequest)]),
+    "fd_server_footprint": (ctypes.c_size_t, [ctypes.POINTER(FdRequest)]),
+    "fd_server_cancel": (ctypes.c_int, [_vp, ctypes.c_longlong]),
+    "fd_server_tick": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "fd_server_poll": (ctypes.c_int, [_vp, ctypes.POINTER(FdResult), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "fd_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(FdServerStats)]),
+    "fd_server_destroy": (ctypes.c_int, [_vp]),
+    "fd_server_last_error": (ctypes.c_char_p, [_vp]),
 }
 
 
@@ -194,3 +246,128 @@ def fd_destroy(h):
 
 def fd_last_error(h=None):
     return load().fd_last_error(h).decode()
+
+
+# ---- batched instances -------------------------------------------------------
+
+
+def _bcheck(rc: int, b=None):
+    if rc != FD_OK:
+        raise FdError(rc, load().fd_batch_last_error(b).decode())
+    return rc
+
+
+def fd_batch_create(descs, dtype, alloc=None, stream=0):
+    """descs: sequence of FdInstanceDesc (or tuples in its field order).  Returns the batch handle."""
+    arr = (FdInstanceDesc * len(descs))(*[d if isinstance(d, FdInstanceDesc) else FdInstanceDesc(*d)
+                                         for d in descs])
+    b = _vp()
+    ap = ctypes.byref(alloc) if alloc is not None else None
+    _bcheck(load().fd_batch_create(ctypes.byref(b), arr, len(descs), dtype, ap, _vp(stream or None)), None)
+    return b.value
+
+
+def fd_batch_step(b, n):
+    return _bcheck(load().fd_batch_step(b, n), b)
+
+
+def fd_batch_get_state(b, i, dst, n_elems=None, dst_is_device=None):
+    if isinstance(dst, np.ndarray):
+        return _bcheck(load().fd_batch_get_state(b, i, _hostptr(dst), dst.size, 0), b)
+    return _bcheck(load().fd_batch_get_state(b, i, dst, n_elems, 1 if dst_is_device is None else dst_is_device), b)
+
+
+def fd_batch_set_state(b, i, src, n_elems=None, src_is_device=None):
+    if isinstance(src, np.ndarray):
+        return _bcheck(load().fd_batch_set_state(b, i, _hostptr(src), src.size, 0), b)
+    return _bcheck(load().fd_batch_set_state(b, i, src, n_elems, 1 if src_is_device is None else src_is_device), b)
+
+
+def fd_batch_diagnostics(b):
+    n = load().fd_batch_count(b)
+    ke = np.empty(n)
+    en = np.empty(n)
+    _bcheck(load().fd_batch_diagnostics(b, ke.ctypes.data_as(_dp), en.ctypes.data_as(_dp)), b)
+    return ke, en
+
+
+def fd_batch_count(b):
+    return load().fd_batch_count(b)
+
+
+def fd_batch_device_bytes(b):
+    return load().fd_batch_device_bytes(b)
+
+
+def fd_batch_profile(b, enable):
+    return _bcheck(load().fd_batch_profile(b, 1 if enable else 0), b)
+
+
+def fd_batch_profile_read(b, kernel_class):
+    ms = ctypes.c_double()
+    cnt = ctypes.c_longlong()
+    _bcheck(load().fd_batch_profile_read(b, kernel_class, ctypes.byref(ms), ctypes.byref(cnt)), b)
+    return ms.value, cnt.value
+
+
+def fd_batch_destroy(b):
+    return _bcheck(load().fd_batch_destroy(b), None)
+
+
+def fd_batch_last_error(b=None):
+    return load().fd_batch_last_error(b).decode()
+
+
+# ---- continuous-batching server ---------------------------------------------
+
+
+def _scheck(rc: int, srv=None):
+    if rc != FD_OK:
+        raise FdError(rc, load().fd_server_last_error(srv).decode())
+    return rc
+
+
+def fd_server_create(arena_bytes, max_active, alloc=None, stream=0):
+    srv = _vp()
+    ap = ctypes.byref(alloc) if alloc is not None else None
+    _scheck(load().fd_server_create(ctypes.byref(srv), arena_bytes, max_active, ap, _vp(stream or None)), None)
+    return srv.value
+
+
+def fd_server_submit(srv, req: FdRequest):
+    return _scheck(load().fd_server_submit(srv, ctypes.byref(req)), srv)
+
+
+def fd_server_footprint(req: FdRequest):
+    return load().fd_server_footprint(ctypes.byref(req))
+
+
+def fd_server_cancel(srv, tag):
+    return _scheck(load().fd_server_cancel(srv, tag), srv)
+
+
+def fd_server_tick(srv):
+    n = ctypes.c_int()
+    _scheck(load().fd_server_tick(srv, ctypes.byref(n)), srv)
+    return n.value
+
+
+def fd_server_poll(srv, max_results=1024):
+    buf = (FdResult * max_results)()
+    n = ctypes.c_int()
+    _scheck(load().fd_server_poll(srv, buf, max_results, ctypes.byref(n)), srv)
+    return [buf[i] for i in range(n.value)]
+
+
+def fd_server_get_stats(srv):
+    st = FdServerStats()
+    _scheck(load().fd_server_get_stats(srv, ctypes.byref(st)), srv)
+    return st
+
+
+def fd_server_destroy(srv):
+    return _scheck(load().fd_server_destroy(srv), None)
+
+
+def fd_server_last_error(srv=None):
+    return load().fd_server_last_error(srv).decode()

@@ -1,0 +1,97 @@
+"""Continuous-batching server: admission by footprint, results equal each solve alone.
+
+Requests that arrive while others are active join the running batch (same
+launches), so a solve's result must not depend on its neighbours: the server's
+kinetic energy and enstrophy of every solve equal, bit for bit, those of the same
+solve run alone through fd_create / fd_step / fd_diagnostics.
+"""
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1610_09146_gb300 as fd  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    fd.build()
+
+
+REQS = [
+    dict(tag=1, n=16, steps=7, Re=1600.0, Mach=0.1, dtype="f32", algorithm="recompute_all", dt=1e-3),
+    dict(tag=2, n=(20, 18, 24), steps=3, Re=500.0, Mach=0.3, dtype="f64", algorithm="store_some", dt=2e-3),
+    dict(tag=3, n=24, steps=5, Re=2000.0, Mach=0.2, dtype="f32", algorithm="store_some", tile_points=128, dt=1e-3),
+    dict(tag=4, n=12, steps=9, Re=900.0, Mach=0.35, dtype="f64", algorithm="recompute_all", dt=1e-3),
+    dict(tag=5, n=16, steps=4, Re=3000.0, Mach=0.15, dtype="f32", algorithm="recompute_all", dt=1e-3),
+]
+
+
+def alone(r):
+    with fd.Solver(r["n"], Re=r["Re"], Mach=r["Mach"], dt=r["dt"], algorithm=r["algorithm"], dtype=r["dtype"]) as s:
+        s.step(r["steps"])
+        return s.diagnostics()
+
+
+def test_results_in_the_mix_equal_alone():
+    got = {}
+    with fd.Server(1 << 30, max_active=8) as srv:
+        srv.submit(REQS[0])
+        srv.submit(REQS[1])
+        srv.tick()
+        srv.submit(REQS[2])      # joins while 1 and 2 are active
+        srv.tick()
+        srv.tick()
+        srv.submit(REQS[3])
+        srv.submit(REQS[4])
+        for _ in range(40):
+            srv.tick()
+            for r in srv.poll():
+                got[r["tag"]] = r
+            if len(got) == len(REQS):
+                break
+    assert set(got) == {r["tag"] for r in REQS}
+    for r in REQS:
+        ke, en = alone(r)
+        assert got[r["tag"]]["status"] == fd.FD_OK
+        assert got[r["tag"]]["steps"] == r["steps"]
+        assert got[r["tag"]]["ke"] == ke and got[r["tag"]]["enstrophy"] == en, r["tag"]
+
+
+def test_admission_respects_the_arena():
+    big = dict(tag=10, n=32, steps=2, dtype="f64", algorithm="store_some", dt=1e-3)
+    with fd.Server(1 << 30, max_active=4) as probe:
+        need = probe.footprint(big)
+    # an arena for exactly one such solve: the second waits until the first retires
+    with fd.Server(need + 4096, max_active=4) as srv:
+        srv.submit(big)
+        srv.submit(dict(big, tag=11))
+        assert srv.tick() == 1
+        assert srv.stats()["queued"] == 1
+        srv.tick()                      # tag 10 finishes (2 steps) and frees its block
+        done = [r["tag"] for r in srv.poll()]
+        assert done == [10]
+        assert srv.tick() == 1          # tag 11 admitted now
+        srv.tick()
+        assert [r["tag"] for r in srv.poll()] == [11]
+        assert srv.stats()["arena_used"] == 0
+
+
+def test_too_large_request_is_refused_and_cancel_works():
+    with fd.Server(1 << 20, max_active=4) as srv:
+        with pytest.raises(fd.FdError) as e:
+            srv.submit(dict(tag=1, n=64, steps=1, dtype="f64"))
+        assert e.value.code == fd.FD_EBUSY
+        srv.submit(dict(tag=2, n=8, steps=50, dtype="f32"))
+        srv.submit(dict(tag=3, n=8, steps=1, dtype="f32"))
+        srv.cancel(3)
+        srv.tick()
+        srv.cancel(2)
+        srv.tick()
+        res = {r["tag"]: r for r in srv.poll()}
+        assert res[3]["status"] == fd.FD_EBUSY and res[3]["steps"] == 0
+        assert res[2]["status"] == fd.FD_EBUSY and res[2]["steps"] == 1
+        with pytest.raises(fd.FdError):
+            srv.cancel(99)
