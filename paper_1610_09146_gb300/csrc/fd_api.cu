@@ -193,7 +193,12 @@ cudaError_t stage_kernels(fd_handle* h, const fd::RKStage& rk, bool resid, const
     cudaError_t e;
     switch (h->algorithm) {
         case FD_RECOMPUTE_ALL:
+            // binary32: fields staged through shared memory (the global-memory
+            // kernel is latency-bound on its tap loads); binary64 is bound by FP64
+            // issue, where staging does not help.
             return timed(h, FD_KERNEL_FUSED, [&] {
+                if (sizeof(T) == sizeof(float))
+                    return fd::launch_ra_tiled<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, h->Qs, Wnext, st);
                 return fd::launch_ra<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, h->Qs, Wnext, st);
             });
         case FD_STORE_SOME:

@@ -31,6 +31,11 @@ cudaError_t launch_prims_f32(const Grid& g, const Phys& ph, const double* Q, flo
 template <class T>
 cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid, const T* Qf,
                       const T* Wf, const double* Q64, double* out, double* Qs, T* Wnext, cudaStream_t st);
+// RA with the fields staged through shared memory (same arithmetic as launch_ra).
+template <class T>
+cudaError_t launch_ra_tiled(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid,
+                            const T* Qf, const T* Wf, const double* Q64, double* out, double* Qs, T* Wnext,
+                            cudaStream_t st);
 template <class T>
 cudaError_t launch_ss_grad(const Grid& g, const Coef<T>& k, const T* Wf, T* Gw, cudaStream_t st);
 template <class T>

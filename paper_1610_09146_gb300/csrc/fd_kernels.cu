@@ -151,6 +151,23 @@ __global__ void __launch_bounds__(256) k_prims(Grid g, Phys ph, const double* __
     prims_point(ph, q, W, n, idx);
 }
 
+// RK update from a preloaded saved register qs (Q_in at stage 0, else Qs):
+// the same arithmetic as the update branch of stage_write below.
+template <class T>
+__device__ __forceinline__ void stage_update(const RKStage& rk, const Phys& ph, int n, int c, const double qs[5],
+                                             const T R[5], double* __restrict__ out, double* __restrict__ Qs,
+                                             T* __restrict__ Wnext) {
+    double qn[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+        const double r = (double)R[f];
+        qn[f] = fmx(rk.adt, r, qs[f]);
+        out[f * n + c] = qn[f];
+        if (rk.stage < 2) Qs[f * n + c] = fmx(rk.bdt, r, qs[f]);
+    }
+    prims_point(ph, qn, Wnext, n, c);
+}
+
 // Final write of a stage: the residual itself (fd_residual), or the
 // two-register RK update (Fig. 1, advance-solution-in-time) in binary64,
 //   Q_out = Qs + a dt R,  Qs <- Qs + b dt R,  with Qs = Q_in at stage 0 (save-state),
@@ -184,6 +201,43 @@ __device__ __forceinline__ void taps(const T* __restrict__ f, int c, const int* 
     for (int a = 0; a < 4; ++a) t[a] = ld(f, c + o[a]);
 }
 
+// Where the fused residual reads its fields.  Field index f: 0..4 the
+// conserved-like working fields Qf, 5..9 the primitive-like fields Wf (u, v,
+// w, p, T).  Taps are ordered -2, -1, +1, +2 along an axis (0 = x, 1 = y,
+// 2 = z).  The global accessor reads through the read-only cache with the
+// periodic neighbour offsets; the shared-memory accessor (tiled kernel) reads a
+// staged ring of planes.  Both feed the same arithmetic below.
+template <class T>
+struct GlobalAcc {
+    const Nbr& s;
+    int n;
+    const T* __restrict__ Qf;
+    const T* __restrict__ Wf;
+    const T* __restrict__ Gw;
+    __device__ __forceinline__ const T* field(int f) const { return f < 5 ? Qf + f * n : Wf + (f - 5) * n; }
+    __device__ __forceinline__ T center(int f) const { return ld(field(f), s.c); }
+    __device__ __forceinline__ void taps(int f, int j, T t[4]) const {
+        const T* p = field(f);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) t[a] = ld(p, s.c + s.o[j][a]);
+    }
+    // taps along j around the point shifted by tap a along axis i
+    __device__ __forceinline__ void taps_shifted(int f, int j, int i, int a, T t[4]) const {
+        const T* p = field(f);
+        const int c = s.c + s.o[i][a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) t[b] = ld(p, c + s.o[j][b]);
+    }
+    __device__ __forceinline__ T grad(int i, int j) const { return ld(Gw + (3 * i + j) * n, s.c); }
+    // taps along i of G_aa + G_bb
+    __device__ __forceinline__ void grad_pair_taps(int ga, int gb, int i, T t[4]) const {
+        const T* pa = Gw + (3 * ga + ga) * n;
+        const T* pb = Gw + (3 * gb + gb) * n;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) t[a] = ld(pa, s.c + s.o[i][a]) + ld(pb, s.c + s.o[i][a]);
+    }
+};
+
 // Residual at one point for the fused families, evaluated into registers
 // (the "thread-local variables" of Section 2, paragraphs SN / SS):
 //   R_f = -1/2 sum_j [ D_j(Q_f u_j) + u_j D_j Q_f ] - 1/2 Q_f div u         (Eq. skewscalar)
@@ -195,50 +249,46 @@ __device__ __forceinline__ void taps(const T* __restrict__ f, int c, const int* 
 // to D_j(Q_f u_j) + u_j D_j Q_f by linearity of the stencil.  STORED_G: SS
 // reads G from the nine gradient arrays and differences G_jj + G_kk for the
 // mixed derivatives; otherwise (RA) G and D_i(D_k u_k) come from u taps.
-template <class T, bool STORED_G>
-__device__ __forceinline__ void fused_residual(const Nbr& s, int n, const T* __restrict__ Qf,
-                                               const T* __restrict__ Wf, const T* __restrict__ Gw,
-                                               const Coef<T>& k, T R[5]) {
-    const int c = s.c;
-    const T* __restrict__ pf = Wf + 3 * n;
-    const T* __restrict__ Tf = Wf + 4 * n;
+template <class T, bool STORED_G, class Acc>
+__device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T R[5]) {
+    constexpr int U = 5, P = 8, TT = 9;  // field indices of u_0, p, T
     T uc[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) uc[i] = ld(Wf + i * n, c);
+    for (int i = 0; i < 3; ++i) uc[i] = A.center(U + i);
 
     T G[3][3];
-    if (STORED_G) {
+    if constexpr (STORED_G) {
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) G[i][j] = ld(Gw + (3 * i + j) * n, c);
+            for (int j = 0; j < 3; ++j) G[i][j] = A.grad(i, j);
     } else {
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 T t[4];
-                taps(Wf + i * n, c, s.o[j], t);
+                A.taps(U + i, j, t);
                 G[i][j] = k.s1[j] * delta1_taps(t);
             }
     }
     const T div = G[0][0] + G[1][1] + G[2][2];
     const T hd = T(-0.5) * div;
 #pragma unroll
-    for (int f = 0; f < 5; ++f) R[f] = ld(Qf + f * n, c) * hd;
+    for (int f = 0; f < 5; ++f) R[f] = A.center(f) * hd;
 
     // convective sums, pressure gradient and pressure work, direction by direction
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         T ut[4], st[4], pt[4];
-        taps(Wf + j * n, c, s.o[j], ut);
-        taps(pf, c, s.o[j], pt);
+        A.taps(U + j, j, ut);
+        A.taps(P, j, pt);
 #pragma unroll
         for (int a = 0; a < 4; ++a) st[a] = ut[a] + uc[j];
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
             T qt[4];
-            taps(Qf + f * n, c, s.o[j], qt);
+            A.taps(f, j, qt);
             R[f] = fmx(k.c1[j], delta1_prod(qt, st), R[f]);
         }
         R[1 + j] = fmx(k.cp[j], delta1_taps(pt), R[1 + j]);
@@ -247,11 +297,11 @@ __device__ __forceinline__ void fused_residual(const Nbr& s, int n, const T* __r
 
     // heat flux
     {
-        const T T0 = ld(Tf, c);
+        const T T0 = A.center(TT);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             T t[4];
-            taps(Tf, c, s.o[j], t);
+            A.taps(TT, j, t);
             R[4] = fmx(k.ks2[j], delta2_taps(t, T0), R[4]);
         }
     }
@@ -263,27 +313,23 @@ __device__ __forceinline__ void fused_residual(const Nbr& s, int n, const T* __r
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             T t[4];
-            taps(Wf + i * n, c, s.o[j], t);
+            A.taps(U + i, j, t);
             vi = fmx(k.vs2[i][j], delta2_taps(t, uc[i]), vi);
         }
         const int j1 = i == 0 ? 1 : 0, j2 = i == 2 ? 1 : 2;  // the two axes other than i
-        if (STORED_G) {
-            const T* __restrict__ ga = Gw + (3 * j1 + j1) * n;
-            const T* __restrict__ gb = Gw + (3 * j2 + j2) * n;
+        if constexpr (STORED_G) {
             T t[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) t[a] = ld(ga, c + s.o[i][a]) + ld(gb, c + s.o[i][a]);
+            A.grad_pair_taps(j1, j2, i, t);
             vi = fmx(k.vmix1[i], delta1_taps(t), vi);
         } else {
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int kk = q == 0 ? j1 : j2;
-                const T* __restrict__ uk = Wf + kk * n;
                 T t[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
                     T u4[4];
-                    taps(uk, c + s.o[i][a], s.o[kk], u4);
+                    A.taps_shifted(U + kk, kk, i, a, u4);
                     t[a] = delta1_taps(u4);
                 }
                 vi = fmx(k.vmix[i][kk], delta1_taps(t), vi);
@@ -325,8 +371,111 @@ __global__ void __launch_bounds__(128) k_ra(Grid g, Coef<T> k, Phys ph, RKStage 
     if (idx >= g.n) return;
     const Nbr s = make_nbr(g, idx);
     T R[5];
-    fused_residual<T, false>(s, g.n, Qf, Wf, nullptr, k, R);
+    fused_residual<T, false>(GlobalAcc<T>{s, g.n, Qf, Wf, nullptr}, k, R);
     stage_write<T, RESID>(rk, ph, g.n, s.c, Q64, R, out, Qs, Wnext);
+}
+
+// Recompute-all with shared-memory staging (binary32 mode).  A block of
+// kTX x kTY threads owns that x-y tile and marches a chunk of z-planes; the
+// ten working fields of planes z-2 .. z+2, each with a two-point x-y halo
+// (periodic, by modulo index), sit in a ring of five shared-memory planes.
+// Each step of the march stages one new plane (one coalesced read of every
+// field per point plus the halo) and evaluates the points of plane z from
+// shared memory with the same arithmetic as k_ra.  The saved register the
+// update needs is loaded before the stencil work so its latency overlaps it.
+constexpr int kTX = 32, kTY = 8, kSX = kTX + 4, kSY = kTY + 4, kPlane = kSX * kSY, kRing = 5, kNF = 10;
+constexpr int kZChunk = 64;
+
+template <class T>
+struct SmemAcc {
+    const T* sm;
+    int slot[5];  // ring slots of planes z-2 .. z+2
+    int tx, ty;
+    __device__ __forceinline__ T at(int f, int dz, int dy, int dx) const {
+        return sm[((slot[dz + 2] * kNF + f) * kSY + (ty + 2 + dy)) * kSX + (tx + 2 + dx)];
+    }
+    __device__ __forceinline__ static int d(int a) { return a < 2 ? a - 2 : a - 1; }
+    __device__ __forceinline__ T center(int f) const { return at(f, 0, 0, 0); }
+    __device__ __forceinline__ void taps(int f, int j, T t[4]) const {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            t[a] = j == 0 ? at(f, 0, 0, d(a)) : (j == 1 ? at(f, 0, d(a), 0) : at(f, d(a), 0, 0));
+    }
+    __device__ __forceinline__ void taps_shifted(int f, int j, int i, int a, T t[4]) const {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int o[3] = {0, 0, 0};
+            o[i] += d(a);
+            o[j] += d(b);
+            t[b] = at(f, o[2], o[1], o[0]);
+        }
+    }
+};
+
+template <class T, bool RESID>
+__global__ void __launch_bounds__(kTX* kTY, sizeof(T) == 4 ? 2 : 1)
+    k_ra_tiled(Grid g, Coef<T> k, Phys ph, RKStage rk, const T* __restrict__ Qf, const T* __restrict__ Wf,
+               const double* __restrict__ Q64, double* __restrict__ out, double* __restrict__ Qs,
+               T* __restrict__ Wnext) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int tx = tid % kTX, ty = tid / kTX;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, n = g.n;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const int zbeg = blockIdx.z * kZChunk, zend = min(nz, zbeg + kZChunk);
+    // in-plane offsets of the (at most two) staged cells of this thread
+    int off[2];
+    bool has[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int e = tid + r * kTX * kTY;
+        has[r] = e < kPlane;
+        const int hx = e % kSX, hy = e / kSX;
+        const int gx = ((x0 + hx - 2) % nx + nx) % nx;
+        const int gy = ((y0 + hy - 2) % ny + ny) % ny;
+        off[r] = gy * nx + gx;
+    }
+    auto stage_plane = [&](int z, int slot) {
+        const int zz = ((z % nz) + nz) % nz;
+        const size_t base = (size_t)zz * nx * ny;
+        T* dst = sm + slot * kNF * kPlane;
+#pragma unroll
+        for (int f = 0; f < kNF; ++f) {
+            const T* src = f < 5 ? Qf + (size_t)f * n : Wf + (size_t)(f - 5) * n;
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+                if (has[r]) dst[f * kPlane + tid + r * kTX * kTY] = __ldg(src + base + off[r]);
+        }
+    };
+    for (int dz = -2; dz <= 1; ++dz) stage_plane(zbeg + dz, dz + 2);
+    const int x = x0 + tx, y = y0 + ty;
+    const bool inside = x < nx && y < ny;
+    for (int z = zbeg; z < zend; ++z) {
+        const int r0 = z - zbeg;  // ring slot of plane z + dz is (r0 + dz + 2) % 5
+        const int c = (z * ny + y) * nx + x;
+        double qs[5];
+        if (!RESID && inside) {
+            const double* src = rk.stage == 0 ? Q64 : Qs;
+#pragma unroll
+            for (int f = 0; f < 5; ++f) qs[f] = src[(size_t)f * n + c];
+        }
+        stage_plane(z + 2, (r0 + 4) % kRing);
+        __syncthreads();
+        if (inside) {
+            SmemAcc<T> A{sm, {r0 % kRing, (r0 + 1) % kRing, (r0 + 2) % kRing, (r0 + 3) % kRing, (r0 + 4) % kRing},
+                         tx, ty};
+            T R[5];
+            fused_residual<T, false>(A, k, R);
+            if (RESID) {
+#pragma unroll
+                for (int f = 0; f < 5; ++f) out[(size_t)f * n + c] = (double)R[f];
+            } else {
+                stage_update(rk, ph, n, c, qs, R, out, Qs, Wnext);
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------------ SS
@@ -359,7 +508,7 @@ __global__ void __launch_bounds__(128) k_ss(Grid g, Coef<T> k, Phys ph, RKStage 
     if (idx >= g.n) return;
     const Nbr s = make_nbr(g, idx);
     T R[5];
-    fused_residual<T, true>(s, g.n, Qf, Wf, Gw, k, R);
+    fused_residual<T, true>(GlobalAcc<T>{s, g.n, Qf, Wf, Gw}, k, R);
     stage_write<T, RESID>(rk, ph, g.n, s.c, Q64, R, out, Qs, Wnext);
 }
 
@@ -527,7 +676,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_batch_fused(con
         for (int p = threadIdx.x; p < tl.count; p += blockDim.x) {
             const Nbr s = make_nbr(I.g, tl.start + p);
             T R[5];
-            fused_residual<T, STORED_G>(s, n, Qf, Wf, I.G, I.k, R);
+            fused_residual<T, STORED_G>(GlobalAcc<T>{s, n, Qf, Wf, I.G}, I.k, R);
             stage_write<T, false>(rk, I.ph, n, s.c, Qin, R, Qout, I.Qs, I.W[1 - parity]);
         }
     }
@@ -747,6 +896,27 @@ cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const Phys& ph, const RKS
 }
 
 template <class T>
+cudaError_t launch_ra_tiled(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid,
+                            const T* Qf, const T* Wf, const double* Q64, double* out, double* Qs, T* Wnext,
+                            cudaStream_t st) {
+    const size_t smem = (size_t)kRing * kNF * kPlane * sizeof(T);
+    dim3 grid((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, (g.nz + kZChunk - 1) / kZChunk);
+    cudaError_t e;
+    if (resid) {
+        if ((e = cudaFuncSetAttribute(k_ra_tiled<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        k_ra_tiled<T, true><<<grid, kTX * kTY, smem, st>>>(g, k, ph, rk, Qf, Wf, Q64, out, Qs, Wnext);
+    } else {
+        if ((e = cudaFuncSetAttribute(k_ra_tiled<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
+            return e;
+        k_ra_tiled<T, false><<<grid, kTX * kTY, smem, st>>>(g, k, ph, rk, Qf, Wf, Q64, out, Qs, Wnext);
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t launch_ss_grad(const Grid& g, const Coef<T>& k, const T* Wf, T* Gw, cudaStream_t st) {
     k_ss_grad<T><<<blocks_for(g.n, 256), 256, 0, st>>>(g, k, Wf, Gw);
     return cudaGetLastError();
@@ -795,6 +965,9 @@ cudaError_t launch_bl_res(const Grid& g, const Phys& ph, const RKStage& rk, bool
 #define FD_INSTANTIATE(T)                                                                                        \
     template cudaError_t launch_ra<T>(const Grid&, const Coef<T>&, const Phys&, const RKStage&, bool, const T*,  \
                                       const T*, const double*, double*, double*, T*, cudaStream_t);             \
+    template cudaError_t launch_ra_tiled<T>(const Grid&, const Coef<T>&, const Phys&, const RKStage&, bool,      \
+                                            const T*, const T*, const double*, double*, double*, T*,            \
+                                            cudaStream_t);                                                      \
     template cudaError_t launch_ss_grad<T>(const Grid&, const Coef<T>&, const T*, T*, cudaStream_t);            \
     template cudaError_t launch_ss<T>(const Grid&, const Coef<T>&, const Phys&, const RKStage&, bool, const T*,  \
                                       const T*, const T*, const double*, double*, double*, T*, cudaStream_t);   \

@@ -84,3 +84,4 @@ def test_mixed_variants_agree():
             out[alg] = s.state()
     assert rel_l2(out["store_some"], out["store_all"]) <= 1e-7
     assert rel_l2(out["recompute_all"], out["store_all"]) <= 1e-7
+
