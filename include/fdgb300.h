@@ -178,7 +178,8 @@ typedef struct fd_instance_desc {
     int nx, ny, nz;                     /* grid, each axis >= 5, nx*ny*nz < 2^31 */
     double Re, Mach, Pr, gamma, dt;     /* as for fd_create */
     int algorithm;                      /* FD_STORE_SOME or FD_RECOMPUTE_ALL */
-    int tile_points;                    /* points per work item, >= 32; 0 = 1024 */
+    int tile_points;                    /* points per work item, >= 32; 0 = 1024 (binary32
+                                           recompute-all uses fixed 32 x 8 x 64 tiles instead) */
 } fd_instance_desc;
 
 typedef struct fd_batch fd_batch;

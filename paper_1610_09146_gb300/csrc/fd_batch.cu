@@ -114,10 +114,17 @@ void fill_inst(const fd_batch* b, std::vector<fd::BatchInst<T>>& out) {
     }
 }
 
-void make_tiles(const fd_batch* b, int family, std::vector<fd::BatchTile>& out) {
+// Work items: point ranges of tile_points each, or (tiled) the x-y tile /
+// z-chunk pairs of the shared-memory recompute-all kernel.
+void make_tiles(const fd_batch* b, int family, bool tiled, std::vector<fd::BatchTile>& out) {
     for (int i = 0; i < b->count; ++i) {
         const InstHost& h = b->inst[i];
         if (family >= 0 && h.d.algorithm != family) continue;
+        if (tiled) {
+            const int m = fd::tiled_work_items(h.d.nx, h.d.ny, h.d.nz);
+            for (int t = 0; t < m; ++t) out.push_back({i, t, 0});
+            continue;
+        }
         int tp = h.d.tile_points > 0 ? h.d.tile_points : kDefaultTile;
         for (int s = 0; s < h.n; s += tp) out.push_back({i, s, std::min(tp, h.n - s)});
     }
@@ -139,6 +146,8 @@ cudaError_t enqueue_family(fd_batch* b, bool ss, int s, int p, cudaStream_t st) 
     }
     if (!b->n_ra) return cudaSuccess;
     return b->prof.timed(st, FD_KERNEL_FUSED, [&] {
+        if (sizeof(T) == sizeof(float))  // binary32: fields staged through shared memory
+            return fd::launch_batch_ra_tiled<T>(I, b->d_ra, b->n_ra, s, p, b->grid_ra_fused, st);
         return fd::launch_batch_fused<T>(I, b->d_ra, b->n_ra, false, s, p, b->grid_ra_fused, st);
     });
 }
@@ -284,9 +293,9 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
         h.g = desc[i].algorithm == FD_STORE_SOME ? take(9 * (size_t)h.n * tsize) : (size_t)-1;
     }
     std::vector<fd::BatchTile> t_ss, t_ra, t_all;
-    make_tiles(b, FD_STORE_SOME, t_ss);
-    make_tiles(b, FD_RECOMPUTE_ALL, t_ra);
-    make_tiles(b, -1, t_all);
+    make_tiles(b, FD_STORE_SOME, false, t_ss);
+    make_tiles(b, FD_RECOMPUTE_ALL, dtype == FD_F32_ACC64, t_ra);
+    make_tiles(b, -1, false, t_all);
     size_t o_ss = take(std::max<size_t>(1, t_ss.size()) * sizeof(fd::BatchTile));
     size_t o_ra = take(std::max<size_t>(1, t_ra.size()) * sizeof(fd::BatchTile));
     size_t o_all = take(t_all.size() * sizeof(fd::BatchTile));
@@ -326,7 +335,7 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
         b->grid_grad = grid_for<double>(sms, false, false);
     } else {
         b->grid_ss_fused = grid_for<float>(sms, true, true);
-        b->grid_ra_fused = grid_for<float>(sms, true, false);
+        b->grid_ra_fused = sms * fd::batch_tiled_blocks_per_sm<float>();
         b->grid_grad = grid_for<float>(sms, false, false);
     }
     b->grid_prims = b->grid_grad;

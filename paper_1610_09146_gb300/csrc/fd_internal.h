@@ -73,6 +73,17 @@ struct BatchTile {
 
 template <class T>
 int batch_blocks_per_sm(bool fused, bool stored_g);
+
+// Batched binary32 recompute-all through shared memory: work items are the
+// (x-y tile, z-chunk) pairs of an instance, numbered 0 .. tiled_work_items-1
+// in BatchTile::start.  batch_tiled_blocks_per_sm also sets the kernel's
+// shared-memory attribute and must run on the device before the first launch.
+int tiled_work_items(int nx, int ny, int nz);
+template <class T>
+int batch_tiled_blocks_per_sm();
+template <class T>
+cudaError_t launch_batch_ra_tiled(const BatchInst<T>* insts, const BatchTile* tiles, int ntiles, int stage,
+                                  int parity, int grid, cudaStream_t st);
 template <class T>
 cudaError_t launch_batch_prims(const BatchInst<T>* insts, const BatchTile* tiles, int ntiles, int parity, int grid,
                                cudaStream_t st);

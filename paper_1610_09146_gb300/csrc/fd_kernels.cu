@@ -412,18 +412,18 @@ struct SmemAcc {
     }
 };
 
+// One tile (x0, y0) and z-chunk starting at zbeg, by one block of kTX x kTY
+// threads, with `sm` the block's ring of staged planes.
 template <class T, bool RESID>
-__global__ void __launch_bounds__(kTX* kTY, sizeof(T) == 4 ? 2 : 1)
-    k_ra_tiled(Grid g, Coef<T> k, Phys ph, RKStage rk, const T* __restrict__ Qf, const T* __restrict__ Wf,
-               const double* __restrict__ Q64, double* __restrict__ out, double* __restrict__ Qs,
-               T* __restrict__ Wnext) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sm = reinterpret_cast<T*>(smem_raw);
+__device__ __forceinline__ void ra_tiled_block(T* sm, const Grid& g, const Coef<T>& k, const Phys& ph,
+                                               const RKStage& rk, const T* __restrict__ Qf,
+                                               const T* __restrict__ Wf, const double* __restrict__ Q64,
+                                               double* __restrict__ out, double* __restrict__ Qs,
+                                               T* __restrict__ Wnext, int x0, int y0, int zbeg) {
     const int tid = threadIdx.x;
     const int tx = tid % kTX, ty = tid / kTX;
     const int nx = g.nx, ny = g.ny, nz = g.nz, n = g.n;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-    const int zbeg = blockIdx.z * kZChunk, zend = min(nz, zbeg + kZChunk);
+    const int zend = min(nz, zbeg + kZChunk);
     // in-plane offsets of the (at most two) staged cells of this thread
     int off[2];
     bool has[2];
@@ -476,6 +476,16 @@ __global__ void __launch_bounds__(kTX* kTY, sizeof(T) == 4 ? 2 : 1)
         }
         __syncthreads();
     }
+}
+
+template <class T, bool RESID>
+__global__ void __launch_bounds__(kTX* kTY, sizeof(T) == 4 ? 2 : 1)
+    k_ra_tiled(Grid g, Coef<T> k, Phys ph, RKStage rk, const T* __restrict__ Qf, const T* __restrict__ Wf,
+               const double* __restrict__ Q64, double* __restrict__ out, double* __restrict__ Qs,
+               T* __restrict__ Wnext) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ra_tiled_block<T, RESID>(reinterpret_cast<T*>(smem_raw), g, k, ph, rk, Qf, Wf, Q64, out, Qs, Wnext,
+                             blockIdx.x * kTX, blockIdx.y * kTY, blockIdx.z * kZChunk);
 }
 
 // ------------------------------------------------------------------ SS
@@ -682,6 +692,33 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_batch_fused(con
     }
 }
 
+// Batched recompute-all with shared-memory staging: work item t of an
+// instance is the x-y tile t % (ntx nty) of z-chunk t / (ntx nty) (tiles of
+// kTX x kTY points, chunks of kZChunk planes), carried in BatchTile::start.
+template <class T>
+__global__ void __launch_bounds__(kTX* kTY, sizeof(T) == 4 ? 2 : 1)
+    k_batch_ra_tiled(const BatchInst<T>* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
+                     int stage, int parity) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BatchInst<T> I;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        __syncthreads();
+        if (threadIdx.x == 0) I = insts[tl.inst];
+        __syncthreads();
+        const int ntx = (I.g.nx + kTX - 1) / kTX, nty = (I.g.ny + kTY - 1) / kTY;
+        const int zt = tl.start / (ntx * nty), r = tl.start % (ntx * nty);
+        const int n = I.g.n;
+        const double* Qin = I.Q[parity];
+        const T* Wc = I.W[parity];
+        const T* Qf = sizeof(T) == sizeof(double) ? reinterpret_cast<const T*>(Qin) : Wc;
+        const T* Wf = sizeof(T) == sizeof(double) ? Wc : Wc + 5 * (size_t)n;
+        const RKStage rk{I.adt[stage], I.bdt[stage], stage};
+        ra_tiled_block<T, false>(reinterpret_cast<T*>(smem_raw), I.g, I.k, I.ph, rk, Qf, Wf, Qin, I.Q[1 - parity],
+                                 I.Qs, I.W[1 - parity], (r % ntx) * kTX, (r / ntx) * kTY, zt * kZChunk);
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_batch_grad(const BatchInst<T>* __restrict__ insts,
                                                     const BatchTile* __restrict__ tiles, int ntiles, int parity) {
@@ -728,6 +765,36 @@ __global__ void __launch_bounds__(256) k_batch_prims(const BatchInst<T>* __restr
     }
 }
 
+int tiled_work_items(int nx, int ny, int nz) {
+    return ((nx + kTX - 1) / kTX) * ((ny + kTY - 1) / kTY) * ((nz + kZChunk - 1) / kZChunk);
+}
+
+template <class T>
+size_t tiled_smem_bytes() {
+    return (size_t)kRing * kNF * kPlane * sizeof(T);
+}
+
+template <class T>
+int batch_tiled_blocks_per_sm() {
+    int b = 0;
+    const size_t smem = tiled_smem_bytes<T>();
+    if (cudaFuncSetAttribute(k_batch_ra_tiled<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 1;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_ra_tiled<T>, kTX * kTY, smem);
+    return e == cudaSuccess && b > 0 ? b : 1;
+}
+
+template <class T>
+cudaError_t launch_batch_ra_tiled(const BatchInst<T>* insts, const BatchTile* tiles, int ntiles, int stage,
+                                  int parity, int grid, cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    // The shared-memory size attribute was set by batch_tiled_blocks_per_sm (a
+    // host call, kept out of this launch so that the launch can be captured).
+    k_batch_ra_tiled<T><<<grid, kTX * kTY, tiled_smem_bytes<T>(), st>>>(insts, tiles, ntiles, stage, parity);
+    return cudaGetLastError();
+}
+
 template <class T>
 int batch_blocks_per_sm(bool fused, bool stored_g) {
     int b = 0;
@@ -770,6 +837,9 @@ cudaError_t launch_batch_fused(const BatchInst<T>* insts, const BatchTile* tiles
 
 #define FD_INSTANTIATE_BATCH(T)                                                                                  \
     template int batch_blocks_per_sm<T>(bool, bool);                                                            \
+    template int batch_tiled_blocks_per_sm<T>();                                                                \
+    template cudaError_t launch_batch_ra_tiled<T>(const BatchInst<T>*, const BatchTile*, int, int, int, int,    \
+                                                  cudaStream_t);                                                \
     template cudaError_t launch_batch_prims<T>(const BatchInst<T>*, const BatchTile*, int, int, int,            \
                                                cudaStream_t);                                                   \
     template cudaError_t launch_batch_grad<T>(const BatchInst<T>*, const BatchTile*, int, int, int, cudaStream_t); \
@@ -899,7 +969,7 @@ template <class T>
 cudaError_t launch_ra_tiled(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid,
                             const T* Qf, const T* Wf, const double* Q64, double* out, double* Qs, T* Wnext,
                             cudaStream_t st) {
-    const size_t smem = (size_t)kRing * kNF * kPlane * sizeof(T);
+    const size_t smem = tiled_smem_bytes<T>();
     dim3 grid((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, (g.nz + kZChunk - 1) / kZChunk);
     cudaError_t e;
     if (resid) {

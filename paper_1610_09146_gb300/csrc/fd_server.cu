@@ -222,7 +222,12 @@ fd::BatchInst<T> record(const fd_server* s, const Active& a) {
     return I;
 }
 
-void append_tiles(const Active& a, std::vector<fd::BatchTile>& v) {
+void append_tiles(const Active& a, std::vector<fd::BatchTile>& v, bool tiled = false) {
+    if (tiled) {  // x-y tile / z-chunk work items of the shared-memory recompute-all kernel
+        const int m = fd::tiled_work_items(a.r.nx, a.r.ny, a.r.nz);
+        for (int t = 0; t < m; ++t) v.push_back({a.slot, t, 0});
+        return;
+    }
     int tp = a.r.tile_points > 0 ? a.r.tile_points : kDefaultTile;
     for (int st = 0; st < a.n; st += tp) v.push_back({a.slot, st, std::min(tp, a.n - st)});
 }
@@ -242,7 +247,8 @@ cudaError_t rebuild(fd_server* s) {
             a.slot = (int)I32.size();
             I32.push_back(record<float>(s, a));
         }
-        append_tiles(a, t[d][a.r.algorithm == FD_STORE_SOME ? 0 : 1]);
+        const bool ss = a.r.algorithm == FD_STORE_SOME;
+        append_tiles(a, t[d][ss ? 0 : 1], !ss && d == 1);
         if (a.fresh) append_tiles(a, f[d]);
     }
     size_t off = 0;
@@ -300,8 +306,9 @@ cudaError_t run_group(fd_server* s, int d) {
             cudaSuccess)
             return e;
     }
+    const bool tiled = sizeof(T) == sizeof(float);  // binary32 RA: shared-memory kernel
     const int gs = s->sms * fd::batch_blocks_per_sm<T>(true, true);
-    const int gr = s->sms * fd::batch_blocks_per_sm<T>(true, false);
+    const int gr = s->sms * (tiled ? fd::batch_tiled_blocks_per_sm<T>() : fd::batch_blocks_per_sm<T>(true, false));
     for (int st = 0, p = s->parity; st < 3; ++st, p ^= 1) {
         if (s->ntiles[d][0]) {
             if ((e = fd::launch_batch_grad<T>(I, s->tiles[d][0], s->ntiles[d][0], p, gg, s->stream)) != cudaSuccess)
@@ -311,9 +318,9 @@ cudaError_t run_group(fd_server* s, int d) {
                 return e;
         }
         if (s->ntiles[d][1]) {
-            if ((e = fd::launch_batch_fused<T>(I, s->tiles[d][1], s->ntiles[d][1], false, st, p, gr, s->stream)) !=
-                cudaSuccess)
-                return e;
+            e = tiled ? fd::launch_batch_ra_tiled<T>(I, s->tiles[d][1], s->ntiles[d][1], st, p, gr, s->stream)
+                      : fd::launch_batch_fused<T>(I, s->tiles[d][1], s->ntiles[d][1], false, st, p, gr, s->stream);
+            if (e != cudaSuccess) return e;
         }
     }
     return cudaSuccess;
