@@ -392,6 +392,88 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------- 512^3 mixed precision
+
+
+def run_mixed512(args):
+    """Taylor-Green 512^3: binary32-stencil / binary64-accumulate recompute-all and store-some
+    against the binary64 store-some run on the GPU, after 100 and after 200 RK3 steps
+    (per conserved variable relative L2 error, kinetic energy and enstrophy error), with
+    each run's throughput.  The binary64 GPU path is itself checked against the oracle
+    (relative L-inf, 10 steps of 64^3) in the same run."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1610_09146_gb300 as fd
+    from paper_1610_09146_gb300 import native
+    torch.cuda.set_device(0)
+    fd.build()
+    n, steps = args.grid, args.solve_steps
+    dt = fd.dt_for_grid(n)
+    half = steps // 2
+
+    def run(alg, dtype):
+        out = {}
+        with fd.Solver(n, dt=dt, algorithm=alg, dtype=dtype) as s:
+            native.fd_profile(s.h, 1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.step(half)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            out["Q_half"] = s.state()
+            out["diag_half"] = s.diagnostics()
+            t2 = time.perf_counter()
+            s.step(steps - half)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            out["Q"] = s.state()
+            out["diag"] = s.diagnostics()
+            fused_ms, fused_n = native.fd_profile_read(s.h, native.FD_KERNEL_FUSED)
+        out["ms_per_step"] = 1e3 * ((t1 - t0) + (t3 - t2)) / steps
+        out["fused_ms"] = fused_ms / max(fused_n, 1)
+        return out
+
+    def rel_l2(a, b):
+        return [float(np.linalg.norm(a[v] - b[v]) / np.linalg.norm(b[v])) for v in range(5)]
+
+    # binary64 path vs oracle at 64^3, 10 steps
+    m = 64
+    ref = oracle.run(oracle.tgv_ic(m, m, m, GAMMA, MACH), 10, dt=fd.dt_for_grid(m))
+    with fd.Solver(m, dt=fd.dt_for_grid(m), algorithm="store_some", dtype="f64") as s:
+        s.step(10)
+        Qm = s.state()
+    val64 = max(float(np.abs(Qm[v] - ref[v]).max() / np.abs(ref[v]).max()) for v in range(5))
+    base = run("store_some", "f64")
+    res = {}
+    for alg in ("recompute_all", "store_some"):
+        r = run(alg, "f32")
+        res[SHORT[alg]] = {
+            "ms_per_step": r["ms_per_step"], "point_updates_per_s": n**3 / (r["ms_per_step"] / 1e3),
+            "fused_ms_per_launch": r["fused_ms"],
+            f"rel_l2_per_var_{half}_steps": rel_l2(r["Q_half"], base["Q_half"]),
+            f"rel_l2_per_var_{steps}_steps": rel_l2(r["Q"], base["Q"]),
+            f"ke_rel_err_{half}_steps": abs(r["diag_half"][0] - base["diag_half"][0]) / base["diag_half"][0],
+            f"ke_rel_err_{steps}_steps": abs(r["diag"][0] - base["diag"][0]) / base["diag"][0],
+            f"enstrophy_rel_err_{steps}_steps": abs(r["diag"][1] - base["diag"][1]) / base["diag"][1],
+        }
+        del r
+    line = {
+        "workload": f"Taylor-Green {n}^3, binary32 stencils / binary64 RK accumulation and reductions, "
+                    f"{steps} RK3 steps, vs the binary64 GPU run",
+        "metric": METRIC, "unit": METRIC, "higher_is_better": True, "grid": [n, n, n], "dt": dt,
+        "value": max(v["point_updates_per_s"] for v in res.values()),
+        "fp64_reference": {"family": "SS", "ms_per_step": base["ms_per_step"],
+                           "point_updates_per_s": n**3 / (base["ms_per_step"] / 1e3),
+                           "ke": base["diag"][0], "enstrophy": base["diag"][1],
+                           "validated_vs_oracle_64cube_10steps_rel_linf": val64},
+        "f32": res,
+        "bounds": {"rel_l2_state": 1e-5, "ke_rel": 1e-6},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ serving
 
 
@@ -517,8 +599,9 @@ def main():
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     ap.add_argument("--variants", nargs="+", default=VARIANTS, choices=VARIANTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["single", "batched", "serve"], default="single",
-                    help="single: the 256^3 line (default); batched / serve: the ensemble and serving runs")
+    ap.add_argument("--workload", choices=["single", "batched", "serve", "mixed512"], default="single",
+                    help="single: the 256^3 line (default); batched / serve / mixed512: the ensemble, "
+                         "serving and 512^3 mixed-precision runs")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--solve-steps", type=int, default=100)
     ap.add_argument("--requests", type=int, default=120)
@@ -534,6 +617,12 @@ def main():
         run_batched(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "mixed512":
+        if args.grid == N_GRID:
+            args.grid = 512
+        if args.solve_steps == 100:
+            args.solve_steps = 200
+        run_mixed512(args)
     else:
         run_ours(args)
 
