@@ -91,6 +91,20 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate_over_ranks(local_ms, points_per_rank, steps, dist=None, device=None):
+    """Whole-job throughput: the slowest rank's time (max over ranks of the timed region)
+    and the points all ranks advanced.  Returns (value, max_ms)."""
+    ws = 1
+    ms = float(local_ms)
+    if dist is not None and dist.is_initialized():
+        import torch
+        ws = dist.get_world_size()
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ws * points_per_rank * steps / (ms / 1e3), ms
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
 
@@ -204,9 +218,9 @@ def roofline_of(dtype, alg, kern, n, hbm_peak, hbm_src):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of a 256^3 launch, from one ncu
-# capture of the current kernel on a 160^3 grid (two launches, 249 B per point) scaled by
+# capture of the current kernel on a 160^3 grid (two launches, 287 B per point) scaled by
 # the point count; None where no capture of the current kernel version exists.
-TRAFFIC = {}
+TRAFFIC = {("f64", "store_some", "fused"): 4.82e9}
 
 
 def e2e_run(fd, torch, s, n, steps, stream):
@@ -275,11 +289,7 @@ def run_ours(args):
     for alg in args.variants:
         s, ms, kern, finite, diag = time_family(fd, torch, alg, args.dtype, n, args.steps, args.warmup, stream,
                                                 barrier, clocks)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        value = ws * npts * args.steps / (ms / 1e3)
+        value, ms = aggregate_over_ranks(ms, npts, args.steps, dist, "cuda")
         launches = sum(k["launches"] for k in kern.values())
         results[alg] = {"value": value, "ms_per_step": ms / args.steps, "finite": finite, "gpu_launches": launches,
                         "kernels": kern, "roofline": roofline_of(args.dtype, alg, kern, npts, hbm_peak, hbm_src),
@@ -294,10 +304,8 @@ def run_ours(args):
             s.close()
     cl = clocks.stop()
     e2e = e2e_run(fd, torch, keep, n, max(3, min(args.steps, 10)), stream.cuda_stream)
-    if dist is not None:
-        t = torch.tensor([npts * e2e["steps"] / e2e["value"]], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e["value"] = ws * npts * e2e["steps"] / float(t.item())
+    e2e["value"], _ = aggregate_over_ranks(1e3 * npts * e2e["steps"] / e2e["value"], npts, e2e["steps"], dist,
+                                           "cuda")
     keep.close()
     r = results[best]
     line = {
