@@ -64,9 +64,19 @@ extern "C" {
  *               perturbation variables (rho-1, p-p0, T-1, rhoE-rhoE0); the
  *               conserved state, the Runge-Kutta accumulation and the kinetic
  *               energy / enstrophy reductions stay in binary64.  The paper has
- *               no counterpart; it is a precision mode of this library. */
+ *               no counterpart; it is a precision mode of this library.
+ * FD_DF64       binary64-accurate results without binary64 instructions: the
+ *               stencils, fluxes, residual, RK accumulation and the stored
+ *               state use double-word ("double-float") arithmetic, pairs of
+ *               binary32 numbers with about 48 significant bits (Knuth
+ *               TwoSum, Dekker FastTwoSum, FMA-based products; the algorithms
+ *               of Joldes, Muller & Popescu 2017), on the shifted fields of
+ *               FD_F32_ACC64.  On GB300 binary32 issues 64x faster than
+ *               binary64.  States cross the API as binary64; the reductions
+ *               run in binary64.  No counterpart in the paper. */
 #define FD_F64 0
 #define FD_F32_ACC64 1
+#define FD_DF64 2
 
 /* Device allocator callbacks (for example PyTorch's caching allocator).
  * alloc returns a device pointer aligned to at least 256 bytes, or NULL;
@@ -89,7 +99,7 @@ typedef struct fd_handle fd_handle;
  *   Re, Mach, Pr, gamma  flow constants (Eqs. 4-7): Re, Mach, Pr > 0,
  *               gamma > 1; dt > 0 is the time step of every fd_step;
  *   algorithm   FD_STORE_ALL, FD_STORE_SOME or FD_RECOMPUTE_ALL;
- *   dtype       FD_F64 or FD_F32_ACC64;
+ *   dtype       FD_F64, FD_F32_ACC64 or FD_DF64;
  *   alloc       NULL for cudaMalloc/cudaFree, else allocator callbacks;
  *   cuda_stream cudaStream_t for all work of this handle (NULL = default).
  * On success *out receives the handle.  Errors: FD_EINVAL, FD_ENOMEM,

@@ -22,6 +22,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/fdgb300.h"
@@ -64,6 +65,7 @@ struct fd_handle {
     double* Qs = nullptr;
     double* W[2] = {nullptr, nullptr};
     float* Wf[2] = {nullptr, nullptr};  // binary32 mode: perturbation fields (10 arrays each)
+    fd::df64* Wd[2] = {nullptr, nullptr};  // df64 mode: perturbation fields (10 arrays each)
     int wcur = 0;                       // W[wcur] / Wf[wcur] hold the primitives of Q[cur] ...
     bool wvalid = false;                // ... when wvalid
     double* G = nullptr;   // SS
@@ -71,6 +73,7 @@ struct fd_handle {
     double* D1 = nullptr;  // BL
     double* D2 = nullptr;  // BL
     float* Gf = nullptr;   // binary32 SS: 9 gradients
+    fd::df64* Gd = nullptr;  // df64 SS: 9 gradients
     double* partial = nullptr;
     double* diag = nullptr;
     int* flag = nullptr;
@@ -78,6 +81,7 @@ struct fd_handle {
     fd::Phys phys{};
     fd::Coef<double> kd{};  // fused-residual coefficients, binary64 mode
     fd::Coef<float> kf{};   // and binary32 perturbation mode
+    fd::Coef<fd::df64> kw{};  // and df64 perturbation mode
     fd::Profiler prof;
 
     template <class T>
@@ -106,6 +110,10 @@ template <>
 const fd::Coef<float>& fd_handle::coef<float>() const {
     return kf;
 }
+template <>
+const fd::Coef<fd::df64>& fd_handle::coef<fd::df64>() const {
+    return kw;
+}
 
 namespace {
 
@@ -115,13 +123,14 @@ int check_args(int nx, int ny, int nz, double Re, double Mach, double Pr, double
         return fail_global(FD_EINVAL, "fd_create: grid %dx%dx%d: %s", nx, ny, nz, why);
     if (algorithm != FD_STORE_ALL && algorithm != FD_STORE_SOME && algorithm != FD_RECOMPUTE_ALL)
         return fail_global(FD_EINVAL, "unknown algorithm %d", algorithm);
-    if (dtype != FD_F64 && dtype != FD_F32_ACC64) return fail_global(FD_EINVAL, "unknown dtype %d", dtype);
+    if (dtype != FD_F64 && dtype != FD_F32_ACC64 && dtype != FD_DF64)
+        return fail_global(FD_EINVAL, "unknown dtype %d", dtype);
     return FD_OK;
 }
 
 // Byte layout of a handle's single device allocation.
 struct Layout {
-    size_t q0, q1, qs, w0, w1, g, p, d1, d2, wf0, wf1, gf, partial, diag, flag, total;
+    size_t q0, q1, qs, w0, w1, g, p, d1, d2, wf0, wf1, gf, wd0, wd1, gd, partial, diag, flag, total;
 };
 
 Layout plan(long long n, int algorithm, int dtype) {
@@ -136,9 +145,19 @@ Layout plan(long long n, int algorithm, int dtype) {
     L.q0 = take(f5);
     L.q1 = take(f5);
     L.qs = take(f5);
-    L.w0 = take(f5);
-    L.w1 = L.g = L.p = L.d1 = L.d2 = L.wf0 = L.wf1 = L.gf = (size_t)-1;
-    if (dtype == FD_F64) {
+    L.w1 = L.g = L.p = L.d1 = L.d2 = L.wf0 = L.wf1 = L.gf = L.wd0 = L.wd1 = L.gd = (size_t)-1;
+    L.w0 = dtype == FD_DF64 ? (size_t)-1 : take(f5);
+    if (dtype == FD_DF64) {
+        // state Q[2], Qs hold double-words (8 bytes per value, like binary64)
+        L.wd0 = take(10 * n * sizeof(fd::df64));
+        L.wd1 = take(10 * n * sizeof(fd::df64));
+        if (algorithm == FD_STORE_SOME) L.gd = take(9 * n * sizeof(fd::df64));
+        if (algorithm == FD_STORE_ALL) {
+            L.p = take(18 * n * sizeof(fd::df64));
+            L.d1 = take(45 * n * sizeof(fd::df64));
+            L.d2 = take(18 * n * sizeof(fd::df64));
+        }
+    } else if (dtype == FD_F64) {
         L.w1 = take(f5);
         if (algorithm == FD_STORE_SOME) L.g = take(9 * n * sizeof(double));
         if (algorithm == FD_STORE_ALL) {
@@ -183,9 +202,9 @@ cudaError_t timed(fd_handle* h, int cls, F launch) {
 }
 
 // Kernels of one stage of family `alg` in precision T.
-template <class T>
+template <class T, class S = fd::state_t<T>>
 cudaError_t stage_kernels(fd_handle* h, const fd::RKStage& rk, bool resid, const T* Qf, const T* Wf, T* G, T* P,
-                          T* D1, T* D2, const double* Qin, double* Qout, T* Wnext) {
+                          T* D1, T* D2, const S* Qin, S* Qout, T* Wnext) {
     const fd::Grid& g = h->grid;
     const fd::Phys& ph = h->phys;
     const fd::Coef<T>& k = h->coef<T>();
@@ -197,15 +216,18 @@ cudaError_t stage_kernels(fd_handle* h, const fd::RKStage& rk, bool resid, const
             // kernel is latency-bound on its tap loads); binary64 is bound by FP64
             // issue, where staging does not help.
             return timed(h, FD_KERNEL_FUSED, [&] {
-                if (sizeof(T) == sizeof(float))
+                if constexpr (std::is_same<T, float>::value)
                     return fd::launch_ra_tiled<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, h->Qs, Wnext, st);
-                return fd::launch_ra<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, h->Qs, Wnext, st);
+                else
+                    return fd::launch_ra<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, reinterpret_cast<S*>(h->Qs),
+                                            Wnext, st);
             });
         case FD_STORE_SOME:
             e = timed(h, FD_KERNEL_GRAD, [&] { return fd::launch_ss_grad<T>(g, k, Wf, G, st); });
             if (e != cudaSuccess) return e;
             return timed(h, FD_KERNEL_FUSED, [&] {
-                return fd::launch_ss<T>(g, k, ph, rk, resid, Qf, Wf, G, Qin, Qout, h->Qs, Wnext, st);
+                return fd::launch_ss<T>(g, k, ph, rk, resid, Qf, Wf, G, Qin, Qout, reinterpret_cast<S*>(h->Qs),
+                                        Wnext, st);
             });
         default:
             e = timed(h, FD_KERNEL_PRODUCTS, [&] { return fd::launch_bl_prod<T>(g, Qf, Wf, P, st); });
@@ -215,7 +237,8 @@ cudaError_t stage_kernels(fd_handle* h, const fd::RKStage& rk, bool resid, const
             e = timed(h, FD_KERNEL_DERIV2, [&] { return fd::launch_bl_d2<T>(g, Wf, D1, D2, st); });
             if (e != cudaSuccess) return e;
             return timed(h, FD_KERNEL_FUSED, [&] {
-                return fd::launch_bl_res<T>(g, ph, rk, resid, Qf, Wf, D1, D2, Qin, Qout, h->Qs, Wnext, st);
+                return fd::launch_bl_res<T>(g, ph, rk, resid, Qf, Wf, D1, D2, Qin, Qout, reinterpret_cast<S*>(h->Qs),
+                                            Wnext, st);
             });
     }
 }
@@ -227,10 +250,11 @@ cudaError_t stage_kernels(fd_handle* h, const fd::RKStage& rk, bool resid, const
 cudaError_t run_stage(fd_handle* h, int s, bool resid, double* out) {
     const fd::Grid& g = h->grid;
     const fd::Phys& ph = h->phys;
-    fd::RKStage rk{kRkA[s] * h->dt, kRkB[s] * h->dt, s};
+    const fd::RKStage rk = fd::make_stage(s, h->dt);
     const double* Qin = h->Q[h->cur];
     double* Qout = resid ? out : h->Q[1 - h->cur];
     const int wc = h->wcur;
+    const long long n = h->n;
     cudaError_t e;
     if (h->dtype == FD_F64) {
         if (!h->wvalid) {
@@ -241,15 +265,36 @@ cudaError_t run_stage(fd_handle* h, int s, bool resid, double* out) {
         return stage_kernels<double>(h, rk, resid, Qin, h->W[wc], h->G, h->P, h->D1, h->D2, Qin, Qout,
                                      resid ? nullptr : h->W[1 - wc]);
     }
+    if (h->dtype == FD_DF64) {
+        using fd::df64;
+        const df64* Qd = reinterpret_cast<const df64*>(Qin);
+        if (!h->wvalid) {
+            e = timed(h, FD_KERNEL_PRIMS, [&] { return fd::launch_prims_df64(g, ph, Qd, h->Wd[wc], h->stream); });
+            if (e != cudaSuccess) return e;
+            h->wvalid = true;
+        }
+        return stage_kernels<df64>(h, rk, resid, h->Wd[wc], h->Wd[wc] + 5 * n, h->Gd, reinterpret_cast<df64*>(h->P),
+                                   reinterpret_cast<df64*>(h->D1), reinterpret_cast<df64*>(h->D2), Qd,
+                                   reinterpret_cast<df64*>(Qout), resid ? nullptr : h->Wd[1 - wc]);
+    }
     if (!h->wvalid) {
         e = timed(h, FD_KERNEL_PRIMS, [&] { return fd::launch_prims_f32(g, ph, Qin, h->Wf[wc], h->stream); });
         if (e != cudaSuccess) return e;
         h->wvalid = true;
     }
-    const long long n = h->n;
     return stage_kernels<float>(h, rk, resid, h->Wf[wc], h->Wf[wc] + 5 * n, h->Gf, reinterpret_cast<float*>(h->P),
                                 reinterpret_cast<float*>(h->D1), reinterpret_cast<float*>(h->D2), Qin, Qout,
                                 resid ? nullptr : h->Wf[1 - wc]);
+}
+
+// df64 mode: the state buffers hold double-words; these move a binary64 copy
+// of the current state through the saved register Qs, which is dead between
+// steps (stage 0 rewrites it).
+fd::Shift5 state_shift(const fd_handle* h) { return fd::Shift5{{1.0, 0.0, 0.0, 0.0, h->phys.rhoE0}}; }
+
+cudaError_t state_to_binary64(fd_handle* h, double* dst) {
+    return fd::launch_from_df64(reinterpret_cast<const fd::df64*>(h->Q[h->cur]), dst, h->n, state_shift(h),
+                                h->stream);
 }
 
 }  // namespace
@@ -311,6 +356,9 @@ int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, d
     h->Qs = at<double>(h->block, L.qs);
     h->W[0] = at<double>(h->block, L.w0);
     h->W[1] = at<double>(h->block, L.w1);
+    h->Wd[0] = at<fd::df64>(h->block, L.wd0);
+    h->Wd[1] = at<fd::df64>(h->block, L.wd1);
+    h->Gd = at<fd::df64>(h->block, L.gd);
     if (dtype == FD_F64) {
         h->G = at<double>(h->block, L.g);
         h->P = at<double>(h->block, L.p);
@@ -335,8 +383,15 @@ int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, d
     const fd::Phys& ph = h->phys;
     h->kd = fd::make_coef<double>(g, ph, false);
     h->kf = fd::make_coef<float>(g, ph, true);
+    h->kw = fd::make_coef<fd::df64>(g, ph, true);
 
-    e = fd::launch_tgv_ic(g, ph, hx, hy, hz, h->Q[0], h->stream);
+    if (dtype == FD_DF64) {
+        e = fd::launch_tgv_ic(g, ph, hx, hy, hz, h->Qs, h->stream);
+        if (e == cudaSuccess)
+            e = fd::launch_to_df64(h->Qs, reinterpret_cast<fd::df64*>(h->Q[0]), h->n, state_shift(h), h->stream);
+    } else {
+        e = fd::launch_tgv_ic(g, ph, hx, hy, hz, h->Q[0], h->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         device_free(h);
@@ -368,8 +423,16 @@ int fd_get_state(fd_handle* h, double* dst, size_t n_elems, int dst_is_device) {
     if (!dst) return h->fail(FD_EINVAL, "fd_get_state: dst is NULL");
     if (n_elems != 5 * (size_t)h->n)
         return h->fail(FD_EINVAL, "fd_get_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h->n);
-    cudaError_t e = cudaMemcpyAsync(dst, h->Q[h->cur], n_elems * sizeof(double),
-                                    dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e = cudaSuccess;
+    const double* src = h->Q[h->cur];
+    if (h->dtype == FD_DF64) {
+        double* tmp = dst_is_device ? dst : h->Qs;
+        e = state_to_binary64(h, tmp);
+        src = tmp;
+    }
+    if (e == cudaSuccess && src != dst)
+        e = cudaMemcpyAsync(dst, src, n_elems * sizeof(double),
+                            dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "fd_get_state");
     return FD_OK;
@@ -381,8 +444,11 @@ int fd_set_state(fd_handle* h, const double* src, size_t n_elems, int src_is_dev
     if (n_elems != 5 * (size_t)h->n)
         return h->fail(FD_EINVAL, "fd_set_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h->n);
     h->wvalid = false;
-    cudaError_t e = cudaMemcpyAsync(h->Q[h->cur], src, n_elems * sizeof(double),
+    double* dst = h->dtype == FD_DF64 ? h->Qs : h->Q[h->cur];
+    cudaError_t e = cudaMemcpyAsync(dst, src, n_elems * sizeof(double),
                                     src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && h->dtype == FD_DF64)
+        e = fd::launch_to_df64(h->Qs, reinterpret_cast<fd::df64*>(h->Q[h->cur]), h->n, state_shift(h), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "fd_set_state");
     return FD_OK;
@@ -391,10 +457,19 @@ int fd_set_state(fd_handle* h, const double* src, size_t n_elems, int src_is_dev
 int fd_diagnostics(fd_handle* h, double* ke, double* enstrophy) {
     if (!h) return fail_global(FD_EINVAL, "fd_diagnostics: NULL handle");
     double out[2];
-    // Scratch for the velocities: the W buffer the next stage will overwrite
-    // (binary64), or W[0], unused by the binary32 stages.
-    double* Wv = h->dtype == FD_F64 ? h->W[1 - h->wcur] : h->W[0];
-    cudaError_t e = fd::launch_diagnostics_f64(h->grid, h->Q[h->cur], Wv, h->partial, h->diag, h->stream);
+    // Scratch for the velocities: the working-field buffer the next stage will
+    // overwrite (binary64, df64), or W[0], unused by the binary32 stages.  The
+    // df64 mode first converts the state to binary64 in Qs (dead between steps).
+    double* Wv = h->dtype == FD_F64    ? h->W[1 - h->wcur]
+                 : h->dtype == FD_DF64 ? reinterpret_cast<double*>(h->Wd[1 - h->wcur])
+                                       : h->W[0];
+    const double* Q = h->Q[h->cur];
+    cudaError_t e = cudaSuccess;
+    if (h->dtype == FD_DF64) {
+        e = state_to_binary64(h, h->Qs);
+        Q = h->Qs;
+    }
+    if (e == cudaSuccess) e = fd::launch_diagnostics_f64(h->grid, Q, Wv, h->partial, h->diag, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->diag, sizeof out, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "fd_diagnostics");
@@ -409,9 +484,19 @@ int fd_residual(fd_handle* h, double* R, size_t n_elems, int dst_is_device) {
     if (n_elems != 5 * (size_t)h->n)
         return h->fail(FD_EINVAL, "fd_residual: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h->n);
     // Between steps the saved register Qs is dead (stage 0 rewrites it), so it
-    // serves as the device buffer for R.
+    // serves as the device buffer for R.  The df64 mode evaluates R as
+    // double-words into the spare working-field buffer, then converts it.
     double* out = dst_is_device ? R : h->Qs;
-    cudaError_t e = run_stage(h, 0, true, out);
+    cudaError_t e;
+    if (h->dtype == FD_DF64) {
+        double* Rw = reinterpret_cast<double*>(h->Wd[1 - h->wcur]);
+        e = run_stage(h, 0, true, Rw);
+        if (e == cudaSuccess)  // a residual is a rate: no shift
+            e = fd::launch_from_df64(reinterpret_cast<const fd::df64*>(Rw), out, h->n, fd::Shift5{{0, 0, 0, 0, 0}},
+                                     h->stream);
+    } else {
+        e = run_stage(h, 0, true, out);
+    }
     if (e == cudaSuccess && !dst_is_device)
         e = cudaMemcpyAsync(R, h->Qs, n_elems * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -422,8 +507,14 @@ int fd_residual(fd_handle* h, double* R, size_t n_elems, int dst_is_device) {
 int fd_check_finite(fd_handle* h) {
     if (!h) return fail_global(FD_EINVAL, "fd_check_finite: NULL handle");
     int flag = 0;
-    cudaError_t e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
-    if (e == cudaSuccess) e = fd::launch_check_finite(h->Q[h->cur], 5LL * h->n, h->flag, h->stream);
+    const double* Q = h->Q[h->cur];
+    cudaError_t e = cudaSuccess;
+    if (h->dtype == FD_DF64) {
+        e = state_to_binary64(h, h->Qs);
+        Q = h->Qs;
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = fd::launch_check_finite(Q, 5LL * h->n, h->flag, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "fd_check_finite");

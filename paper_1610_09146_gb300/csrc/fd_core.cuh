@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fd_df64.cuh"
+
 namespace fd {
 
 // Grid of the periodic cube [0, 2*pi]^3 (Section 3); h_a = 2*pi / n_a.
@@ -19,6 +21,8 @@ struct Grid {
     double inv12h2[3];   // 1 / (12 h_a^2)
     float inv12hf[3];
     float inv12h2f[3];
+    df64 inv12h_w[3];    // as double-words (df64 mode)
+    df64 inv12h2_w[3];
 };
 
 // Flow constants of Eqs. 4-7, with negative powers precomputed.
@@ -29,6 +33,8 @@ struct Phys {
     double kappa;        // 1 / ((gamma - 1) Mach^2 Pr Re)
     double p0;           // 1 / (gamma Mach^2): mean pressure of the TGV state
     double rhoE0;        // p0 / (gamma - 1): mean total energy at rest
+    df64 gm1_w, gM2_w, rhoE0_w;  // the same constants as double-words (df64 mode)
+    df64 nu_w, kappa_w, cE_w;     // nu, kappa and rhoE0 + p0 as double-words
 };
 
 // Two-register low-storage RK3 (Section 2 / Fig. 1, read as
@@ -38,7 +44,40 @@ struct RKStage {
     double adt;   // a_s * dt
     double bdt;   // b_s * dt
     int stage;    // 0, 1, 2 (stage 0 reads Q as Qs; stage 2 leaves Qs alone)
+    df64 adt_w, bdt_w;  // a_s dt, b_s dt as double-words (df64 mode)
 };
+
+// Five per-variable constants (the shift of the df64 state at the API boundary).
+struct Shift5 {
+    double s[5];
+};
+
+// Precision modes.  T is the arithmetic of the stencils and the residual; the
+// conserved state (and the RK accumulation) is kept in state_t<T>:
+//   double  binary64 everywhere;
+//   float   binary32 stencils on shifted fields, binary64 state;
+//   df64    double-word stencils on shifted fields and a double-word state,
+//           itself shifted (rho - 1, rho u_i, rho E - rhoE0), so that no
+//           binary64 instruction is issued in a step.
+template <class T>
+struct Prec;
+template <>
+struct Prec<double> {
+    using S = double;
+    static constexpr bool shifted = false;
+};
+template <>
+struct Prec<float> {
+    using S = double;
+    static constexpr bool shifted = true;
+};
+template <>
+struct Prec<df64> {
+    using S = df64;
+    static constexpr bool shifted = true;
+};
+template <class T>
+using state_t = typename Prec<T>::S;
 
 // Linear index of a grid point and the offsets to its periodic neighbours
 // at -2, -1, +1, +2 along each axis.  Offsets along different axes add, so

@@ -32,6 +32,8 @@ inline Grid make_grid(int nx, int ny, int nz) {
         g.inv12h2[a] = 1.0 / (12.0 * h * h);
         g.inv12hf[a] = (float)g.inv12h[a];
         g.inv12h2f[a] = (float)g.inv12h2[a];
+        g.inv12h_w[a] = df64(g.inv12h[a]);
+        g.inv12h2_w[a] = df64(g.inv12h2[a]);
     }
     return g;
 }
@@ -45,11 +47,28 @@ inline Phys make_phys(double Re, double Mach, double Pr, double gamma) {
     ph.kappa = 1.0 / ((gamma - 1.0) * Mach * Mach * Pr * Re);
     ph.p0 = 1.0 / (gamma * Mach * Mach);
     ph.rhoE0 = ph.p0 / (gamma - 1.0);
+    ph.gm1_w = df64(ph.gm1);
+    ph.gM2_w = df64(ph.gM2);
+    ph.rhoE0_w = df64(ph.rhoE0);
+    ph.nu_w = df64(ph.nu);
+    ph.kappa_w = df64(ph.kappa);
+    ph.cE_w = df64(ph.rhoE0 + ph.p0);
     return ph;
 }
 
 // Constants of the fused residual (see fd::Coef); `shifted` selects the
 // binary32 perturbation form.
+// The RK constants of stage s for a time step dt.
+inline RKStage make_stage(int s, double dt) {
+    RKStage rk{};
+    rk.adt = kRkA[s] * dt;
+    rk.bdt = kRkB[s] * dt;
+    rk.stage = s;
+    rk.adt_w = df64(rk.adt);
+    rk.bdt_w = df64(rk.bdt);
+    return rk;
+}
+
 template <class T>
 Coef<T> make_coef(const Grid& g, const Phys& ph, bool shifted) {
     Coef<T> k{};

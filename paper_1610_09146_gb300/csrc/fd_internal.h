@@ -19,6 +19,11 @@ cudaError_t launch_tgv_ic(const Grid& g, const Phys& ph, double hx, double hy, d
 // perturbation fields F = (rho-1, rho u, rho v, rho w, rhoE-rhoE0, u, v, w, p-p0, T-1).
 cudaError_t launch_prims_f64(const Grid& g, const Phys& ph, const double* Q, double* W, cudaStream_t st);
 cudaError_t launch_prims_f32(const Grid& g, const Phys& ph, const double* Q, float* F, cudaStream_t st);
+cudaError_t launch_prims_df64(const Grid& g, const Phys& ph, const df64* Q, df64* F, cudaStream_t st);
+// binary64 <-> double-word conversion of 5 arrays of n values, subtracting /
+// adding a per-array shift (df64 mode at the API boundary).
+cudaError_t launch_to_df64(const double* src, df64* dst, long long n, const Shift5& sh, cudaStream_t st);
+cudaError_t launch_from_df64(const df64* src, double* dst, long long n, const Shift5& sh, cudaStream_t st);
 
 // Kernels of one stage in precision T (double or float), one launch each.
 // Qf / Wf are the five conserved-like and five primitive-like working
@@ -30,17 +35,17 @@ cudaError_t launch_prims_f32(const Grid& g, const Phys& ph, const double* Q, flo
 //   BL: launch_bl_prod, launch_bl_d1, launch_bl_d2, launch_bl_res
 template <class T>
 cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid, const T* Qf,
-                      const T* Wf, const double* Q64, double* out, double* Qs, T* Wnext, cudaStream_t st);
+                      const T* Wf, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext, cudaStream_t st);
 // RA with the fields staged through shared memory (same arithmetic as launch_ra).
 template <class T>
 cudaError_t launch_ra_tiled(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid,
-                            const T* Qf, const T* Wf, const double* Q64, double* out, double* Qs, T* Wnext,
+                            const T* Qf, const T* Wf, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext,
                             cudaStream_t st);
 template <class T>
 cudaError_t launch_ss_grad(const Grid& g, const Coef<T>& k, const T* Wf, T* Gw, cudaStream_t st);
 template <class T>
 cudaError_t launch_ss(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid, const T* Qf,
-                      const T* Wf, const T* Gw, const double* Q64, double* out, double* Qs, T* Wnext,
+                      const T* Wf, const T* Gw, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext,
                       cudaStream_t st);
 template <class T>
 cudaError_t launch_bl_prod(const Grid& g, const T* Qf, const T* Wf, T* P, cudaStream_t st);
@@ -50,7 +55,7 @@ template <class T>
 cudaError_t launch_bl_d2(const Grid& g, const T* Wf, const T* D1, T* D2, cudaStream_t st);
 template <class T>
 cudaError_t launch_bl_res(const Grid& g, const Phys& ph, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
-                          const T* D1, const T* D2, const double* Q64, double* out, double* Qs, T* Wnext,
+                          const T* D1, const T* D2, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext,
                           cudaStream_t st);
 // ---- batched path ----------------------------------------------------------
 // One instance of a batch as the kernels see it (device memory, read per tile).

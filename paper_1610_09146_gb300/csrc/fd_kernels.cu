@@ -29,6 +29,10 @@ template <class T>
 __device__ __forceinline__ T ld(const T* __restrict__ p, int i) {
     return __ldg(p + i);
 }
+__device__ __forceinline__ df64 ld(const df64* __restrict__ p, int i) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p + i));
+    return df64(v.x, v.y);
+}
 
 __device__ __forceinline__ int grid_index() { return blockIdx.x * blockDim.x + threadIdx.x; }
 
@@ -42,6 +46,10 @@ template <>
 __device__ __forceinline__ float s1<float>(const Grid& g, int a) {
     return g.inv12hf[a];
 }
+template <>
+__device__ __forceinline__ df64 s1<df64>(const Grid& g, int a) {
+    return g.inv12h_w[a];
+}
 template <class T>
 __device__ __forceinline__ T s2(const Grid& g, int a);
 template <>
@@ -51,6 +59,10 @@ __device__ __forceinline__ double s2<double>(const Grid& g, int a) {
 template <>
 __device__ __forceinline__ float s2<float>(const Grid& g, int a) {
     return g.inv12h2f[a];
+}
+template <>
+__device__ __forceinline__ df64 s2<df64>(const Grid& g, int a) {
+    return g.inv12h2_w[a];
 }
 
 // Constants that restore the mean-field terms removed by the shift (see
@@ -69,6 +81,33 @@ template <>
 __device__ __forceinline__ Shift<float> shift_of<float>(const Phys& ph) {
     return {1.0f, (float)(ph.rhoE0 + ph.p0)};
 }
+template <>
+__device__ __forceinline__ Shift<df64> shift_of<df64>(const Phys& ph) {
+    return {df64(1.0f, 0.0f), ph.cE_w};
+}
+
+// nu and kappa in the working precision.
+__device__ __forceinline__ void visc_consts(const Phys& ph, double& nu, double& ka) {
+    nu = ph.nu;
+    ka = ph.kappa;
+}
+__device__ __forceinline__ void visc_consts(const Phys& ph, float& nu, float& ka) {
+    nu = (float)ph.nu;
+    ka = (float)ph.kappa;
+}
+__device__ __forceinline__ void visc_consts(const Phys& ph, df64& nu, df64& ka) {
+    nu = ph.nu_w;
+    ka = ph.kappa_w;
+}
+
+// The stage's residual in the state precision, and the RK constants in it.
+__device__ __forceinline__ double to_state(double r) { return r; }
+__device__ __forceinline__ double to_state(float r) { return (double)r; }
+__device__ __forceinline__ df64 to_state(df64 r) { return r; }
+__device__ __forceinline__ double rk_a(const RKStage& rk, double) { return rk.adt; }
+__device__ __forceinline__ df64 rk_a(const RKStage& rk, df64) { return rk.adt_w; }
+__device__ __forceinline__ double rk_b(const RKStage& rk, double) { return rk.bdt; }
+__device__ __forceinline__ df64 rk_b(const RKStage& rk, df64) { return rk.bdt_w; }
 
 }  // namespace
 
@@ -138,14 +177,37 @@ __device__ __forceinline__ void prims_point(const Phys& ph, const double q[5], f
     F[9 * n + c] = Tp;
 }
 
+// Double-word perturbation fields from the double-word state, which is itself
+// stored shifted (q0 = rho - 1, q4 = rho E - rhoE0): the binary32 formulas
+// above in double-word arithmetic (1/rho by one Newton step).
+__device__ __forceinline__ void prims_point(const Phys& ph, const df64 q[5], df64* __restrict__ F, int n, int c) {
+    const df64 rp = q[0];
+    const df64 Ep = q[4];
+    const df64 inv = recip(q[0] + df64(1.0f, 0.0f));
+    const df64 u = q[1] * inv, v = q[2] * inv, w = q[3] * inv;
+    const df64 pp = ph.gm1_w * fmx(df64(-0.5f, 0.0f), fmx(q[1], u, fmx(q[2], v, q[3] * w)), Ep);
+    const df64 Tp = fmx(ph.gM2_w, pp, -rp) * inv;
+    F[c] = rp;
+    F[n + c] = q[1];
+    F[2 * n + c] = q[2];
+    F[3 * n + c] = q[3];
+    F[4 * n + c] = Ep;
+    F[5 * n + c] = u;
+    F[6 * n + c] = v;
+    F[7 * n + c] = w;
+    F[8 * n + c] = pp;
+    F[9 * n + c] = Tp;
+}
+
 // Primitives of the whole state (at creation, after fd_set_state, or when
 // no stage has produced them yet).
 template <class T>
-__global__ void __launch_bounds__(256) k_prims(Grid g, Phys ph, const double* __restrict__ Q, T* __restrict__ W) {
+__global__ void __launch_bounds__(256) k_prims(Grid g, Phys ph, const state_t<T>* __restrict__ Q,
+                                               T* __restrict__ W) {
     int idx = grid_index();
     if (idx >= g.n) return;
     const int n = g.n;
-    double q[5];
+    state_t<T> q[5];
 #pragma unroll
     for (int f = 0; f < 5; ++f) q[f] = Q[f * n + idx];
     prims_point(ph, q, W, n, idx);
@@ -153,42 +215,43 @@ __global__ void __launch_bounds__(256) k_prims(Grid g, Phys ph, const double* __
 
 // RK update from a preloaded saved register qs (Q_in at stage 0, else Qs):
 // the same arithmetic as the update branch of stage_write below.
-template <class T>
-__device__ __forceinline__ void stage_update(const RKStage& rk, const Phys& ph, int n, int c, const double qs[5],
-                                             const T R[5], double* __restrict__ out, double* __restrict__ Qs,
+template <class T, class S = state_t<T>>
+__device__ __forceinline__ void stage_update(const RKStage& rk, const Phys& ph, int n, int c, const S qs[5],
+                                             const T R[5], S* __restrict__ out, S* __restrict__ Qs,
                                              T* __restrict__ Wnext) {
-    double qn[5];
+    S qn[5];
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
-        const double r = (double)R[f];
-        qn[f] = fmx(rk.adt, r, qs[f]);
+        const S r = to_state(R[f]);
+        qn[f] = fmx(rk_a(rk, S()), r, qs[f]);
         out[f * n + c] = qn[f];
-        if (rk.stage < 2) Qs[f * n + c] = fmx(rk.bdt, r, qs[f]);
+        if (rk.stage < 2) Qs[f * n + c] = fmx(rk_b(rk, S()), r, qs[f]);
     }
     prims_point(ph, qn, Wnext, n, c);
 }
 
 // Final write of a stage: the residual itself (fd_residual), or the
-// two-register RK update (Fig. 1, advance-solution-in-time) in binary64,
+// two-register RK update (Fig. 1, advance-solution-in-time) in the state
+// precision (binary64, or double-word in the df64 mode),
 //   Q_out = Qs + a dt R,  Qs <- Qs + b dt R,  with Qs = Q_in at stage 0 (save-state),
 // followed by the primitives of Q_out for the next stage (evaluate-u_i,p,T of
 // Fig. 1 moved to the end of the previous stage: it is pointwise, so the point
 // that produces Q_out can produce them without another pass over memory).
-template <class T, bool RESID>
+template <class T, bool RESID, class S = state_t<T>>
 __device__ __forceinline__ void stage_write(const RKStage& rk, const Phys& ph, int n, int c,
-                                            const double* __restrict__ Q64, const T R[5], double* __restrict__ out,
-                                            double* __restrict__ Qs, T* __restrict__ Wnext) {
-    double qn[5];
+                                            const S* __restrict__ Q64, const T R[5], S* __restrict__ out,
+                                            S* __restrict__ Qs, T* __restrict__ Wnext) {
+    S qn[5];
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
-        double r = (double)R[f];
+        const S r = to_state(R[f]);
         if (RESID) {
             out[f * n + c] = r;
         } else {
-            double qs = rk.stage == 0 ? Q64[f * n + c] : Qs[f * n + c];
-            qn[f] = fmx(rk.adt, r, qs);
+            const S qs = rk.stage == 0 ? Q64[f * n + c] : Qs[f * n + c];
+            qn[f] = fmx(rk_a(rk, S()), r, qs);
             out[f * n + c] = qn[f];
-            if (rk.stage < 2) Qs[f * n + c] = fmx(rk.bdt, r, qs);
+            if (rk.stage < 2) Qs[f * n + c] = fmx(rk_b(rk, S()), r, qs);
         }
     }
     if (!RESID) prims_point(ph, qn, Wnext, n, c);
@@ -364,8 +427,8 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
 // evaluated from its finite-difference formula at the point of use.
 template <class T, bool RESID>
 __global__ void __launch_bounds__(128) k_ra(Grid g, Coef<T> k, Phys ph, RKStage rk, const T* __restrict__ Qf,
-                                            const T* __restrict__ Wf, const double* __restrict__ Q64,
-                                            double* __restrict__ out, double* __restrict__ Qs,
+                                            const T* __restrict__ Wf, const state_t<T>* __restrict__ Q64,
+                                            state_t<T>* __restrict__ out, state_t<T>* __restrict__ Qs,
                                             T* __restrict__ Wnext) {
     int idx = grid_index();
     if (idx >= g.n) return;
@@ -417,8 +480,8 @@ struct SmemAcc {
 template <class T, bool RESID>
 __device__ __forceinline__ void ra_tiled_block(T* sm, const Grid& g, const Coef<T>& k, const Phys& ph,
                                                const RKStage& rk, const T* __restrict__ Qf,
-                                               const T* __restrict__ Wf, const double* __restrict__ Q64,
-                                               double* __restrict__ out, double* __restrict__ Qs,
+                                               const T* __restrict__ Wf, const state_t<T>* __restrict__ Q64,
+                                               state_t<T>* __restrict__ out, state_t<T>* __restrict__ Qs,
                                                T* __restrict__ Wnext, int x0, int y0, int zbeg) {
     const int tid = threadIdx.x;
     const int tx = tid % kTX, ty = tid / kTX;
@@ -454,9 +517,9 @@ __device__ __forceinline__ void ra_tiled_block(T* sm, const Grid& g, const Coef<
     for (int z = zbeg; z < zend; ++z) {
         const int r0 = z - zbeg;  // ring slot of plane z + dz is (r0 + dz + 2) % 5
         const int c = (z * ny + y) * nx + x;
-        double qs[5];
+        state_t<T> qs[5];
         if (!RESID && inside) {
-            const double* src = rk.stage == 0 ? Q64 : Qs;
+            const state_t<T>* src = rk.stage == 0 ? Q64 : Qs;
 #pragma unroll
             for (int f = 0; f < 5; ++f) qs[f] = src[(size_t)f * n + c];
         }
@@ -469,7 +532,7 @@ __device__ __forceinline__ void ra_tiled_block(T* sm, const Grid& g, const Coef<
             fused_residual<T, false>(A, k, R);
             if (RESID) {
 #pragma unroll
-                for (int f = 0; f < 5; ++f) out[(size_t)f * n + c] = (double)R[f];
+                for (int f = 0; f < 5; ++f) out[(size_t)f * n + c] = to_state(R[f]);
             } else {
                 stage_update(rk, ph, n, c, qs, R, out, Qs, Wnext);
             }
@@ -481,7 +544,7 @@ __device__ __forceinline__ void ra_tiled_block(T* sm, const Grid& g, const Coef<
 template <class T, bool RESID>
 __global__ void __launch_bounds__(kTX* kTY, sizeof(T) == 4 ? 2 : 1)
     k_ra_tiled(Grid g, Coef<T> k, Phys ph, RKStage rk, const T* __restrict__ Qf, const T* __restrict__ Wf,
-               const double* __restrict__ Q64, double* __restrict__ out, double* __restrict__ Qs,
+               const state_t<T>* __restrict__ Q64, state_t<T>* __restrict__ out, state_t<T>* __restrict__ Qs,
                T* __restrict__ Wnext) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ra_tiled_block<T, RESID>(reinterpret_cast<T*>(smem_raw), g, k, ph, rk, Qf, Wf, Q64, out, Qs, Wnext,
@@ -512,8 +575,8 @@ __global__ void __launch_bounds__(256) k_ss_grad(Grid g, Coef<T> k, const T* __r
 template <class T, bool RESID>
 __global__ void __launch_bounds__(128) k_ss(Grid g, Coef<T> k, Phys ph, RKStage rk, const T* __restrict__ Qf,
                                             const T* __restrict__ Wf, const T* __restrict__ Gw,
-                                            const double* __restrict__ Q64, double* __restrict__ out,
-                                            double* __restrict__ Qs, T* __restrict__ Wnext) {
+                                            const state_t<T>* __restrict__ Q64, state_t<T>* __restrict__ out,
+                                            state_t<T>* __restrict__ Qs, T* __restrict__ Wnext) {
     int idx = grid_index();
     if (idx >= g.n) return;
     const Nbr s = make_nbr(g, idx);
@@ -610,8 +673,8 @@ __global__ void __launch_bounds__(256) k_bl_d2(Grid g, const T* __restrict__ Wf,
 template <class T, bool RESID>
 __global__ void __launch_bounds__(256) k_bl_res(Grid g, Phys ph, RKStage rk, const T* __restrict__ Qf,
                                                 const T* __restrict__ Wf, const T* __restrict__ D1,
-                                                const T* __restrict__ D2, const double* __restrict__ Q64,
-                                                double* __restrict__ out, double* __restrict__ Qs,
+                                                const T* __restrict__ D2, const state_t<T>* __restrict__ Q64,
+                                                state_t<T>* __restrict__ out, state_t<T>* __restrict__ Qs,
                                                 T* __restrict__ Wnext) {
     int idx = grid_index();
     if (idx >= g.n) return;
@@ -654,8 +717,10 @@ __global__ void __launch_bounds__(256) k_bl_res(Grid g, Phys ph, RKStage rk, con
     }
     t.lapT = D2[9 * n + c] + D2[10 * n + c] + D2[11 * n + c];
     const Shift<T> sh = shift_of<T>(ph);
+    T nu, ka;
+    visc_consts(ph, nu, ka);
     T R[5];
-    assemble<T>(t, q, uc, (T)ph.nu, (T)ph.kappa, sh.c_rho, sh.c_E, R);
+    assemble<T>(t, q, uc, nu, ka, sh.c_rho, sh.c_E, R);
     stage_write<T, RESID>(rk, ph, n, c, Q64, R, out, Qs, Wnext);
 }
 
@@ -955,9 +1020,37 @@ cudaError_t launch_prims_f32(const Grid& g, const Phys& ph, const double* Q, flo
     return cudaGetLastError();
 }
 
+cudaError_t launch_prims_df64(const Grid& g, const Phys& ph, const df64* Q, df64* F, cudaStream_t st) {
+    k_prims<df64><<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, Q, F);
+    return cudaGetLastError();
+}
+
+// binary64 <-> double-word conversion of 5 arrays of n values (API boundary of
+// the df64 mode).  The double-word state is kept shifted, Q - shift with
+// shift = (1, 0, 0, 0, rhoE0) for the state, so its 48 bits resolve the
+// perturbations rather than the means; the shift is applied in binary64.
+__global__ void k_to_df64(const double* __restrict__ src, df64* __restrict__ dst, long long n, Shift5 sh) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 5 * n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = df64(src[i] - sh.s[i / n]);
+}
+__global__ void k_from_df64(const df64* __restrict__ src, double* __restrict__ dst, long long n, Shift5 sh) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 5 * n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i].to_double() + sh.s[i / n];
+}
+cudaError_t launch_to_df64(const double* src, df64* dst, long long n, const Shift5& sh, cudaStream_t st) {
+    k_to_df64<<<kDiagBlocks, 256, 0, st>>>(src, dst, n, sh);
+    return cudaGetLastError();
+}
+cudaError_t launch_from_df64(const df64* src, double* dst, long long n, const Shift5& sh, cudaStream_t st) {
+    k_from_df64<<<kDiagBlocks, 256, 0, st>>>(src, dst, n, sh);
+    return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid, const T* Qf,
-                      const T* Wf, const double* Q64, double* out, double* Qs, T* Wnext, cudaStream_t st) {
+                      const T* Wf, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext, cudaStream_t st) {
     if (resid)
         k_ra<T, true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Qf, Wf, Q64, out, Qs, Wnext);
     else
@@ -967,7 +1060,7 @@ cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const Phys& ph, const RKS
 
 template <class T>
 cudaError_t launch_ra_tiled(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid,
-                            const T* Qf, const T* Wf, const double* Q64, double* out, double* Qs, T* Wnext,
+                            const T* Qf, const T* Wf, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext,
                             cudaStream_t st) {
     const size_t smem = tiled_smem_bytes<T>();
     dim3 grid((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, (g.nz + kZChunk - 1) / kZChunk);
@@ -994,7 +1087,7 @@ cudaError_t launch_ss_grad(const Grid& g, const Coef<T>& k, const T* Wf, T* Gw, 
 
 template <class T>
 cudaError_t launch_ss(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid, const T* Qf,
-                      const T* Wf, const T* Gw, const double* Q64, double* out, double* Qs, T* Wnext,
+                      const T* Wf, const T* Gw, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext,
                       cudaStream_t st) {
     if (resid)
         k_ss<T, true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
@@ -1023,7 +1116,7 @@ cudaError_t launch_bl_d2(const Grid& g, const T* Wf, const T* D1, T* D2, cudaStr
 
 template <class T>
 cudaError_t launch_bl_res(const Grid& g, const Phys& ph, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
-                          const T* D1, const T* D2, const double* Q64, double* out, double* Qs, T* Wnext,
+                          const T* D1, const T* D2, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext,
                           cudaStream_t st) {
     if (resid)
         k_bl_res<T, true><<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, rk, Qf, Wf, D1, D2, Q64, out, Qs, Wnext);
@@ -1034,21 +1127,27 @@ cudaError_t launch_bl_res(const Grid& g, const Phys& ph, const RKStage& rk, bool
 
 #define FD_INSTANTIATE(T)                                                                                        \
     template cudaError_t launch_ra<T>(const Grid&, const Coef<T>&, const Phys&, const RKStage&, bool, const T*,  \
-                                      const T*, const double*, double*, double*, T*, cudaStream_t);             \
-    template cudaError_t launch_ra_tiled<T>(const Grid&, const Coef<T>&, const Phys&, const RKStage&, bool,      \
-                                            const T*, const T*, const double*, double*, double*, T*,            \
-                                            cudaStream_t);                                                      \
+                                      const T*, const state_t<T>*, state_t<T>*, state_t<T>*, T*, cudaStream_t); \
     template cudaError_t launch_ss_grad<T>(const Grid&, const Coef<T>&, const T*, T*, cudaStream_t);            \
     template cudaError_t launch_ss<T>(const Grid&, const Coef<T>&, const Phys&, const RKStage&, bool, const T*,  \
-                                      const T*, const T*, const double*, double*, double*, T*, cudaStream_t);   \
+                                      const T*, const T*, const state_t<T>*, state_t<T>*, state_t<T>*, T*,      \
+                                      cudaStream_t);                                                            \
     template cudaError_t launch_bl_prod<T>(const Grid&, const T*, const T*, T*, cudaStream_t);                  \
     template cudaError_t launch_bl_d1<T>(const Grid&, const T*, const T*, const T*, T*, cudaStream_t);          \
     template cudaError_t launch_bl_d2<T>(const Grid&, const T*, const T*, T*, cudaStream_t);                    \
     template cudaError_t launch_bl_res<T>(const Grid&, const Phys&, const RKStage&, bool, const T*, const T*,    \
-                                          const T*, const T*, const double*, double*, double*, T*, cudaStream_t);
+                                          const T*, const T*, const state_t<T>*, state_t<T>*, state_t<T>*, T*,  \
+                                          cudaStream_t);
 FD_INSTANTIATE(double)
 FD_INSTANTIATE(float)
+FD_INSTANTIATE(df64)
 #undef FD_INSTANTIATE
+template cudaError_t launch_ra_tiled<double>(const Grid&, const Coef<double>&, const Phys&, const RKStage&, bool,
+                                             const double*, const double*, const double*, double*, double*, double*,
+                                             cudaStream_t);
+template cudaError_t launch_ra_tiled<float>(const Grid&, const Coef<float>&, const Phys&, const RKStage&, bool,
+                                            const float*, const float*, const double*, double*, double*, float*,
+                                            cudaStream_t);
 
 cudaError_t launch_diagnostics_f64(const Grid& g, const double* Q, double* Wv, double* partial, double* out,
                                    cudaStream_t st) {
