@@ -149,6 +149,18 @@ __device__ __forceinline__ T delta2_taps(const T t[4], T f0) {
     return fmx(T(-30), f0, fmx(T(16), t[2] + t[1], -(t[3] + t[0])));
 }
 
+// Double-word forms of the three stencil helpers: the weights 8 and 16 scale
+// exactly (powers of two), 30 through a double-word x binary32 product.
+__device__ __forceinline__ df64 delta1_prod(const df64 a[4], const df64 b[4]) {
+    df64 x = a[2] * b[2] - a[1] * b[1];
+    df64 y = a[3] * b[3] - a[0] * b[0];
+    return scale2(x, 8.0f) - y;
+}
+__device__ __forceinline__ df64 delta1_taps(const df64 t[4]) { return scale2(t[2] - t[1], 8.0f) + (t[0] - t[3]); }
+__device__ __forceinline__ df64 delta2_taps(const df64 t[4], df64 f0) {
+    return (scale2(t[2] + t[1], 16.0f) - (t[3] + t[0])) - times_fp(f0, 30.0f);
+}
+
 // Coefficients of the fused residual (RA and SS), precomputed on the host so
 // that every derivative enters the residual through one multiply-add:
 //   c1[j]      = -1/2 / (12 h_j)      skew convective sums (Eq. skewscalar)

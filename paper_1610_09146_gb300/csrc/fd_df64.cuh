@@ -6,11 +6,15 @@
 //   TwoSum      (Knuth 1969):  s + e = a + b exactly, any a, b;
 //   FastTwoSum  (Dekker 1971): s + e = a + b exactly, |a| >= |b|;
 //   TwoProd     (with FMA):    p + e = a * b exactly;
-// and the double-word algorithms analysed by Joldes, Muller and Popescu,
-// "Tight and rigorous error bounds for basic building blocks of double-word
-// arithmetic" (ACM TOMS 44, 2017): AccurateDWPlusDW (relative error below
-// 3u^2, u = 2^-24, also under cancellation) for sums and DWTimesDW with FMA
-// (below 5u^2) for products.
+// and double-word algorithms analysed by Joldes, Muller and Popescu, "Tight
+// and rigorous error bounds for basic building blocks of double-word
+// arithmetic" (ACM TOMS 44, 2017):
+//   sums      SloppyDWPlusDW: error below about 2u^2 (|x| + |y|), u = 2^-24,
+//             the size of the operands' own 48-bit representation error, which
+//             is what the stencil differences need (the accurate variant also
+//             bounds the error relative to a cancelled result, at twice the cost);
+//   products  DWTimesDW with FMA (relative error below 5u^2), DWTimesFP with
+//             FMA for a binary32 factor, and exact scaling by powers of two.
 //
 // Every step must be evaluated exactly as written: the library is compiled
 // with -fmad=false and without fast-math, so no multiply-add is contracted and
@@ -44,14 +48,12 @@ __device__ __forceinline__ df64 fast_two_sum(float a, float b) {
     return df64(s, e);
 }
 
-// AccurateDWPlusDW
+// SloppyDWPlusDW
 __device__ __forceinline__ df64 operator+(df64 x, df64 y) {
     df64 s = two_sum(x.hi, y.hi);
-    df64 t = two_sum(x.lo, y.lo);
-    float c = __fadd_rn(s.lo, t.hi);
-    df64 v = fast_two_sum(s.hi, c);
-    float w = __fadd_rn(t.lo, v.lo);
-    return fast_two_sum(v.hi, w);
+    float v = __fadd_rn(x.lo, y.lo);
+    float w = __fadd_rn(s.lo, v);
+    return fast_two_sum(s.hi, w);
 }
 
 __device__ __forceinline__ df64 operator-(df64 x) { return df64(-x.hi, -x.lo); }
@@ -68,6 +70,17 @@ __device__ __forceinline__ df64 operator*(df64 x, df64 y) {
     float cl3 = __fadd_rn(cl1, cl2);
     return fast_two_sum(ch, cl3);
 }
+
+// DWTimesFP with FMA
+__device__ __forceinline__ df64 times_fp(df64 x, float y) {
+    float ch = __fmul_rn(x.hi, y);
+    float cl1 = __fmaf_rn(x.hi, y, -ch);
+    float cl3 = __fmaf_rn(x.lo, y, cl1);
+    return fast_two_sum(ch, cl3);
+}
+
+// x * p for a power of two p: exact, word by word.
+__device__ __forceinline__ df64 scale2(df64 x, float p) { return df64(__fmul_rn(x.hi, p), __fmul_rn(x.lo, p)); }
 
 __device__ __forceinline__ bool operator!=(df64 x, df64 y) { return x.hi != y.hi || x.lo != y.lo; }
 
