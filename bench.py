@@ -72,6 +72,16 @@ COST = {
     ("f32", "store_all", "deriv2"): (114, 100, 0),
     ("f32", "store_all", "products"): (18, 108, 0),
     ("f32", "*", "prims"): (14, 80, 2),
+    # df64: the binary64 algorithm's flops, done in double-word arithmetic on the binary32
+    # pipe (no FP64 instructions); state and fields are 8-byte double-words
+    ("df64", "store_some", "fused"): (409.7, 338.7, 0),
+    ("df64", "store_some", "grad"): (45, 96, 0),
+    ("df64", "recompute_all", "fused"): (556.7, 266.7, 0),
+    ("df64", "store_all", "fused"): (177, 781.3, 0),
+    ("df64", "store_all", "deriv1"): (225, 576, 0),
+    ("df64", "store_all", "deriv2"): (114, 200, 0),
+    ("df64", "store_all", "products"): (18, 216, 0),
+    ("df64", "*", "prims"): (14, 120, 0),
 }
 # FP64 pipe issue peak: 2 instructions per SM per clock.
 FP64_PEAK_INSTR = 152 * 2 * 2.07e9
@@ -201,7 +211,7 @@ def roofline_of(dtype, alg, kern, n, hbm_peak, hbm_src):
     sec = k["ms_avg"] / 1e3
     gbs = bytes_pt * n / sec / 1e9
     tflops = flops_pt * n / sec / 1e12
-    if dtype == "f64":
+    if dtype in ("f64", "df64"):
         entry = {"kernel": f"{SHORT[alg]}:{name}", "bound": "alu", "achieved": round(tflops, 4),
                  "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
                  "peak_source": "FP64 nominal: 152 SMs x 4 flop/clk x 2.07 GHz",
@@ -302,6 +312,21 @@ def run_ours(args):
             keep = s
         else:
             s.close()
+    # binary64-accurate double-word families (FD_DF64): reported beside the binary64 line
+    df64 = {}
+    if args.dtype == "f64" and not args.no_df64:
+        for alg in args.variants:
+            s, ms, kern, finite, diag = time_family(fd, torch, alg, "df64", n, args.steps, args.warmup, stream,
+                                                    barrier, clocks)
+            s.close()
+            value, ms = aggregate_over_ranks(ms, npts, args.steps, dist, "cuda")
+            name, k = max(kern.items(), key=lambda kv: kv[1]["ms_total"])
+            flops_pt = cost_of("f64", alg, name)[0]
+            eq = flops_pt * npts / (k["ms_avg"] / 1e3) / 1e12
+            df64[SHORT[alg]] = {"value": value, "ms_per_step": ms / args.steps, "finite": finite,
+                                "dominant_kernel": name, "kernels": {kk: round(vv["ms_avg"], 4) for kk, vv in kern.items()},
+                                "binary64_equivalent_tflops": round(eq, 4),
+                                "vs_fp64_peak": round(eq / FP64_PEAK_TFLOPS, 4), "ke": diag[0]}
     cl = clocks.stop()
     e2e = e2e_run(fd, torch, keep, n, max(3, min(args.steps, 10)), stream.cuda_stream)
     e2e["value"], _ = aggregate_over_ranks(1e3 * npts * e2e["steps"] / e2e["value"], npts, e2e["steps"], dist,
@@ -323,6 +348,9 @@ def run_ours(args):
         "variants": {SHORT[a]: {k: v for k, v in results[a].items() if k != "kernels"} | {
             "kernels": {kk: round(vv["ms_avg"], 4) for kk, vv in results[a]["kernels"].items()}}
             for a in results},
+        "variants_df64": df64,
+        "variants_df64_note": "dtype df64: double-word arithmetic on the binary32 pipe, parity 1e-12 vs the "
+                              "binary64 oracle; binary64_equivalent_tflops counts the binary64 algorithm's flops",
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_full(n)
@@ -604,9 +632,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--grid", type=int, default=N_GRID)
-    ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--dtype", choices=["f64", "f32", "df64"], default="f64")
     ap.add_argument("--variants", nargs="+", default=VARIANTS, choices=VARIANTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-df64", action="store_true", help="skip the double-word (df64) families")
     ap.add_argument("--workload", choices=["single", "batched", "serve", "mixed512"], default="single",
                     help="single: the 256^3 line (default); batched / serve / mixed512: the ensemble, "
                          "serving and 512^3 mixed-precision runs")
