@@ -415,7 +415,7 @@ def run_batched(args):
         "workload": f"batched ensemble: {len(specs)} Taylor-Green solves, grids {{32,48,64,96,128}}^3, "
                     f"Re U[400,3200], Mach U[0.1,0.4], {steps} RK3 steps, seed 1610",
         "metric": "solves/s", "value": len(specs) / tb, "unit": "solves/s", "higher_is_better": True,
-        "dtype": "f32 stencils / f64 accumulation",
+        "dtype": "f32 stencils / compensated-f32 (double-word) accumulation",
         "seconds": tb, "point_updates_per_s": pts * steps / tb,
         "fp64_loop": {"solves_per_s": len(specs) / tl, "seconds": tl, "family": "store_some"},
         "fp64_batched": {"solves_per_s": len(specs) / t64b, "seconds": t64b,
@@ -496,7 +496,7 @@ def run_mixed512(args):
         }
         del r
     line = {
-        "workload": f"Taylor-Green {n}^3, binary32 stencils / binary64 RK accumulation and reductions, "
+        "workload": f"Taylor-Green {n}^3, binary32 stencils / compensated binary32 (double-word) RK accumulation, binary64 reductions, "
                     f"{steps} RK3 steps, vs the binary64 GPU run",
         "metric": METRIC, "unit": METRIC, "higher_is_better": True, "grid": [n, n, n], "dt": dt,
         "value": max(v["point_updates_per_s"] for v in res.values()),

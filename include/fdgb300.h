@@ -60,22 +60,26 @@ extern "C" {
 /* ---- arithmetic ----------------------------------------------------------
  * FD_F64        all arithmetic in IEEE binary64 (the paper's precision,
  *               Section 3).
- * FD_F32_ACC64  stencils, fluxes and the residual in binary32 on
+ * FD_F32_ACCDW  stencils, fluxes and the residual in binary32 on
  *               perturbation variables (rho-1, p-p0, T-1, rhoE-rhoE0); the
- *               conserved state, the Runge-Kutta accumulation and the kinetic
- *               energy / enstrophy reductions stay in binary64.  The paper has
- *               no counterpart; it is a precision mode of this library.
+ *               conserved state and the Runge-Kutta accumulation are kept in
+ *               compensated binary32 (double-words of FD_DF64, about 48
+ *               significant bits, shifted by (1, 0, 0, 0, rhoE0)), so a step
+ *               issues no binary64 instruction; states cross the API as
+ *               binary64 and the kinetic energy / enstrophy reductions run in
+ *               binary64.  The paper has no counterpart; it is a precision
+ *               mode of this library.
  * FD_DF64       binary64-accurate results without binary64 instructions: the
  *               stencils, fluxes, residual, RK accumulation and the stored
  *               state use double-word ("double-float") arithmetic, pairs of
  *               binary32 numbers with about 48 significant bits (Knuth
  *               TwoSum, Dekker FastTwoSum, FMA-based products; the algorithms
  *               of Joldes, Muller & Popescu 2017), on the shifted fields of
- *               FD_F32_ACC64.  On GB300 binary32 issues 64x faster than
+ *               FD_F32_ACCDW.  On GB300 binary32 issues 64x faster than
  *               binary64.  States cross the API as binary64; the reductions
  *               run in binary64.  No counterpart in the paper. */
 #define FD_F64 0
-#define FD_F32_ACC64 1
+#define FD_F32_ACCDW 1
 #define FD_DF64 2
 
 /* Device allocator callbacks (for example PyTorch's caching allocator).
@@ -99,7 +103,7 @@ typedef struct fd_handle fd_handle;
  *   Re, Mach, Pr, gamma  flow constants (Eqs. 4-7): Re, Mach, Pr > 0,
  *               gamma > 1; dt > 0 is the time step of every fd_step;
  *   algorithm   FD_STORE_ALL, FD_STORE_SOME or FD_RECOMPUTE_ALL;
- *   dtype       FD_F64, FD_F32_ACC64 or FD_DF64;
+ *   dtype       FD_F64, FD_F32_ACCDW or FD_DF64;
  *   alloc       NULL for cudaMalloc/cudaFree, else allocator callbacks;
  *   cuda_stream cudaStream_t for all work of this handle (NULL = default).
  * On success *out receives the handle.  Errors: FD_EINVAL, FD_ENOMEM,
@@ -195,7 +199,7 @@ typedef struct fd_instance_desc {
 typedef struct fd_batch fd_batch;
 
 /* Create `count` >= 1 instances described by desc[0..count-1], all in one
- * dtype (FD_F64 or FD_F32_ACC64), each set to its Taylor-Green initial state.
+ * dtype (FD_F64 or FD_F32_ACCDW), each set to its Taylor-Green initial state.
  * One device allocation holds every instance (through alloc, else
  * cudaMalloc).  Errors: FD_EINVAL (a bad descriptor; FD_STORE_ALL is not
  * batched), FD_ENOMEM, FD_ECUDA; the message is in fd_batch_last_error(NULL). */
@@ -245,7 +249,7 @@ typedef struct fd_request {
     int nx, ny, nz;                  /* grid, as for fd_create */
     double Re, Mach, Pr, gamma, dt;  /* as for fd_create */
     int steps;                       /* RK3 steps to run, >= 1 */
-    int dtype;                       /* FD_F64 or FD_F32_ACC64 */
+    int dtype;                       /* FD_F64 or FD_F32_ACCDW */
     int algorithm;                   /* FD_STORE_SOME or FD_RECOMPUTE_ALL */
     int tile_points;                 /* as in fd_instance_desc */
     long long tag;                   /* caller's identifier, returned with the result */

@@ -123,7 +123,7 @@ int check_args(int nx, int ny, int nz, double Re, double Mach, double Pr, double
         return fail_global(FD_EINVAL, "fd_create: grid %dx%dx%d: %s", nx, ny, nz, why);
     if (algorithm != FD_STORE_ALL && algorithm != FD_STORE_SOME && algorithm != FD_RECOMPUTE_ALL)
         return fail_global(FD_EINVAL, "unknown algorithm %d", algorithm);
-    if (dtype != FD_F64 && dtype != FD_F32_ACC64 && dtype != FD_DF64)
+    if (dtype != FD_F64 && dtype != FD_F32_ACCDW && dtype != FD_DF64)
         return fail_global(FD_EINVAL, "unknown dtype %d", dtype);
     return FD_OK;
 }
@@ -217,7 +217,8 @@ cudaError_t stage_kernels(fd_handle* h, const fd::RKStage& rk, bool resid, const
             // issue, where staging does not help.
             return timed(h, FD_KERNEL_FUSED, [&] {
                 if constexpr (std::is_same<T, float>::value)
-                    return fd::launch_ra_tiled<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, h->Qs, Wnext, st);
+                    return fd::launch_ra_tiled<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, reinterpret_cast<S*>(h->Qs),
+                                                  Wnext, st);
                 else
                     return fd::launch_ra<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, reinterpret_cast<S*>(h->Qs),
                                             Wnext, st);
@@ -277,19 +278,23 @@ cudaError_t run_stage(fd_handle* h, int s, bool resid, double* out) {
                                    reinterpret_cast<df64*>(h->D1), reinterpret_cast<df64*>(h->D2), Qd,
                                    reinterpret_cast<df64*>(Qout), resid ? nullptr : h->Wd[1 - wc]);
     }
+    using fd::df64;
+    const df64* Qd = reinterpret_cast<const df64*>(Qin);
     if (!h->wvalid) {
-        e = timed(h, FD_KERNEL_PRIMS, [&] { return fd::launch_prims_f32(g, ph, Qin, h->Wf[wc], h->stream); });
+        e = timed(h, FD_KERNEL_PRIMS, [&] { return fd::launch_prims_f32(g, ph, Qd, h->Wf[wc], h->stream); });
         if (e != cudaSuccess) return e;
         h->wvalid = true;
     }
     return stage_kernels<float>(h, rk, resid, h->Wf[wc], h->Wf[wc] + 5 * n, h->Gf, reinterpret_cast<float*>(h->P),
-                                reinterpret_cast<float*>(h->D1), reinterpret_cast<float*>(h->D2), Qin, Qout,
-                                resid ? nullptr : h->Wf[1 - wc]);
+                                reinterpret_cast<float*>(h->D1), reinterpret_cast<float*>(h->D2), Qd,
+                                reinterpret_cast<df64*>(Qout), resid ? nullptr : h->Wf[1 - wc]);
 }
 
-// df64 mode: the state buffers hold double-words; these move a binary64 copy
-// of the current state through the saved register Qs, which is dead between
-// steps (stage 0 rewrites it).
+// binary32 and df64 modes: the state buffers hold shifted double-words; these
+// move a binary64 copy of the current state through the saved register Qs,
+// which is dead between steps (stage 0 rewrites it).
+bool dw_state(int dtype) { return dtype != FD_F64; }
+
 fd::Shift5 state_shift(const fd_handle* h) { return fd::Shift5{{1.0, 0.0, 0.0, 0.0, h->phys.rhoE0}}; }
 
 cudaError_t state_to_binary64(fd_handle* h, double* dst) {
@@ -385,7 +390,7 @@ int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, d
     h->kf = fd::make_coef<float>(g, ph, true);
     h->kw = fd::make_coef<fd::df64>(g, ph, true);
 
-    if (dtype == FD_DF64) {
+    if (dw_state(dtype)) {
         e = fd::launch_tgv_ic(g, ph, hx, hy, hz, h->Qs, h->stream);
         if (e == cudaSuccess)
             e = fd::launch_to_df64(h->Qs, reinterpret_cast<fd::df64*>(h->Q[0]), h->n, state_shift(h), h->stream);
@@ -425,7 +430,7 @@ int fd_get_state(fd_handle* h, double* dst, size_t n_elems, int dst_is_device) {
         return h->fail(FD_EINVAL, "fd_get_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h->n);
     cudaError_t e = cudaSuccess;
     const double* src = h->Q[h->cur];
-    if (h->dtype == FD_DF64) {
+    if (dw_state(h->dtype)) {
         double* tmp = dst_is_device ? dst : h->Qs;
         e = state_to_binary64(h, tmp);
         src = tmp;
@@ -444,10 +449,10 @@ int fd_set_state(fd_handle* h, const double* src, size_t n_elems, int src_is_dev
     if (n_elems != 5 * (size_t)h->n)
         return h->fail(FD_EINVAL, "fd_set_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h->n);
     h->wvalid = false;
-    double* dst = h->dtype == FD_DF64 ? h->Qs : h->Q[h->cur];
+    double* dst = dw_state(h->dtype) ? h->Qs : h->Q[h->cur];
     cudaError_t e = cudaMemcpyAsync(dst, src, n_elems * sizeof(double),
                                     src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess && h->dtype == FD_DF64)
+    if (e == cudaSuccess && dw_state(h->dtype))
         e = fd::launch_to_df64(h->Qs, reinterpret_cast<fd::df64*>(h->Q[h->cur]), h->n, state_shift(h), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "fd_set_state");
@@ -459,13 +464,14 @@ int fd_diagnostics(fd_handle* h, double* ke, double* enstrophy) {
     double out[2];
     // Scratch for the velocities: the working-field buffer the next stage will
     // overwrite (binary64, df64), or W[0], unused by the binary32 stages.  The
-    // df64 mode first converts the state to binary64 in Qs (dead between steps).
+    // double-word modes first convert the state to binary64 in Qs (dead
+    // between steps).
     double* Wv = h->dtype == FD_F64    ? h->W[1 - h->wcur]
                  : h->dtype == FD_DF64 ? reinterpret_cast<double*>(h->Wd[1 - h->wcur])
                                        : h->W[0];
     const double* Q = h->Q[h->cur];
     cudaError_t e = cudaSuccess;
-    if (h->dtype == FD_DF64) {
+    if (dw_state(h->dtype)) {
         e = state_to_binary64(h, h->Qs);
         Q = h->Qs;
     }
@@ -484,12 +490,13 @@ int fd_residual(fd_handle* h, double* R, size_t n_elems, int dst_is_device) {
     if (n_elems != 5 * (size_t)h->n)
         return h->fail(FD_EINVAL, "fd_residual: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h->n);
     // Between steps the saved register Qs is dead (stage 0 rewrites it), so it
-    // serves as the device buffer for R.  The df64 mode evaluates R as
-    // double-words into the spare working-field buffer, then converts it.
+    // serves as the device buffer for R.  The double-word modes evaluate R as
+    // double-words into a spare buffer (the df64 working fields the next stage
+    // overwrites, or W[0], unused by the binary32 stages), then convert it.
     double* out = dst_is_device ? R : h->Qs;
     cudaError_t e;
-    if (h->dtype == FD_DF64) {
-        double* Rw = reinterpret_cast<double*>(h->Wd[1 - h->wcur]);
+    if (dw_state(h->dtype)) {
+        double* Rw = h->dtype == FD_DF64 ? reinterpret_cast<double*>(h->Wd[1 - h->wcur]) : h->W[0];
         e = run_stage(h, 0, true, Rw);
         if (e == cudaSuccess)  // a residual is a rate: no shift
             e = fd::launch_from_df64(reinterpret_cast<const fd::df64*>(Rw), out, h->n, fd::Shift5{{0, 0, 0, 0, 0}},
@@ -509,7 +516,7 @@ int fd_check_finite(fd_handle* h) {
     int flag = 0;
     const double* Q = h->Q[h->cur];
     cudaError_t e = cudaSuccess;
-    if (h->dtype == FD_DF64) {
+    if (dw_state(h->dtype)) {
         e = state_to_binary64(h, h->Qs);
         Q = h->Qs;
     }

@@ -5,7 +5,8 @@
 //   instance table  BatchInst<T>[count]   grid, coefficients, buffer pointers
 //   tile lists      BatchTile[...]        one list per family (SS, RA) and one
 //                                         over all instances (primitives pass)
-//   per instance    Q[2], Qs (binary64), W[2] working fields, G (SS)
+//   per instance    Q[2], Qs state (binary64, or shifted double-words in the
+//                   binary32 mode), W[2] working fields, G (SS)
 //   diagnostics     partial sums and 2 x count results
 // A step is three stages; each stage launches, per family present, the
 // persistent kernels of fd_kernels.cu (SS: gradients then fused; RA: fused).
@@ -91,6 +92,18 @@ struct fd_batch {
 
 namespace {
 
+// binary32 mode: the state holds shifted double-words (rho - 1, rho u_i,
+// rho E - rhoE0); a binary64 copy passes through the instance's saved
+// register Qs, which is dead between steps (stage 0 rewrites it).
+fd::Shift5 state_shift(const InstHost& h) {
+    return fd::Shift5{{1.0, 0.0, 0.0, 0.0, fd::make_phys(h.d.Re, h.d.Mach, h.d.Pr, h.d.gamma).rhoE0}};
+}
+
+cudaError_t to_binary64(const fd_batch* b, const InstHost& h, double* dst) {
+    const char* q = b->base() + (b->parity ? h.q1 : h.q0);
+    return fd::launch_from_df64(reinterpret_cast<const fd::df64*>(q), dst, h.n, state_shift(h), b->stream);
+}
+
 template <class T>
 void fill_inst(const fd_batch* b, std::vector<fd::BatchInst<T>>& out) {
     out.resize(b->count);
@@ -101,16 +114,13 @@ void fill_inst(const fd_batch* b, std::vector<fd::BatchInst<T>>& out) {
         I.g = fd::make_grid(h.d.nx, h.d.ny, h.d.nz);
         I.ph = fd::make_phys(h.d.Re, h.d.Mach, h.d.Pr, h.d.gamma);
         I.k = fd::make_coef<T>(I.g, I.ph, sizeof(T) == sizeof(float));
-        I.Q[0] = reinterpret_cast<double*>(b->base() + h.q0);
-        I.Q[1] = reinterpret_cast<double*>(b->base() + h.q1);
-        I.Qs = reinterpret_cast<double*>(b->base() + h.qs);
+        I.Q[0] = reinterpret_cast<fd::state_t<T>*>(b->base() + h.q0);
+        I.Q[1] = reinterpret_cast<fd::state_t<T>*>(b->base() + h.q1);
+        I.Qs = reinterpret_cast<fd::state_t<T>*>(b->base() + h.qs);
         I.W[0] = reinterpret_cast<T*>(b->base() + h.w0);
         I.W[1] = reinterpret_cast<T*>(b->base() + h.w1);
         I.G = h.g == (size_t)-1 ? nullptr : reinterpret_cast<T*>(b->base() + h.g);
-        for (int s = 0; s < 3; ++s) {
-            I.adt[s] = fd::kRkA[s] * h.d.dt;
-            I.bdt[s] = fd::kRkB[s] * h.d.dt;
-        }
+        for (int s = 0; s < 3; ++s) I.rk[s] = fd::make_stage(s, h.d.dt);
     }
 }
 
@@ -247,7 +257,7 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
     if (!out) return fail_global(FD_EINVAL, "fd_batch_create: out is NULL");
     *out = nullptr;
     if (!desc || count < 1) return fail_global(FD_EINVAL, "fd_batch_create: need count >= 1 descriptors");
-    if (dtype != FD_F64 && dtype != FD_F32_ACC64) return fail_global(FD_EINVAL, "fd_batch_create: dtype %d", dtype);
+    if (dtype != FD_F64 && dtype != FD_F32_ACCDW) return fail_global(FD_EINVAL, "fd_batch_create: dtype %d", dtype);
     if (alloc && (!alloc->alloc || !alloc->free))
         return fail_global(FD_EINVAL, "fd_batch_create: allocator needs both alloc and free");
     for (int i = 0; i < count; ++i) {
@@ -294,7 +304,7 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
     }
     std::vector<fd::BatchTile> t_ss, t_ra, t_all;
     make_tiles(b, FD_STORE_SOME, false, t_ss);
-    make_tiles(b, FD_RECOMPUTE_ALL, dtype == FD_F32_ACC64, t_ra);
+    make_tiles(b, FD_RECOMPUTE_ALL, dtype == FD_F32_ACCDW, t_ra);
     make_tiles(b, -1, false, t_all);
     size_t o_ss = take(std::max<size_t>(1, t_ss.size()) * sizeof(fd::BatchTile));
     size_t o_ra = take(std::max<size_t>(1, t_ra.size()) * sizeof(fd::BatchTile));
@@ -366,8 +376,11 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
         const InstHost& h = b->inst[i];
         fd::Grid g = fd::make_grid(h.d.nx, h.d.ny, h.d.nz);
         fd::Phys ph = fd::make_phys(h.d.Re, h.d.Mach, h.d.Pr, h.d.gamma);
-        e = fd::launch_tgv_ic(g, ph, 2.0 * fd::kPi / h.d.nx, 2.0 * fd::kPi / h.d.ny, 2.0 * fd::kPi / h.d.nz,
-                              reinterpret_cast<double*>(b->base() + h.q0), b->stream);
+        double* ic = reinterpret_cast<double*>(b->base() + (dtype == FD_F64 ? h.q0 : h.qs));
+        e = fd::launch_tgv_ic(g, ph, 2.0 * fd::kPi / h.d.nx, 2.0 * fd::kPi / h.d.ny, 2.0 * fd::kPi / h.d.nz, ic,
+                              b->stream);
+        if (e == cudaSuccess && dtype != FD_F64)
+            e = fd::launch_to_df64(ic, reinterpret_cast<fd::df64*>(b->base() + h.q0), h.n, state_shift(h), b->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
@@ -410,8 +423,15 @@ int fd_batch_get_state(fd_batch* b, int i, double* dst, size_t n_elems, int dst_
     if (n_elems != 5 * (size_t)h.n)
         return b->fail(FD_EINVAL, "fd_batch_get_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h.n);
     const char* src = b->base() + (b->parity ? h.q1 : h.q0);
-    cudaError_t e = cudaMemcpyAsync(dst, src, n_elems * sizeof(double),
-                                    dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream);
+    cudaError_t e = cudaSuccess;
+    if (b->dtype != FD_F64) {
+        double* tmp = dst_is_device ? dst : reinterpret_cast<double*>(b->base() + h.qs);
+        e = to_binary64(b, h, tmp);
+        src = reinterpret_cast<const char*>(tmp);
+    }
+    if (e == cudaSuccess && src != reinterpret_cast<const char*>(dst))
+        e = cudaMemcpyAsync(dst, src, n_elems * sizeof(double),
+                            dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return b->cuda_fail(e, "fd_batch_get_state");
     return FD_OK;
@@ -425,9 +445,13 @@ int fd_batch_set_state(fd_batch* b, int i, const double* src, size_t n_elems, in
     if (n_elems != 5 * (size_t)h.n)
         return b->fail(FD_EINVAL, "fd_batch_set_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h.n);
     b->wvalid = false;
-    char* dst = b->base() + (b->parity ? h.q1 : h.q0);
+    char* q = b->base() + (b->parity ? h.q1 : h.q0);
+    char* dst = b->dtype == FD_F64 ? q : b->base() + h.qs;
     cudaError_t e = cudaMemcpyAsync(dst, src, n_elems * sizeof(double),
                                     src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && b->dtype != FD_F64)
+        e = fd::launch_to_df64(reinterpret_cast<const double*>(dst), reinterpret_cast<fd::df64*>(q), h.n,
+                               state_shift(h), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return b->cuda_fail(e, "fd_batch_set_state");
     return FD_OK;
@@ -440,10 +464,15 @@ int fd_batch_diagnostics(fd_batch* b, double* ke, double* enstrophy) {
         const InstHost& h = b->inst[i];
         fd::Grid g = fd::make_grid(h.d.nx, h.d.ny, h.d.nz);
         const double* Q = reinterpret_cast<const double*>(b->base() + (b->parity ? h.q1 : h.q0));
+        if (b->dtype != FD_F64) {
+            double* tmp = reinterpret_cast<double*>(b->base() + h.qs);
+            e = to_binary64(b, h, tmp);
+            Q = tmp;
+        }
         // Scratch for the velocities: the working-field buffer the next stage
         // overwrites (at least 3 x n doubles in either precision).
         double* Wv = reinterpret_cast<double*>(b->base() + (b->parity ? h.w0 : h.w1));
-        e = fd::launch_diagnostics_f64(g, Q, Wv, b->partial, b->diag + 2 * i, b->stream);
+        if (e == cudaSuccess) e = fd::launch_diagnostics_f64(g, Q, Wv, b->partial, b->diag + 2 * i, b->stream);
     }
     std::vector<double> out(2 * (size_t)b->count);
     if (e == cudaSuccess)

@@ -55,10 +55,12 @@ struct Shift5 {
 // Precision modes.  T is the arithmetic of the stencils and the residual; the
 // conserved state (and the RK accumulation) is kept in state_t<T>:
 //   double  binary64 everywhere;
-//   float   binary32 stencils on shifted fields, binary64 state;
-//   df64    double-word stencils on shifted fields and a double-word state,
-//           itself shifted (rho - 1, rho u_i, rho E - rhoE0), so that no
-//           binary64 instruction is issued in a step.
+//   float   binary32 stencils on shifted fields; double-word (compensated
+//           binary32, ~48 bits) state and RK accumulation;
+//   df64    double-word stencils on shifted fields and a double-word state.
+// A double-word state is itself shifted (rho - 1, rho u_i, rho E - rhoE0) so
+// that its bits resolve the perturbations; in both of these modes no binary64
+// instruction is issued in a step.
 template <class T>
 struct Prec;
 template <>
@@ -68,7 +70,7 @@ struct Prec<double> {
 };
 template <>
 struct Prec<float> {
-    using S = double;
+    using S = df64;
     static constexpr bool shifted = true;
 };
 template <>

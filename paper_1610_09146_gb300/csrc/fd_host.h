@@ -56,8 +56,6 @@ inline Phys make_phys(double Re, double Mach, double Pr, double gamma) {
     return ph;
 }
 
-// Constants of the fused residual (see fd::Coef); `shifted` selects the
-// binary32 perturbation form.
 // The RK constants of stage s for a time step dt.
 inline RKStage make_stage(int s, double dt) {
     RKStage rk{};
@@ -69,6 +67,8 @@ inline RKStage make_stage(int s, double dt) {
     return rk;
 }
 
+// Constants of the fused residual (see fd::Coef); `shifted` selects the
+// perturbation form of the binary32 and df64 modes.
 template <class T>
 Coef<T> make_coef(const Grid& g, const Phys& ph, bool shifted) {
     Coef<T> k{};

@@ -18,7 +18,7 @@ cudaError_t launch_tgv_ic(const Grid& g, const Phys& ph, double hx, double hy, d
 // Primitive variables: binary64 W = (u, v, w, p, T), or the ten binary32
 // perturbation fields F = (rho-1, rho u, rho v, rho w, rhoE-rhoE0, u, v, w, p-p0, T-1).
 cudaError_t launch_prims_f64(const Grid& g, const Phys& ph, const double* Q, double* W, cudaStream_t st);
-cudaError_t launch_prims_f32(const Grid& g, const Phys& ph, const double* Q, float* F, cudaStream_t st);
+cudaError_t launch_prims_f32(const Grid& g, const Phys& ph, const df64* Q, float* F, cudaStream_t st);
 cudaError_t launch_prims_df64(const Grid& g, const Phys& ph, const df64* Q, df64* F, cudaStream_t st);
 // binary64 <-> double-word conversion of 5 arrays of n values, subtracting /
 // adding a per-array shift (df64 mode at the API boundary).
@@ -64,11 +64,11 @@ struct BatchInst {
     Grid g;
     Coef<T> k;
     Phys ph;
-    double* Q[2];  // ping-pong state
-    double* Qs;    // saved RK register
+    state_t<T>* Q[2];  // ping-pong state (binary64, or shifted double-words in the binary32 mode)
+    state_t<T>* Qs;    // saved RK register
     T* W[2];       // working fields of Q[0] / Q[1] (binary64: 5 primitives; binary32: 10 perturbation fields)
     T* G;          // SS: nine velocity gradients (else null)
-    double adt[3], bdt[3];  // a_s dt, b_s dt per stage
+    RKStage rk[3];  // a_s dt, b_s dt of each stage (binary64 and double-word)
 };
 
 // A contiguous run of points [start, start + count) of one instance.

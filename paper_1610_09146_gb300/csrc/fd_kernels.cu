@@ -102,8 +102,13 @@ __device__ __forceinline__ void visc_consts(const Phys& ph, df64& nu, df64& ka) 
 
 // The stage's residual in the state precision, and the RK constants in it.
 __device__ __forceinline__ double to_state(double r) { return r; }
-__device__ __forceinline__ double to_state(float r) { return (double)r; }
+__device__ __forceinline__ df64 to_state(float r) { return df64(r, 0.0f); }
 __device__ __forceinline__ df64 to_state(df64 r) { return r; }
+// a R + q for the update: a binary32 residual multiplies a double-word
+// constant with the cheaper double-word x binary32 product.
+__device__ __forceinline__ double upd(double a, double r, double q) { return fmx(a, r, q); }
+__device__ __forceinline__ df64 upd(df64 a, df64 r, df64 q) { return fmx(a, r, q); }
+__device__ __forceinline__ df64 upd(df64 a, float r, df64 q) { return times_fp(a, r) + q; }
 __device__ __forceinline__ double rk_a(const RKStage& rk, double) { return rk.adt; }
 __device__ __forceinline__ df64 rk_a(const RKStage& rk, df64) { return rk.adt_w; }
 __device__ __forceinline__ double rk_b(const RKStage& rk, double) { return rk.bdt; }
@@ -152,19 +157,19 @@ __device__ __forceinline__ void prims_point(const Phys& ph, const double q[5], d
 }
 
 // binary32 perturbation fields F = (rho-1, rho u, rho v, rho w, rhoE-rhoE0,
-// u, v, w, p-p0, T-1) from the binary64 state.  With p0 = (gamma-1) rhoE0
-// and gamma M^2 p0 = 1, Eqs. 6-7 become
+// u, v, w, p-p0, T-1) from the shifted double-word state (q0 = rho - 1,
+// q4 = rho E - rhoE0).  With p0 = (gamma-1) rhoE0 and gamma M^2 p0 = 1, Eqs.
+// 6-7 become
 //   p - p0 = (gamma-1)(E' - rho u_i u_i / 2),  T - 1 = (gamma M^2 (p-p0) - rho') / rho.
-// Only the two shifts rho-1 and rhoE-rhoE0 are taken in binary64.
-__device__ __forceinline__ void prims_point(const Phys& ph, const double q[5], float* __restrict__ F, int n,
-                                            int c) {
-    float rp = (float)(q[0] - 1.0);
-    float Ep = (float)(q[4] - ph.rhoE0);
-    float m0 = (float)q[1], m1 = (float)q[2], m2 = (float)q[3];
-    float inv = 1.0f / (float)q[0];
+__device__ __forceinline__ float to_f32(df64 x) { return __fadd_rn(x.hi, x.lo); }
+__device__ __forceinline__ void prims_point(const Phys& ph, const df64 q[5], float* __restrict__ F, int n, int c) {
+    float rp = to_f32(q[0]);
+    float Ep = to_f32(q[4]);
+    float m0 = to_f32(q[1]), m1 = to_f32(q[2]), m2 = to_f32(q[3]);
+    float inv = 1.0f / to_f32(q[0] + df64(1.0f, 0.0f));
     float u = m0 * inv, v = m1 * inv, w = m2 * inv;
-    float pp = (float)ph.gm1 * fmx(-0.5f, fmx(m0, u, fmx(m1, v, m2 * w)), Ep);
-    float Tp = fmx((float)ph.gM2, pp, -rp) * inv;
+    float pp = ph.gm1_w.hi * fmx(-0.5f, fmx(m0, u, fmx(m1, v, m2 * w)), Ep);
+    float Tp = fmx(ph.gM2_w.hi, pp, -rp) * inv;
     F[c] = rp;
     F[n + c] = m0;
     F[2 * n + c] = m1;
@@ -222,17 +227,16 @@ __device__ __forceinline__ void stage_update(const RKStage& rk, const Phys& ph, 
     S qn[5];
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
-        const S r = to_state(R[f]);
-        qn[f] = fmx(rk_a(rk, S()), r, qs[f]);
+        qn[f] = upd(rk_a(rk, S()), R[f], qs[f]);
         out[f * n + c] = qn[f];
-        if (rk.stage < 2) Qs[f * n + c] = fmx(rk_b(rk, S()), r, qs[f]);
+        if (rk.stage < 2) Qs[f * n + c] = upd(rk_b(rk, S()), R[f], qs[f]);
     }
     prims_point(ph, qn, Wnext, n, c);
 }
 
 // Final write of a stage: the residual itself (fd_residual), or the
 // two-register RK update (Fig. 1, advance-solution-in-time) in the state
-// precision (binary64, or double-word in the df64 mode),
+// precision (binary64, or double-word in the binary32 and df64 modes),
 //   Q_out = Qs + a dt R,  Qs <- Qs + b dt R,  with Qs = Q_in at stage 0 (save-state),
 // followed by the primitives of Q_out for the next stage (evaluate-u_i,p,T of
 // Fig. 1 moved to the end of the previous stage: it is pointwise, so the point
@@ -244,14 +248,13 @@ __device__ __forceinline__ void stage_write(const RKStage& rk, const Phys& ph, i
     S qn[5];
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
-        const S r = to_state(R[f]);
         if (RESID) {
-            out[f * n + c] = r;
+            out[f * n + c] = to_state(R[f]);
         } else {
             const S qs = rk.stage == 0 ? Q64[f * n + c] : Qs[f * n + c];
-            qn[f] = fmx(rk_a(rk, S()), r, qs);
+            qn[f] = upd(rk_a(rk, S()), R[f], qs);
             out[f * n + c] = qn[f];
-            if (rk.stage < 2) Qs[f * n + c] = fmx(rk_b(rk, S()), r, qs);
+            if (rk.stage < 2) Qs[f * n + c] = upd(rk_b(rk, S()), R[f], qs);
         }
     }
     if (!RESID) prims_point(ph, qn, Wnext, n, c);
@@ -742,12 +745,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_batch_fused(con
         if (threadIdx.x == 0) I = insts[tl.inst];
         __syncthreads();
         const int n = I.g.n;
-        const double* Qin = I.Q[parity];
-        double* Qout = I.Q[1 - parity];
+        const state_t<T>* Qin = I.Q[parity];
+        state_t<T>* Qout = I.Q[1 - parity];
         const T* Wc = I.W[parity];
         const T* Qf = sizeof(T) == sizeof(double) ? reinterpret_cast<const T*>(Qin) : Wc;
         const T* Wf = sizeof(T) == sizeof(double) ? Wc : Wc + 5 * (size_t)n;
-        const RKStage rk{I.adt[stage], I.bdt[stage], stage};
+        const RKStage rk = I.rk[stage];
         for (int p = threadIdx.x; p < tl.count; p += blockDim.x) {
             const Nbr s = make_nbr(I.g, tl.start + p);
             T R[5];
@@ -774,11 +777,11 @@ __global__ void __launch_bounds__(kTX* kTY, sizeof(T) == 4 ? 2 : 1)
         const int ntx = (I.g.nx + kTX - 1) / kTX, nty = (I.g.ny + kTY - 1) / kTY;
         const int zt = tl.start / (ntx * nty), r = tl.start % (ntx * nty);
         const int n = I.g.n;
-        const double* Qin = I.Q[parity];
+        const state_t<T>* Qin = I.Q[parity];
         const T* Wc = I.W[parity];
         const T* Qf = sizeof(T) == sizeof(double) ? reinterpret_cast<const T*>(Qin) : Wc;
         const T* Wf = sizeof(T) == sizeof(double) ? Wc : Wc + 5 * (size_t)n;
-        const RKStage rk{I.adt[stage], I.bdt[stage], stage};
+        const RKStage rk = I.rk[stage];
         ra_tiled_block<T, false>(reinterpret_cast<T*>(smem_raw), I.g, I.k, I.ph, rk, Qf, Wf, Qin, I.Q[1 - parity],
                                  I.Qs, I.W[1 - parity], (r % ntx) * kTX, (r / ntx) * kTY, zt * kZChunk);
     }
@@ -822,7 +825,7 @@ __global__ void __launch_bounds__(256) k_batch_prims(const BatchInst<T>* __restr
         const int n = I.g.n;
         for (int p = threadIdx.x; p < tl.count; p += blockDim.x) {
             const int c = tl.start + p;
-            double q[5];
+            state_t<T> q[5];
 #pragma unroll
             for (int f = 0; f < 5; ++f) q[f] = I.Q[parity][f * n + c];
             prims_point(I.ph, q, I.W[parity], n, c);
@@ -1015,7 +1018,7 @@ cudaError_t launch_prims_f64(const Grid& g, const Phys& ph, const double* Q, dou
     return cudaGetLastError();
 }
 
-cudaError_t launch_prims_f32(const Grid& g, const Phys& ph, const double* Q, float* F, cudaStream_t st) {
+cudaError_t launch_prims_f32(const Grid& g, const Phys& ph, const df64* Q, float* F, cudaStream_t st) {
     k_prims<float><<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, Q, F);
     return cudaGetLastError();
 }
@@ -1146,7 +1149,7 @@ template cudaError_t launch_ra_tiled<double>(const Grid&, const Coef<double>&, c
                                              const double*, const double*, const double*, double*, double*, double*,
                                              cudaStream_t);
 template cudaError_t launch_ra_tiled<float>(const Grid&, const Coef<float>&, const Phys&, const RKStage&, bool,
-                                            const float*, const float*, const double*, double*, double*, float*,
+                                            const float*, const float*, const df64*, df64*, df64*, float*,
                                             cudaStream_t);
 
 cudaError_t launch_diagnostics_f64(const Grid& g, const double* Q, double* Wv, double* partial, double* out,

@@ -121,7 +121,7 @@ const char* check_request(const fd_request* r) {
     if (!r) return "request is NULL";
     if (const char* why = fd::check_instance(r->nx, r->ny, r->nz, r->Re, r->Mach, r->Pr, r->gamma, r->dt)) return why;
     if (r->steps < 1) return "steps must be >= 1";
-    if (r->dtype != FD_F64 && r->dtype != FD_F32_ACC64) return "unknown dtype";
+    if (r->dtype != FD_F64 && r->dtype != FD_F32_ACCDW) return "unknown dtype";
     if (r->algorithm != FD_STORE_SOME && r->algorithm != FD_RECOMPUTE_ALL) return "algorithm must be SS or RA";
     if (r->tile_points != 0 && r->tile_points < 32) return "tile_points must be 0 or >= 32";
     return nullptr;
@@ -209,16 +209,13 @@ fd::BatchInst<T> record(const fd_server* s, const Active& a) {
     I.ph = fd::make_phys(a.r.Re, a.r.Mach, a.r.Pr, a.r.gamma);
     I.k = fd::make_coef<T>(I.g, I.ph, sizeof(T) == sizeof(float));
     char* b = s->base() + a.off;
-    I.Q[0] = reinterpret_cast<double*>(b + a.L.q0);
-    I.Q[1] = reinterpret_cast<double*>(b + a.L.q1);
-    I.Qs = reinterpret_cast<double*>(b + a.L.qs);
+    I.Q[0] = reinterpret_cast<fd::state_t<T>*>(b + a.L.q0);
+    I.Q[1] = reinterpret_cast<fd::state_t<T>*>(b + a.L.q1);
+    I.Qs = reinterpret_cast<fd::state_t<T>*>(b + a.L.qs);
     I.W[0] = reinterpret_cast<T*>(b + a.L.w0);
     I.W[1] = reinterpret_cast<T*>(b + a.L.w1);
     I.G = a.L.g == (size_t)-1 ? nullptr : reinterpret_cast<T*>(b + a.L.g);
-    for (int st = 0; st < 3; ++st) {
-        I.adt[st] = fd::kRkA[st] * a.r.dt;
-        I.bdt[st] = fd::kRkB[st] * a.r.dt;
-    }
+    for (int st = 0; st < 3; ++st) I.rk[st] = fd::make_stage(st, a.r.dt);
     return I;
 }
 
@@ -437,9 +434,15 @@ int fd_server_tick(fd_server* s, int* active_out) {
         a.n = it->nx * it->ny * it->nz;
         fd::Grid g = fd::make_grid(a.r.nx, a.r.ny, a.r.nz);
         fd::Phys ph = fd::make_phys(a.r.Re, a.r.Mach, a.r.Pr, a.r.gamma);
-        double* Q = reinterpret_cast<double*>(s->base() + off + (s->parity ? L.q1 : L.q0));
-        e = fd::launch_tgv_ic(g, ph, 2.0 * fd::kPi / a.r.nx, 2.0 * fd::kPi / a.r.ny, 2.0 * fd::kPi / a.r.nz, Q,
+        // binary32 solves keep a shifted double-word state (rho - 1, rho u_i,
+        // rho E - rhoE0): the binary64 initial condition passes through Qs.
+        char* Q = s->base() + off + (s->parity ? L.q1 : L.q0);
+        double* ic = reinterpret_cast<double*>(a.r.dtype == FD_F64 ? Q : s->base() + off + L.qs);
+        e = fd::launch_tgv_ic(g, ph, 2.0 * fd::kPi / a.r.nx, 2.0 * fd::kPi / a.r.ny, 2.0 * fd::kPi / a.r.nz, ic,
                               s->stream);
+        if (e == cudaSuccess && a.r.dtype != FD_F64)
+            e = fd::launch_to_df64(ic, reinterpret_cast<fd::df64*>(Q), a.n, fd::Shift5{{1.0, 0.0, 0.0, 0.0, ph.rhoE0}},
+                                   s->stream);
         if (e != cudaSuccess) {
             s->arena.release(off, L.total);
             return s->cuda_fail(e, "fd_server_tick: initial condition");
@@ -475,8 +478,15 @@ int fd_server_tick(fd_server* s, int* active_out) {
         fd::Grid g = fd::make_grid(a.r.nx, a.r.ny, a.r.nz);
         char* b = s->base() + a.off;
         const double* Q = reinterpret_cast<const double*>(b + (s->parity ? a.L.q1 : a.L.q0));
+        if (a.r.dtype != FD_F64) {  // double-word state to binary64 in the retiring solve's Qs
+            double* tmp = reinterpret_cast<double*>(b + a.L.qs);
+            fd::Phys ph = fd::make_phys(a.r.Re, a.r.Mach, a.r.Pr, a.r.gamma);
+            e = fd::launch_from_df64(reinterpret_cast<const fd::df64*>(Q), tmp, a.n,
+                                     fd::Shift5{{1.0, 0.0, 0.0, 0.0, ph.rhoE0}}, s->stream);
+            Q = tmp;
+        }
         double* Wv = reinterpret_cast<double*>(b + (s->parity ? a.L.w0 : a.L.w1));
-        e = fd::launch_diagnostics_f64(g, Q, Wv, s->partial, s->results + 2 * k, s->stream);
+        if (e == cudaSuccess) e = fd::launch_diagnostics_f64(g, Q, Wv, s->partial, s->results + 2 * k, s->stream);
     }
     std::vector<double> res(2 * fin.size());
     if (e == cudaSuccess && !fin.empty())

@@ -26,7 +26,7 @@ FD_STORE_SOME = 1
 FD_RECOMPUTE_ALL = 2
 
 FD_F64 = 0
-FD_F32_ACC64 = 1
+FD_F32_ACCDW = 1
 FD_DF64 = 2
 
 FD_KERNEL_PRIMS = 0

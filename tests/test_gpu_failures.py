@@ -64,7 +64,7 @@ def test_batch_reports_out_of_memory_and_frees_everything():
     a = CountingAlloc(0)
     d = native.FdInstanceDesc(16, 16, 16, 1600.0, 0.1, 0.71, 1.4, 1e-3, fd.FD_RECOMPUTE_ALL, 0)
     with pytest.raises(fd.FdError) as e:
-        native.fd_batch_create([d], fd.FD_F32_ACC64, a.struct, 0)
+        native.fd_batch_create([d], fd.FD_F32_ACCDW, a.struct, 0)
     assert e.value.code == fd.FD_ENOMEM and not a.live
 
 

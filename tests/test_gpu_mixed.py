@@ -1,4 +1,5 @@
-"""binary32-stencil / binary64-accumulate mode (FD_F32_ACC64) against binary64.
+"""binary32-stencil mode (FD_F32_ACCDW: compensated binary32 state and RK
+accumulation, binary64 reductions) against binary64.
 
 Bounds: relative L2 <= 1e-5 per conserved variable and relative kinetic
 energy error <= 1e-6 after 100 steps of the 64^3 Taylor-Green vortex, against
