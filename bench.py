@@ -37,12 +37,13 @@ if ROOT not in sys.path:
 N_GRID = 256
 RE, MACH, PR, GAMMA = 1600.0, 0.1, 0.71, 1.4
 METRIC = "point-updates/s"
-VARIANTS = ["store_all", "store_some", "recompute_all"]
-SHORT = {"store_all": "BL", "store_some": "SS", "recompute_all": "RA"}
+VARIANTS = ["store_all", "store_some", "recompute_all", "recompute_some", "store_none"]
+SHORT = {"store_all": "BL", "store_some": "SS", "recompute_all": "RA", "recompute_some": "RS", "store_none": "SN"}
 
 # Table 1 (Section 4): run-time in seconds of 500 iterations at 256^3 on one 24-core
 # ARCHER node (24 MPI ranks, Cray C -O3, binary64).  Context only, another machine.
-PAPER_256_SECONDS = {"store_all": 1561.52, "recompute_all": 765.42, "store_some": 685.25}
+PAPER_256_SECONDS = {"store_all": 1561.52, "recompute_all": 765.42, "recompute_some": 802.76, "store_none": 693.66,
+                     "store_some": 685.25}
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # binary64 arithmetic peak of GB300: 152 SMs x 2 FP64 FMA lanes per SM per clock x 2 flop
@@ -64,19 +65,33 @@ COST = {
     ("f64", "store_all", "deriv2"): (114, 200, 84),
     ("f64", "store_all", "products"): (18, 216, 18),
     ("f64", "*", "prims"): (14, 80, 20),
-    ("f32", "store_some", "fused"): (415.7, 222.7, 10.3),
+    # RS and SN: the derivative set of the paper as written (BL's arithmetic per derivative);
+    # RS re-evaluates the viscous terms in the energy equation, SN the inner derivatives of
+    # the six mixed derivatives at the shifted taps; same bytes as SS / RA.  Flops and
+    # instructions are ncu's DADD + DMUL + 2 DFMA (resp. their sum) per point, 64^3 grid
+    ("f64", "recompute_some", "fused"): (669.7, 285.3, 518.3),
+    ("f64", "recompute_some", "grad"): (45, 96, 36),
+    ("f64", "store_none", "fused"): (710.7, 213.3, 553.3),
+    # binary32 mode: the state and its RK update are double-words (no FP64 instructions)
+    ("f32", "store_some", "fused"): (415.7, 222.7, 0),
     ("f32", "store_some", "grad"): (45, 48, 0),
-    ("f32", "recompute_all", "fused"): (562.7, 186.7, 10.3),
-    ("f32", "store_all", "fused"): (183, 430.7, 10.3),
+    ("f32", "recompute_all", "fused"): (562.7, 186.7, 0),
+    ("f32", "recompute_some", "fused"): (669.7, 222.7, 0),
+    ("f32", "recompute_some", "grad"): (45, 48, 0),
+    ("f32", "store_none", "fused"): (710.7, 186.7, 0),
+    ("f32", "store_all", "fused"): (183, 430.7, 0),
     ("f32", "store_all", "deriv1"): (225, 288, 0),
     ("f32", "store_all", "deriv2"): (114, 100, 0),
     ("f32", "store_all", "products"): (18, 108, 0),
-    ("f32", "*", "prims"): (14, 80, 2),
+    ("f32", "*", "prims"): (14, 80, 0),
     # df64: the binary64 algorithm's flops, done in double-word arithmetic on the binary32
     # pipe (no FP64 instructions); state and fields are 8-byte double-words
     ("df64", "store_some", "fused"): (409.7, 338.7, 0),
     ("df64", "store_some", "grad"): (45, 96, 0),
     ("df64", "recompute_all", "fused"): (556.7, 266.7, 0),
+    ("df64", "recompute_some", "fused"): (669.7, 338.7, 0),
+    ("df64", "recompute_some", "grad"): (45, 96, 0),
+    ("df64", "store_none", "fused"): (710.7, 266.7, 0),
     ("df64", "store_all", "fused"): (177, 781.3, 0),
     ("df64", "store_all", "deriv1"): (225, 576, 0),
     ("df64", "store_all", "deriv2"): (114, 200, 0),

@@ -42,20 +42,32 @@ extern "C" {
 #define FD_EUNSTABLE (-4) /* non-finite value found by fd_check_finite          */
 #define FD_EBUSY (-5)     /* resource exhausted (batch slots, server capacity)  */
 
-/* ---- algorithm families (Section 2, paragraphs BL, SS, RA) --------------
- * FD_STORE_ALL     "BL": every derivative (and every product inside a
- *                  derivative, via a product work array) is written to a
- *                  grid-sized work array; the residual is then pointwise.
- * FD_STORE_SOME    "SS": the nine velocity gradients du_i/dx_j are stored in
- *                  work arrays; every other derivative is evaluated into
- *                  thread-local registers inside the fused residual kernel.
- * FD_RECOMPUTE_ALL "RA": no derivative is stored; every derivative is
- *                  evaluated from its finite-difference formula where used.
- * In all three the primitive variables u_i, p, T are evaluated and stored
- * (Section 2, the paragraph after Fig. 1). */
+/* ---- algorithm families (Section 2, paragraphs BL, RA, SN, RS, SS) -------
+ * FD_STORE_ALL       "BL": every derivative (and every product inside a
+ *                    derivative, via a product work array) is written to a
+ *                    grid-sized work array; the residual is then pointwise.
+ * FD_STORE_SOME      "SS": the nine velocity gradients du_i/dx_j are stored
+ *                    in work arrays; every other derivative is evaluated into
+ *                    thread-local registers inside the fused residual kernel.
+ * FD_RECOMPUTE_ALL   "RA": no derivative is stored; every derivative is
+ *                    evaluated from its finite-difference formula where used.
+ * FD_RECOMPUTE_SOME  "RS": the nine velocity gradients are stored; every other
+ *                    derivative is written out inside each equation that uses
+ *                    it, so a derivative two equations need is evaluated twice.
+ * FD_STORE_NONE      "SN": no derivative is stored; each one is evaluated once
+ *                    into a thread-local variable and the equations are
+ *                    assembled from those.
+ * SS and RA merge the derivatives that a residual adds along one direction
+ * into one stencil (a GB300-specific arithmetic saving); BL, RS and SN
+ * evaluate the derivative set of the paper as written, with identical
+ * arithmetic per derivative.  In all five the primitive variables u_i, p, T
+ * are evaluated and stored (Section 2, the paragraph after Fig. 1).  Every
+ * family exists for every dtype; the batch and server take SS and RA. */
 #define FD_STORE_ALL 0
 #define FD_STORE_SOME 1
 #define FD_RECOMPUTE_ALL 2
+#define FD_RECOMPUTE_SOME 3
+#define FD_STORE_NONE 4
 
 /* ---- arithmetic ----------------------------------------------------------
  * FD_F64        all arithmetic in IEEE binary64 (the paper's precision,
@@ -102,7 +114,8 @@ typedef struct fd_handle fd_handle;
  *               distinct neighbours) and nx*ny*nz < 2^31;
  *   Re, Mach, Pr, gamma  flow constants (Eqs. 4-7): Re, Mach, Pr > 0,
  *               gamma > 1; dt > 0 is the time step of every fd_step;
- *   algorithm   FD_STORE_ALL, FD_STORE_SOME or FD_RECOMPUTE_ALL;
+ *   algorithm   FD_STORE_ALL, FD_STORE_SOME, FD_RECOMPUTE_ALL,
+ *               FD_RECOMPUTE_SOME or FD_STORE_NONE;
  *   dtype       FD_F64, FD_F32_ACCDW or FD_DF64;
  *   alloc       NULL for cudaMalloc/cudaFree, else allocator callbacks;
  *   cuda_stream cudaStream_t for all work of this handle (NULL = default).

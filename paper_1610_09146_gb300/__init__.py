@@ -21,12 +21,14 @@ import numpy as np
 
 from . import native
 from .native import (FD_DF64, FD_EBUSY, FD_ECUDA, FD_EINVAL, FD_ENOMEM, FD_EUNSTABLE, FD_F32_ACCDW, FD_F64, FD_OK,
-                     FD_RECOMPUTE_ALL, FD_STORE_ALL, FD_STORE_SOME, FdAlloc, FdError, fd_check_finite, fd_create,
+                     FD_RECOMPUTE_ALL, FD_RECOMPUTE_SOME, FD_STORE_ALL, FD_STORE_NONE, FD_STORE_SOME, FdAlloc, FdError, fd_check_finite, fd_create,
                      fd_destroy, fd_device_bytes, fd_diagnostics, fd_get_state, fd_last_error, fd_residual,
                      fd_set_state, fd_step)
 
 ALGORITHMS = {"store_all": FD_STORE_ALL, "store_some": FD_STORE_SOME, "recompute_all": FD_RECOMPUTE_ALL,
-              "BL": FD_STORE_ALL, "SS": FD_STORE_SOME, "RA": FD_RECOMPUTE_ALL}
+              "recompute_some": FD_RECOMPUTE_SOME, "store_none": FD_STORE_NONE,
+              "BL": FD_STORE_ALL, "SS": FD_STORE_SOME, "RA": FD_RECOMPUTE_ALL, "RS": FD_RECOMPUTE_SOME,
+              "SN": FD_STORE_NONE}
 DTYPES = {"f64": FD_F64, "f32": FD_F32_ACCDW, "f32_accdw": FD_F32_ACCDW, "df64": FD_DF64}
 
 from .workloads import dt_for_grid  # noqa: E402  (Section 3 time-step rule)

@@ -121,7 +121,8 @@ int check_args(int nx, int ny, int nz, double Re, double Mach, double Pr, double
                int dtype) {
     if (const char* why = fd::check_instance(nx, ny, nz, Re, Mach, Pr, gamma, dt))
         return fail_global(FD_EINVAL, "fd_create: grid %dx%dx%d: %s", nx, ny, nz, why);
-    if (algorithm != FD_STORE_ALL && algorithm != FD_STORE_SOME && algorithm != FD_RECOMPUTE_ALL)
+    if (algorithm != FD_STORE_ALL && algorithm != FD_STORE_SOME && algorithm != FD_RECOMPUTE_ALL &&
+        algorithm != FD_RECOMPUTE_SOME && algorithm != FD_STORE_NONE)
         return fail_global(FD_EINVAL, "unknown algorithm %d", algorithm);
     if (dtype != FD_F64 && dtype != FD_F32_ACCDW && dtype != FD_DF64)
         return fail_global(FD_EINVAL, "unknown dtype %d", dtype);
@@ -132,6 +133,9 @@ int check_args(int nx, int ny, int nz, double Re, double Mach, double Pr, double
 struct Layout {
     size_t q0, q1, qs, w0, w1, g, p, d1, d2, wf0, wf1, gf, wd0, wd1, gd, partial, diag, flag, total;
 };
+
+// SS and RS keep the nine velocity gradients in work arrays.
+bool stores_g(int algorithm) { return algorithm == FD_STORE_SOME || algorithm == FD_RECOMPUTE_SOME; }
 
 Layout plan(long long n, int algorithm, int dtype) {
     Layout L{};
@@ -151,7 +155,7 @@ Layout plan(long long n, int algorithm, int dtype) {
         // state Q[2], Qs hold double-words (8 bytes per value, like binary64)
         L.wd0 = take(10 * n * sizeof(fd::df64));
         L.wd1 = take(10 * n * sizeof(fd::df64));
-        if (algorithm == FD_STORE_SOME) L.gd = take(9 * n * sizeof(fd::df64));
+        if (stores_g(algorithm)) L.gd = take(9 * n * sizeof(fd::df64));
         if (algorithm == FD_STORE_ALL) {
             L.p = take(18 * n * sizeof(fd::df64));
             L.d1 = take(45 * n * sizeof(fd::df64));
@@ -159,7 +163,7 @@ Layout plan(long long n, int algorithm, int dtype) {
         }
     } else if (dtype == FD_F64) {
         L.w1 = take(f5);
-        if (algorithm == FD_STORE_SOME) L.g = take(9 * n * sizeof(double));
+        if (stores_g(algorithm)) L.g = take(9 * n * sizeof(double));
         if (algorithm == FD_STORE_ALL) {
             L.p = take(18 * n * sizeof(double));
             L.d1 = take(45 * n * sizeof(double));
@@ -168,7 +172,7 @@ Layout plan(long long n, int algorithm, int dtype) {
     } else {
         L.wf0 = take(10 * n * sizeof(float));
         L.wf1 = take(10 * n * sizeof(float));
-        if (algorithm == FD_STORE_SOME) L.gf = take(9 * n * sizeof(float));
+        if (stores_g(algorithm)) L.gf = take(9 * n * sizeof(float));
         if (algorithm == FD_STORE_ALL) {
             L.p = take(18 * n * sizeof(float));
             L.d1 = take(45 * n * sizeof(float));
@@ -222,6 +226,17 @@ cudaError_t stage_kernels(fd_handle* h, const fd::RKStage& rk, bool resid, const
                 else
                     return fd::launch_ra<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, reinterpret_cast<S*>(h->Qs),
                                             Wnext, st);
+            });
+        case FD_STORE_NONE:
+            return timed(h, FD_KERNEL_FUSED, [&] {
+                return fd::launch_sn<T>(g, ph, rk, resid, Qf, Wf, Qin, Qout, reinterpret_cast<S*>(h->Qs), Wnext, st);
+            });
+        case FD_RECOMPUTE_SOME:
+            e = timed(h, FD_KERNEL_GRAD, [&] { return fd::launch_ss_grad<T>(g, k, Wf, G, st); });
+            if (e != cudaSuccess) return e;
+            return timed(h, FD_KERNEL_FUSED, [&] {
+                return fd::launch_rs<T>(g, ph, rk, resid, Qf, Wf, G, Qin, Qout, reinterpret_cast<S*>(h->Qs), Wnext,
+                                        st);
             });
         case FD_STORE_SOME:
             e = timed(h, FD_KERNEL_GRAD, [&] { return fd::launch_ss_grad<T>(g, k, Wf, G, st); });

@@ -57,6 +57,15 @@ template <class T>
 cudaError_t launch_bl_res(const Grid& g, const Phys& ph, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
                           const T* D1, const T* D2, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext,
                           cudaStream_t st);
+// SN: derivatives into thread-local variables, nothing stored.  RS: the nine
+// gradients of launch_ss_grad, every other derivative inside each equation.
+template <class T>
+cudaError_t launch_sn(const Grid& g, const Phys& ph, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
+                      const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext, cudaStream_t st);
+template <class T>
+cudaError_t launch_rs(const Grid& g, const Phys& ph, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
+                      const T* Gw, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext,
+                      cudaStream_t st);
 // ---- batched path ----------------------------------------------------------
 // One instance of a batch as the kernels see it (device memory, read per tile).
 template <class T>

@@ -295,6 +295,12 @@ struct GlobalAcc {
         for (int b = 0; b < 4; ++b) t[b] = ld(p, c + s.o[j][b]);
     }
     __device__ __forceinline__ T grad(int i, int j) const { return ld(Gw + (3 * i + j) * n, s.c); }
+    // taps along i of the stored gradient G_ab
+    __device__ __forceinline__ void grad_taps(int ga, int gb, int i, T t[4]) const {
+        const T* p = Gw + (3 * ga + gb) * n;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) t[a] = ld(p, s.c + s.o[i][a]);
+    }
     // taps along i of G_aa + G_bb
     __device__ __forceinline__ void grad_pair_taps(int ga, int gb, int i, T t[4]) const {
         const T* pa = Gw + (3 * ga + ga) * n;
@@ -727,6 +733,244 @@ __global__ void __launch_bounds__(256) k_bl_res(Grid g, Phys ph, RKStage rk, con
     stage_write<T, RESID>(rk, ph, n, c, Q64, R, out, Qs, Wnext);
 }
 
+// ------------------------------------------------------- SN and RS families
+// The two remaining families of Section 2 evaluate the paper's derivative set
+// as written: every derivative of a product is the difference of the product
+// formed at the taps, D_j(Q_f u_j) and u_j D_j Q_f are separate derivatives,
+// the mixed derivatives are D_i of D_k u_k, and the residual is assembled by
+// the same pointwise code as BL (fd::assemble).  Each derivative is the same
+// arithmetic as BL's work-array entry, so BL, SN and RS differ only in where a
+// derivative lives and how often it is evaluated.  (RA and SS instead merge
+// the derivatives that the residual adds along one direction into one
+// stencil; see fused_residual.)
+//
+// One derivative from the taps of field f along axis j, scaled as BL scales it.
+template <class T, class Acc>
+__device__ __forceinline__ T d1_of(const Acc& A, const Grid& g, int f, int j) {
+    T t[4];
+    A.taps(f, j, t);
+    return s1<T>(g, j) * delta1_taps(t);
+}
+
+// D_j of the product of fields f and w formed at the taps along j.
+template <class T, class Acc>
+__device__ __forceinline__ T d1_prod_of(const Acc& A, const Grid& g, int f, int w, int j) {
+    T a[4], b[4], pr[4];
+    A.taps(f, j, a);
+    A.taps(w, j, b);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pr[q] = a[q] * b[q];
+    return s1<T>(g, j) * delta1_taps(pr);
+}
+
+template <class T, class Acc>
+__device__ __forceinline__ T d2_of(const Acc& A, const Grid& g, int f, int j, T f0) {
+    T t[4];
+    A.taps(f, j, t);
+    return s2<T>(g, j) * delta2_taps(t, f0);
+}
+
+// conv_f = sum_j [ D_j(Q_f u_j) + u_j D_j Q_f ], in BL's order of operations.
+template <class T, class Acc>
+__device__ __forceinline__ T conv_of(const Acc& A, const Grid& g, int f, const T uc[3]) {
+    constexpr int U = 5;
+    T acc = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) acc += fmx(uc[j], d1_of<T>(A, g, f, j), d1_prod_of<T>(A, g, f, U + j, j));
+    return acc;
+}
+
+// sum_j D2_j u_i and D2_i u_i + sum_{k != i} D_i(D_k u_k); the inner D_k u_k
+// comes from u_k taps at the shifted points (SN) or the stored gradient G_kk
+// (RS), both the arithmetic of BL's two passes.
+template <class T, bool STORED_G, class Acc>
+__device__ __forceinline__ void viscous_of(const Acc& A, const Grid& g, int i, T uci, T& lap, T& gd) {
+    constexpr int U = 5;
+    T d2[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) d2[j] = d2_of<T>(A, g, U + i, j, uci);
+    lap = d2[0] + d2[1] + d2[2];
+    gd = d2[i];
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+        if (kk == i) continue;
+        T t[4];
+        if constexpr (STORED_G) {
+            A.grad_taps(kk, kk, i, t);
+        } else {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                T u4[4];
+                A.taps_shifted(U + kk, kk, i, a, u4);
+                t[a] = s1<T>(g, kk) * delta1_taps(u4);
+            }
+        }
+        gd += s1<T>(g, i) * delta1_taps(t);
+    }
+}
+
+// Store-none (Section 2, paragraph SN, and its pseudo-code figure): no work
+// arrays; every derivative is evaluated once into a thread-local variable
+// (the Terms record) and the residual of each equation is assembled from
+// those locals, so a derivative that several equations use (div u, G_ij, the
+// viscous terms) is evaluated once.
+template <class T, bool RESID>
+__global__ void __launch_bounds__(128) k_sn(Grid g, Phys ph, RKStage rk, const T* __restrict__ Qf,
+                                            const T* __restrict__ Wf, const state_t<T>* __restrict__ Q64,
+                                            state_t<T>* __restrict__ out, state_t<T>* __restrict__ Qs,
+                                            T* __restrict__ Wnext) {
+    constexpr int U = 5, P = 8, TT = 9;
+    int idx = grid_index();
+    if (idx >= g.n) return;
+    const Nbr s = make_nbr(g, idx);
+    const GlobalAcc<T> A{s, g.n, Qf, Wf, nullptr};
+    Terms<T> t;
+    T uc[3], q[5];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) uc[i] = A.center(U + i);
+#pragma unroll
+    for (int f = 0; f < 5; ++f) q[f] = A.center(f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) t.G[i][j] = d1_of<T>(A, g, U + i, j);
+#pragma unroll
+    for (int f = 0; f < 5; ++f) t.conv[f] = conv_of<T>(A, g, f, uc);
+    T dpu = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        t.dp[j] = d1_of<T>(A, g, P, j);
+        dpu += d1_prod_of<T>(A, g, P, U + j, j);
+    }
+    t.dpu = dpu;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) viscous_of<T, false>(A, g, i, uc[i], t.lap[i], t.gd[i]);
+    {
+        const T T0 = A.center(TT);
+        T d2[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) d2[j] = d2_of<T>(A, g, TT, j, T0);
+        t.lapT = d2[0] + d2[1] + d2[2];
+    }
+    const Shift<T> sh = shift_of<T>(ph);
+    T nu, ka;
+    visc_consts(ph, nu, ka);
+    T R[5];
+    assemble<T>(t, q, uc, nu, ka, sh.c_rho, sh.c_E, R);
+    stage_write<T, RESID>(rk, ph, g.n, s.c, Q64, R, out, Qs, Wnext);
+}
+
+// Recompute-some (Section 2, paragraph RS): the nine velocity gradients come
+// from the work arrays of the gradient pass (k_ss_grad); every other
+// derivative is written out as its formula inside the equation that uses it.
+// Equation E evaluates exactly the terms fd::assemble gives it, with the same
+// operations, so a derivative that several equations use is evaluated again
+// in each: the energy equation re-evaluates the three viscous terms of the
+// momentum equations, and every equation re-reads div u and the velocities.
+template <class T, int E, class Acc>
+__device__ __forceinline__ T rs_equation(const Acc& A, const Grid& g, const Phys& ph) {
+    constexpr int U = 5, P = 8, TT = 9;
+    T uc[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) uc[i] = A.center(U + i);
+    const T div = A.grad(0, 0) + A.grad(1, 1) + A.grad(2, 2);
+    const Shift<T> sh = shift_of<T>(ph);
+    T nu, ka;
+    visc_consts(ph, nu, ka);
+    T r = T(-0.5) * fmx(A.center(E), div, conv_of<T>(A, g, E, uc));
+    if constexpr (E == 0) {
+        r = fmx(-sh.c_rho, div, r);
+    } else if constexpr (E < 4) {
+        constexpr int i = E - 1;
+        T lap, gd;
+        viscous_of<T, true>(A, g, i, uc[i], lap, gd);
+        const T vi = nu * fmx(gd, T(1.0 / 3.0), lap);
+        r += vi - d1_of<T>(A, g, P, i);
+    } else {
+        r = fmx(-sh.c_E, div, r);
+        T work = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            T lap, gd;
+            viscous_of<T, true>(A, g, i, uc[i], lap, gd);
+            work = fmx(uc[i], nu * fmx(gd, T(1.0 / 3.0), lap), work);
+        }
+        T diss = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                T sij = A.grad(i, j) + A.grad(j, i);
+                if (i == j) sij = fmx(T(-2.0 / 3.0), div, sij);
+                diss = fmx(sij, A.grad(i, j), diss);
+            }
+        T dpu = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dpu += d1_prod_of<T>(A, g, P, U + j, j);
+        T lapT;
+        {
+            const T T0 = A.center(TT);
+            T d2[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) d2[j] = d2_of<T>(A, g, TT, j, T0);
+            lapT = d2[0] + d2[1] + d2[2];
+        }
+        r += fmx(nu, diss, fmx(ka, lapT, work)) - dpu;
+    }
+    return r;
+}
+
+// One thread per (point, equation): threadIdx.y is the equation, so a warp
+// (32 consecutive points of one equation) never diverges, and no derivative
+// is shared between the equations of a point, since each is evaluated by its
+// own thread.  Each thread updates its own conserved variable; the five new
+// values of a point meet in shared memory for the next-stage primitives.
+constexpr int kRsPoints = 64;
+
+template <class T, bool RESID>
+__global__ void __launch_bounds__(kRsPoints * 5) k_rs(Grid g, Phys ph, RKStage rk, const T* __restrict__ Qf,
+                                                      const T* __restrict__ Wf, const T* __restrict__ Gw,
+                                                      const state_t<T>* __restrict__ Q64,
+                                                      state_t<T>* __restrict__ out, state_t<T>* __restrict__ Qs,
+                                                      T* __restrict__ Wnext) {
+    using S = state_t<T>;
+    __shared__ S qn_sh[5][kRsPoints];
+    const int tx = threadIdx.x, e = threadIdx.y;
+    const int idx = blockIdx.x * kRsPoints + tx;
+    const int n = g.n;
+    const bool valid = idx < n;
+    if (valid) {
+        const Nbr s = make_nbr(g, idx);
+        const GlobalAcc<T> A{s, n, Qf, Wf, Gw};
+        T r;
+        switch (e) {
+            case 0: r = rs_equation<T, 0>(A, g, ph); break;
+            case 1: r = rs_equation<T, 1>(A, g, ph); break;
+            case 2: r = rs_equation<T, 2>(A, g, ph); break;
+            case 3: r = rs_equation<T, 3>(A, g, ph); break;
+            default: r = rs_equation<T, 4>(A, g, ph); break;
+        }
+        // the per-variable branch of stage_write
+        if (RESID) {
+            out[e * n + idx] = to_state(r);
+        } else {
+            const S qs = rk.stage == 0 ? Q64[e * n + idx] : Qs[e * n + idx];
+            const S qn = upd(rk_a(rk, S()), r, qs);
+            out[e * n + idx] = qn;
+            if (rk.stage < 2) Qs[e * n + idx] = upd(rk_b(rk, S()), r, qs);
+            qn_sh[e][tx] = qn;
+        }
+    }
+    if (RESID) return;
+    __syncthreads();
+    if (valid && e == 0) {
+        S q[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) q[f] = qn_sh[f][tx];
+        prims_point(ph, q, Wnext, n, idx);
+    }
+}
+
 // ------------------------------------------------------------- batched path
 // Many instances of different grids in one launch per kernel: a persistent
 // grid walks a work list of tiles (instance, first point, count) with a grid
@@ -1128,6 +1372,28 @@ cudaError_t launch_bl_res(const Grid& g, const Phys& ph, const RKStage& rk, bool
     return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t launch_sn(const Grid& g, const Phys& ph, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
+                      const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext, cudaStream_t st) {
+    if (resid)
+        k_sn<T, true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, ph, rk, Qf, Wf, Q64, out, Qs, Wnext);
+    else
+        k_sn<T, false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, ph, rk, Qf, Wf, Q64, out, Qs, Wnext);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_rs(const Grid& g, const Phys& ph, const RKStage& rk, bool resid, const T* Qf, const T* Wf,
+                      const T* Gw, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext,
+                      cudaStream_t st) {
+    const dim3 block(kRsPoints, 5);
+    if (resid)
+        k_rs<T, true><<<blocks_for(g.n, kRsPoints), block, 0, st>>>(g, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
+    else
+        k_rs<T, false><<<blocks_for(g.n, kRsPoints), block, 0, st>>>(g, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
+    return cudaGetLastError();
+}
+
 #define FD_INSTANTIATE(T)                                                                                        \
     template cudaError_t launch_ra<T>(const Grid&, const Coef<T>&, const Phys&, const RKStage&, bool, const T*,  \
                                       const T*, const state_t<T>*, state_t<T>*, state_t<T>*, T*, cudaStream_t); \
@@ -1140,7 +1406,11 @@ cudaError_t launch_bl_res(const Grid& g, const Phys& ph, const RKStage& rk, bool
     template cudaError_t launch_bl_d2<T>(const Grid&, const T*, const T*, T*, cudaStream_t);                    \
     template cudaError_t launch_bl_res<T>(const Grid&, const Phys&, const RKStage&, bool, const T*, const T*,    \
                                           const T*, const T*, const state_t<T>*, state_t<T>*, state_t<T>*, T*,  \
-                                          cudaStream_t);
+                                          cudaStream_t);                                                        \
+    template cudaError_t launch_sn<T>(const Grid&, const Phys&, const RKStage&, bool, const T*, const T*,        \
+                                      const state_t<T>*, state_t<T>*, state_t<T>*, T*, cudaStream_t);           \
+    template cudaError_t launch_rs<T>(const Grid&, const Phys&, const RKStage&, bool, const T*, const T*,        \
+                                      const T*, const state_t<T>*, state_t<T>*, state_t<T>*, T*, cudaStream_t);
 FD_INSTANTIATE(double)
 FD_INSTANTIATE(float)
 FD_INSTANTIATE(df64)

@@ -24,6 +24,8 @@ FD_EBUSY = -5
 FD_STORE_ALL = 0
 FD_STORE_SOME = 1
 FD_RECOMPUTE_ALL = 2
+FD_RECOMPUTE_SOME = 3
+FD_STORE_NONE = 4
 
 FD_F64 = 0
 FD_F32_ACCDW = 1

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 import paper_1610_09146_gb300 as fd  # noqa: E402
 
-VARIANTS = ["store_all", "store_some", "recompute_all"]
+VARIANTS = ["store_all", "store_some", "recompute_all", "recompute_some", "store_none"]
 
 
 @pytest.fixture(scope="module", autouse=True)
