@@ -525,6 +525,69 @@ def run_mixed512(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ long-time history
+
+
+def run_history(args):
+    """Taylor-Green vortex (Re 1600, M 0.1) integrated to t = args.t_end on one grid, in one
+    precision mode and family, sampling the kinetic energy and enstrophy every
+    args.sample_dt time units (Section 3, Fig. 3 shows these two curves).  The reference
+    curves of Wang et al. 2013 are not available, so the run checks what the equations fix
+    instead: at low Mach number the kinetic energy decays at the rate 2 nu Omega (the
+    incompressible energy identity, with O(M^2) compressible corrections), and a second
+    grid or precision mode must give the same curves."""
+    import numpy as np
+    import torch
+
+    import paper_1610_09146_gb300 as fd
+    torch.cuda.set_device(0)
+    fd.build()
+    n = args.grid
+    alg = args.variants[0]
+    dt = fd.dt_for_grid(n)
+    per = max(1, int(round(args.sample_dt / dt)))
+    nsamp = int(np.ceil(args.t_end / (per * dt)))
+    t, ke, en = [0.0], [], []
+    with fd.Solver(n, dt=dt, algorithm=alg, dtype=args.dtype) as s:
+        k0, e0 = s.diagnostics()
+        ke.append(k0)
+        en.append(e0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(nsamp):
+            s.step(per)
+            k, e = s.diagnostics()
+            t.append((i + 1) * per * dt)
+            ke.append(k)
+            en.append(e)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        finite = s.check_finite()
+    t, ke, en = np.array(t), np.array(ke), np.array(en)
+    nu = 1.0 / RE
+    eps = -(ke[2:] - ke[:-2]) / (t[2:] - t[:-2])       # -dKE/dt, central differences
+    two_nu_omega = 2 * nu * en[1:-1]
+    ip = int(np.argmax(eps))
+    ie = int(np.argmax(en))
+    line = {
+        "workload": f"Taylor-Green vortex {n}^3 to t = {args.t_end}, Re {RE:g}, M {MACH:g}, "
+                    f"{SHORT[alg]} family, dtype {args.dtype}",
+        "metric": METRIC, "unit": METRIC, "higher_is_better": True,
+        "value": n**3 * per * nsamp / sec, "seconds": sec, "grid": [n, n, n], "dt": dt,
+        "steps": per * nsamp, "dtype": args.dtype, "family": SHORT[alg], "finite": finite,
+        "summary": {
+            "ke_final": float(ke[-1]),
+            "enstrophy_peak": {"t": float(t[ie]), "value": float(en[ie])},
+            "dissipation_peak": {"t": float(t[1 + ip]), "value": float(eps[ip])},
+            "eps_minus_2nu_omega_at_peak_rel": float((eps[ip] - two_nu_omega[ip]) / eps[ip]),
+            "eps_minus_2nu_omega_max_rel": float(np.max(np.abs(eps - two_nu_omega)) / eps[ip]),
+        },
+        "series": {"t": [round(float(x), 6) for x in t], "ke": [float(x) for x in ke],
+                   "enstrophy": [float(x) for x in en]},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ serving
 
 
@@ -651,15 +714,17 @@ def main():
     ap.add_argument("--variants", nargs="+", default=VARIANTS, choices=VARIANTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-df64", action="store_true", help="skip the double-word (df64) families")
-    ap.add_argument("--workload", choices=["single", "batched", "serve", "mixed512"], default="single",
+    ap.add_argument("--workload", choices=["single", "batched", "serve", "mixed512", "history"], default="single",
                     help="single: the 256^3 line (default); batched / serve / mixed512: the ensemble, "
-                         "serving and 512^3 mixed-precision runs")
+                         "serving and 512^3 mixed-precision runs; history: KE / enstrophy to --t-end")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--solve-steps", type=int, default=100)
     ap.add_argument("--requests", type=int, default=120)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--arena-gb", type=int, default=64)
     ap.add_argument("--max-active", type=int, default=256)
+    ap.add_argument("--t-end", type=float, default=20.0)
+    ap.add_argument("--sample-dt", type=float, default=0.1)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -675,6 +740,10 @@ def main():
         if args.solve_steps == 100:
             args.solve_steps = 200
         run_mixed512(args)
+    elif args.workload == "history":
+        if args.variants == VARIANTS:
+            args.variants = ["recompute_all" if args.dtype == "f32" else "store_some"]
+        run_history(args)
     else:
         run_ours(args)
 
