@@ -18,6 +18,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -77,6 +78,9 @@ struct fd_handle {
     double* partial = nullptr;
     double* diag = nullptr;
     int* flag = nullptr;
+    int* kerr = nullptr;       // set by a kernel whose bounded wait ran out
+    bool use_tma = false;      // binary32 RA: planes staged by TMA (fmap[b] describes Wf[b])
+    CUtensorMap fmap[2]{};
     fd::Grid grid{};
     fd::Phys phys{};
     fd::Coef<double> kd{};  // fused-residual coefficients, binary64 mode
@@ -131,13 +135,15 @@ int check_args(int nx, int ny, int nz, double Re, double Mach, double Pr, double
 
 // Byte layout of a handle's single device allocation.
 struct Layout {
-    size_t q0, q1, qs, w0, w1, g, p, d1, d2, wf0, wf1, gf, wd0, wd1, gd, partial, diag, flag, total;
+    size_t q0, q1, qs, w0, w1, g, p, d1, d2, wf0, wf1, gf, wd0, wd1, gd, partial, diag, flag, kerr, total;
 };
 
 // SS and RS keep the nine velocity gradients in work arrays.
 bool stores_g(int algorithm) { return algorithm == FD_STORE_SOME || algorithm == FD_RECOMPUTE_SOME; }
 
-Layout plan(long long n, int algorithm, int dtype) {
+// wf_points: values per binary32 working field (n, or the ghost-padded size
+// of the TMA-staged recompute-all kernel).
+Layout plan(long long n, int algorithm, int dtype, size_t wf_points) {
     Layout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -170,8 +176,8 @@ Layout plan(long long n, int algorithm, int dtype) {
             L.d2 = take(18 * n * sizeof(double));
         }
     } else {
-        L.wf0 = take(10 * n * sizeof(float));
-        L.wf1 = take(10 * n * sizeof(float));
+        L.wf0 = take(10 * wf_points * sizeof(float));
+        L.wf1 = take(10 * wf_points * sizeof(float));
         if (stores_g(algorithm)) L.gf = take(9 * n * sizeof(float));
         if (algorithm == FD_STORE_ALL) {
             L.p = take(18 * n * sizeof(float));
@@ -182,6 +188,7 @@ Layout plan(long long n, int algorithm, int dtype) {
     L.partial = take(2 * fd::kDiagBlocks * sizeof(double));
     L.diag = take(2 * sizeof(double));
     L.flag = take(sizeof(int));
+    L.kerr = take(sizeof(int));
     L.total = off;
     return L;
 }
@@ -220,9 +227,13 @@ cudaError_t stage_kernels(fd_handle* h, const fd::RKStage& rk, bool resid, const
             // kernel is latency-bound on its tap loads); binary64 is bound by FP64
             // issue, where staging does not help.
             return timed(h, FD_KERNEL_FUSED, [&] {
-                if constexpr (std::is_same<T, float>::value)
+                if constexpr (std::is_same<T, float>::value) {
+                    if (h->use_tma)  // Qf is the first of the ten fields of Wf[0] or Wf[1]
+                        return fd::launch_ra_tma(h->fmap[Qf == h->Wf[0] ? 0 : 1], g, k, ph, rk, resid, Qin, Qout,
+                                                 reinterpret_cast<S*>(h->Qs), Wnext, h->kerr, st);
                     return fd::launch_ra_tiled<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, reinterpret_cast<S*>(h->Qs),
                                                   Wnext, st);
+                }
                 else
                     return fd::launch_ra<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, reinterpret_cast<S*>(h->Qs),
                                             Wnext, st);
@@ -296,7 +307,10 @@ cudaError_t run_stage(fd_handle* h, int s, bool resid, double* out) {
     using fd::df64;
     const df64* Qd = reinterpret_cast<const df64*>(Qin);
     if (!h->wvalid) {
-        e = timed(h, FD_KERNEL_PRIMS, [&] { return fd::launch_prims_f32(g, ph, Qd, h->Wf[wc], h->stream); });
+        e = timed(h, FD_KERNEL_PRIMS, [&] {
+            return h->use_tma ? fd::launch_prims_padded(g, ph, Qd, h->Wf[wc], h->stream)
+                              : fd::launch_prims_f32(g, ph, Qd, h->Wf[wc], h->stream);
+        });
         if (e != cudaSuccess) return e;
         h->wvalid = true;
     }
@@ -311,6 +325,20 @@ cudaError_t run_stage(fd_handle* h, int s, bool resid, double* out) {
 bool dw_state(int dtype) { return dtype != FD_F64; }
 
 fd::Shift5 state_shift(const fd_handle* h) { return fd::Shift5{{1.0, 0.0, 0.0, 0.0, h->phys.rhoE0}}; }
+
+// A kernel whose bounded wait ran out (TMA-staged binary32 RA) leaves a
+// nonzero error word; the synchronising calls report it.
+int check_kernel_error(fd_handle* h, const char* what) {
+    if (!h->use_tma) return FD_OK;
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, what);
+    if (v)
+        return h->fail(FD_ECUDA, "%s: %s; the state is not valid", what,
+                       v == 2 ? "the TMA ring was not 128-byte aligned" : "a staging wait in a kernel ran out");
+    return FD_OK;
+}
 
 cudaError_t state_to_binary64(fd_handle* h, double* dst) {
     return fd::launch_from_df64(reinterpret_cast<const fd::df64*>(h->Q[h->cur]), dst, h->n, state_shift(h),
@@ -348,7 +376,15 @@ int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, d
         delete h;
         return fail_global(FD_ECUDA, "fd_create: cudaGetDevice: %s", cudaGetErrorString(e));
     }
-    Layout L = plan(h->n, algorithm, dtype);
+    // binary32 recompute-all stages its planes with TMA where the grid allows it
+    // (FDGB300_NO_TMA=1 selects the thread-staged kernel, for comparison); its
+    // working fields then use the ghost-padded layout.
+    const fd::Grid grid0 = fd::make_grid(nx, ny, nz);
+    if (dtype == FD_F32_ACCDW && algorithm == FD_RECOMPUTE_ALL && fd::tma_staging_ok(grid0)) {
+        const char* off = std::getenv("FDGB300_NO_TMA");
+        h->use_tma = !(off && off[0] == '1');
+    }
+    Layout L = plan(h->n, algorithm, dtype, h->use_tma ? fd::padded_field_points(grid0) : (size_t)h->n);
     h->block_bytes = L.total;
     if (alloc) {
         h->alloc = *alloc;
@@ -395,6 +431,7 @@ int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, d
     h->partial = at<double>(h->block, L.partial);
     h->diag = at<double>(h->block, L.diag);
     h->flag = at<int>(h->block, L.flag);
+    h->kerr = at<int>(h->block, L.kerr);
 
     const double hx = 2.0 * fd::kPi / nx, hy = 2.0 * fd::kPi / ny, hz = 2.0 * fd::kPi / nz;
     h->grid = fd::make_grid(nx, ny, nz);
@@ -405,6 +442,21 @@ int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, d
     h->kf = fd::make_coef<float>(g, ph, true);
     h->kw = fd::make_coef<fd::df64>(g, ph, true);
 
+    e = cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess && h->use_tma) {
+        // the padding columns no point writes are copied but never read: zero them once
+        const size_t wf_bytes = 10 * fd::padded_field_points(g) * sizeof(float);
+        e = fd::prepare_ra_tma();
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaMemsetAsync(h->Wf[b], 0, wf_bytes, h->stream);
+            if (e == cudaSuccess) e = fd::encode_field_map(&h->fmap[b], h->Wf[b], g);
+        }
+    }
+    if (e != cudaSuccess) {
+        device_free(h);
+        delete h;
+        return fail_global(FD_ECUDA, "fd_create: staging set-up: %s", cudaGetErrorString(e));
+    }
     if (dw_state(dtype)) {
         e = fd::launch_tgv_ic(g, ph, hx, hy, hz, h->Qs, h->stream);
         if (e == cudaSuccess)
@@ -455,7 +507,7 @@ int fd_get_state(fd_handle* h, double* dst, size_t n_elems, int dst_is_device) {
                             dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "fd_get_state");
-    return FD_OK;
+    return check_kernel_error(h, "fd_get_state");
 }
 
 int fd_set_state(fd_handle* h, const double* src, size_t n_elems, int src_is_device) {
@@ -494,6 +546,7 @@ int fd_diagnostics(fd_handle* h, double* ke, double* enstrophy) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->diag, sizeof out, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "fd_diagnostics");
+    if (int rc = check_kernel_error(h, "fd_diagnostics")) return rc;
     if (ke) *ke = out[0];
     if (enstrophy) *enstrophy = out[1];
     return FD_OK;
@@ -523,7 +576,7 @@ int fd_residual(fd_handle* h, double* R, size_t n_elems, int dst_is_device) {
         e = cudaMemcpyAsync(R, h->Qs, n_elems * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "fd_residual");
-    return FD_OK;
+    return check_kernel_error(h, "fd_residual");
 }
 
 int fd_check_finite(fd_handle* h) {
@@ -540,6 +593,7 @@ int fd_check_finite(fd_handle* h) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "fd_check_finite");
+    if (int rc = check_kernel_error(h, "fd_check_finite")) return rc;
     if (flag) return h->fail(FD_EUNSTABLE, "state holds NaN or infinity");
     return FD_OK;
 }

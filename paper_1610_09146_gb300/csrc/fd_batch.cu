@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -50,6 +51,7 @@ constexpr int kDefaultTile = 1024;
 struct InstHost {
     fd_instance_desc d;
     int n;
+    bool padded;                   // TMA-staged binary32 RA: ghost-padded working fields
     size_t q0, q1, qs, w0, w1, g;  // byte offsets in the allocation
 };
 
@@ -69,6 +71,8 @@ struct fd_batch {
     int grid_ss_fused = 0, grid_ra_fused = 0, grid_grad = 0, grid_prims = 0;
     double* partial = nullptr;
     double* diag = nullptr;
+    int* kerr = nullptr;  // set by a kernel whose bounded wait ran out
+    bool ra_tma = false;  // binary32 RA instances staged by TMA (all of them qualify)
     int parity = 0;
     bool wvalid = false;
     cudaStream_t cap[2] = {nullptr, nullptr};      // capture streams
@@ -120,18 +124,30 @@ void fill_inst(const fd_batch* b, std::vector<fd::BatchInst<T>>& out) {
         I.W[0] = reinterpret_cast<T*>(b->base() + h.w0);
         I.W[1] = reinterpret_cast<T*>(b->base() + h.w1);
         I.G = h.g == (size_t)-1 ? nullptr : reinterpret_cast<T*>(b->base() + h.g);
+        I.padded = h.padded ? 1 : 0;
         for (int s = 0; s < 3; ++s) I.rk[s] = fd::make_stage(s, h.d.dt);
     }
 }
 
+// Tensor maps of the working fields of the TMA-staged binary32 RA instances.
+cudaError_t fill_maps(const fd_batch* b, std::vector<fd::BatchInst<float>>& out) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < b->count && e == cudaSuccess; ++i)
+        if (b->inst[i].padded)
+            for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = fd::encode_field_map(&out[i].fmap[w], out[i].W[w], out[i].g);
+    return e;
+}
+
 // Work items: point ranges of tile_points each, or (tiled) the x-y tile /
-// z-chunk pairs of the shared-memory recompute-all kernel.
+// z-chunk pairs of the shared-memory recompute-all kernel, thread-staged or
+// (b->ra_tma) TMA-staged.
 void make_tiles(const fd_batch* b, int family, bool tiled, std::vector<fd::BatchTile>& out) {
     for (int i = 0; i < b->count; ++i) {
         const InstHost& h = b->inst[i];
         if (family >= 0 && h.d.algorithm != family) continue;
         if (tiled) {
-            const int m = fd::tiled_work_items(h.d.nx, h.d.ny, h.d.nz);
+            const int m = b->ra_tma ? fd::tma_work_items(h.d.nx, h.d.ny, h.d.nz)
+                                    : fd::tiled_work_items(h.d.nx, h.d.ny, h.d.nz);
             for (int t = 0; t < m; ++t) out.push_back({i, t, 0});
             continue;
         }
@@ -156,8 +172,11 @@ cudaError_t enqueue_family(fd_batch* b, bool ss, int s, int p, cudaStream_t st) 
     }
     if (!b->n_ra) return cudaSuccess;
     return b->prof.timed(st, FD_KERNEL_FUSED, [&] {
-        if (sizeof(T) == sizeof(float))  // binary32: fields staged through shared memory
+        if constexpr (sizeof(T) == sizeof(float)) {  // binary32: fields staged through shared memory
+            if (b->ra_tma)
+                return fd::launch_batch_ra_tma(I, b->d_ra, b->n_ra, s, p, b->grid_ra_fused, b->kerr, st);
             return fd::launch_batch_ra_tiled<T>(I, b->d_ra, b->n_ra, s, p, b->grid_ra_fused, st);
+        }
         return fd::launch_batch_fused<T>(I, b->d_ra, b->n_ra, false, s, p, b->grid_ra_fused, st);
     });
 }
@@ -229,6 +248,20 @@ void release(fd_batch* b) {
     b->block = nullptr;
 }
 
+// A TMA-staged kernel whose bounded wait ran out leaves a nonzero error word;
+// the synchronising calls report it.
+int check_kernel_error(fd_batch* b, const char* what) {
+    if (!b->ra_tma) return FD_OK;
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, b->kerr, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return b->cuda_fail(e, what);
+    if (v)
+        return b->fail(FD_ECUDA, "%s: %s; the states are not valid", what,
+                       v == 2 ? "the TMA ring was not 128-byte aligned" : "a staging wait in a kernel ran out");
+    return FD_OK;
+}
+
 int ensure_prims(fd_batch* b) {
     if (b->wvalid) return FD_OK;
     cudaError_t e = b->prof.timed(b->stream, FD_KERNEL_PRIMS, [&] {
@@ -274,6 +307,14 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
     b->count = count;
     b->dtype = dtype;
     b->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (dtype == FD_F32_ACCDW) {  // TMA staging when every RA instance allows it
+        const char* off_env = std::getenv("FDGB300_NO_TMA");
+        b->ra_tma = !(off_env && off_env[0] == '1');
+        for (int i = 0; i < count; ++i)
+            if (desc[i].algorithm == FD_RECOMPUTE_ALL &&
+                !fd::tma_staging_ok(fd::make_grid(desc[i].nx, desc[i].ny, desc[i].nz)))
+                b->ra_tma = false;
+    }
     cudaError_t e = cudaGetDevice(&b->device);
     if (e != cudaSuccess) {
         delete b;
@@ -298,8 +339,10 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
         h.q0 = take(f5);
         h.q1 = take(f5);
         h.qs = take(f5);
-        h.w0 = take(wfields * h.n * tsize);
-        h.w1 = take(wfields * h.n * tsize);
+        h.padded = b->ra_tma && desc[i].algorithm == FD_RECOMPUTE_ALL;
+        const size_t wpts = h.padded ? fd::padded_field_points(fd::make_grid(h.d.nx, h.d.ny, h.d.nz)) : (size_t)h.n;
+        h.w0 = take(wfields * wpts * tsize);
+        h.w1 = take(wfields * wpts * tsize);
         h.g = desc[i].algorithm == FD_STORE_SOME ? take(9 * (size_t)h.n * tsize) : (size_t)-1;
     }
     std::vector<fd::BatchTile> t_ss, t_ra, t_all;
@@ -311,6 +354,7 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
     size_t o_all = take(t_all.size() * sizeof(fd::BatchTile));
     size_t o_part = take(2 * fd::kDiagBlocks * sizeof(double));
     size_t o_diag = take(2 * (size_t)count * sizeof(double));
+    size_t o_err = take(sizeof(int));
     b->block_bytes = off;
     if (alloc) {
         b->alloc = *alloc;
@@ -335,6 +379,7 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
     b->n_all = (int)t_all.size();
     b->partial = reinterpret_cast<double*>(b->base() + o_part);
     b->diag = reinterpret_cast<double*>(b->base() + o_diag);
+    b->kerr = reinterpret_cast<int*>(b->base() + o_err);
 
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -345,7 +390,12 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
         b->grid_grad = grid_for<double>(sms, false, false);
     } else {
         b->grid_ss_fused = grid_for<float>(sms, true, true);
-        b->grid_ra_fused = sms * fd::batch_tiled_blocks_per_sm<float>();
+        if (b->ra_tma) {
+            e = fd::prepare_ra_tma();
+            b->grid_ra_fused = sms * fd::batch_tma_blocks_per_sm();  // 115 KB ring per block
+        } else {
+            b->grid_ra_fused = sms * fd::batch_tiled_blocks_per_sm<float>();
+        }
         b->grid_grad = grid_for<float>(sms, false, false);
     }
     b->grid_prims = b->grid_grad;
@@ -360,7 +410,9 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
     } else {
         std::vector<fd::BatchInst<float>> I;
         fill_inst<float>(b, I);
-        e = cudaMemcpyAsync(b->d_inst, I.data(), I.size() * sizeof I[0], cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = fill_maps(b, I);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_inst, I.data(), I.size() * sizeof I[0], cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     }
     auto up = [&](fd::BatchTile* dst, const std::vector<fd::BatchTile>& v) {
@@ -371,6 +423,15 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
     up(b->d_ss, t_ss);
     up(b->d_ra, t_ra);
     up(b->d_all, t_all);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->kerr, 0, sizeof(int), b->stream);
+    // padded working fields: the padding columns no point writes are copied but never read
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        const InstHost& h = b->inst[i];
+        if (!h.padded) continue;
+        const size_t bytes = 10 * fd::padded_field_points(fd::make_grid(h.d.nx, h.d.ny, h.d.nz)) * sizeof(float);
+        e = cudaMemsetAsync(b->base() + h.w0, 0, bytes, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->base() + h.w1, 0, bytes, b->stream);
+    }
     // Taylor-Green initial state of every instance (Section 3).
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
         const InstHost& h = b->inst[i];
@@ -434,7 +495,7 @@ int fd_batch_get_state(fd_batch* b, int i, double* dst, size_t n_elems, int dst_
                             dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return b->cuda_fail(e, "fd_batch_get_state");
-    return FD_OK;
+    return check_kernel_error(b, "fd_batch_get_state");
 }
 
 int fd_batch_set_state(fd_batch* b, int i, const double* src, size_t n_elems, int src_is_device) {
@@ -479,6 +540,7 @@ int fd_batch_diagnostics(fd_batch* b, double* ke, double* enstrophy) {
         e = cudaMemcpyAsync(out.data(), b->diag, out.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return b->cuda_fail(e, "fd_batch_diagnostics");
+    if (int rc = check_kernel_error(b, "fd_batch_diagnostics")) return rc;
     for (int i = 0; i < b->count; ++i) {
         if (ke) ke[i] = out[2 * i];
         if (enstrophy) enstrophy[i] = out[2 * i + 1];

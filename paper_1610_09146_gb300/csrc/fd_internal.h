@@ -2,6 +2,7 @@
 // the C-ABI implementation (not part of the public interface).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "fd_core.cuh"
@@ -37,6 +38,22 @@ template <class T>
 cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid, const T* Qf,
                       const T* Wf, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext, cudaStream_t st);
 // RA with the fields staged through shared memory (same arithmetic as launch_ra).
+// binary32 recompute-all with TMA-staged planes.  Its ten working fields use a
+// ghost-padded layout, [10][nz][ny+4][nx+8] with the periodic images in the
+// padding (padded_field_points(g) values per field): launch_prims_padded
+// writes it from a state, and the kernel writes the next stage's fields in it.
+// `map` describes one such buffer (box 40 x 12 x 1 x 10, made by
+// encode_field_map); usable when tma_staging_ok(g).  prepare_ra_tma sets the
+// kernels' shared-memory size (host set-up, once per device).  A bounded wait
+// that runs out sets *err to 1 (2: the shared ring was misaligned).
+bool tma_staging_ok(const Grid& g);
+size_t padded_field_points(const Grid& g);
+cudaError_t launch_prims_padded(const Grid& g, const Phys& ph, const df64* Q, float* F, cudaStream_t st);
+cudaError_t encode_field_map(CUtensorMap* map, const float* F, const Grid& g);
+cudaError_t prepare_ra_tma();
+cudaError_t launch_ra_tma(const CUtensorMap& map, const Grid& g, const Coef<float>& k, const Phys& ph,
+                          const RKStage& rk, bool resid, const df64* Q64, df64* out, df64* Qs, float* Wnext,
+                          int* err, cudaStream_t st);
 template <class T>
 cudaError_t launch_ra_tiled(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid,
                             const T* Qf, const T* Wf, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext,
@@ -75,8 +92,10 @@ struct BatchInst {
     Phys ph;
     state_t<T>* Q[2];  // ping-pong state (binary64, or shifted double-words in the binary32 mode)
     state_t<T>* Qs;    // saved RK register
+    CUtensorMap fmap[2];  // binary32 RA with TMA staging: maps of W[0] / W[1] (else unused)
     T* W[2];       // working fields of Q[0] / Q[1] (binary64: 5 primitives; binary32: 10 perturbation fields)
     T* G;          // SS: nine velocity gradients (else null)
+    int padded;    // binary32 RA with TMA staging: W[] in the ghost-padded layout
     RKStage rk[3];  // a_s dt, b_s dt of each stage (binary64 and double-word)
 };
 
@@ -95,6 +114,15 @@ int batch_blocks_per_sm(bool fused, bool stored_g);
 int tiled_work_items(int nx, int ny, int nz);
 template <class T>
 int batch_tiled_blocks_per_sm();
+// Batched binary32 recompute-all with TMA-staged planes: work items are the
+// (32 x 8 tile, 64-plane z-chunk) pairs of an instance, numbered 0 ..
+// tma_work_items-1 in BatchTile::start; two blocks per SM where they fit
+// (each ring takes 115 KB of shared memory); prepare_ra_tma must have run on
+// the device.
+int tma_work_items(int nx, int ny, int nz);
+int batch_tma_blocks_per_sm();  // after prepare_ra_tma
+cudaError_t launch_batch_ra_tma(const BatchInst<float>* insts, const BatchTile* tiles, int ntiles, int stage,
+                                int parity, int grid, int* err, cudaStream_t st);
 template <class T>
 cudaError_t launch_batch_ra_tiled(const BatchInst<T>* insts, const BatchTile* tiles, int ntiles, int stage,
                                   int parity, int grid, cudaStream_t st);

@@ -18,6 +18,8 @@
 // On GB300 binary64 issues at 1/64 of the binary32 rate, so the binary64
 // kernels are bound by FP64 instructions per point, not by memory traffic;
 // stencil taps are read through the read-only data cache.
+#include <cuda.h>
+
 #include "fd_core.cuh"
 #include "fd_internal.h"
 
@@ -162,24 +164,72 @@ __device__ __forceinline__ void prims_point(const Phys& ph, const double q[5], d
 // 6-7 become
 //   p - p0 = (gamma-1)(E' - rho u_i u_i / 2),  T - 1 = (gamma M^2 (p-p0) - rho') / rho.
 __device__ __forceinline__ float to_f32(df64 x) { return __fadd_rn(x.hi, x.lo); }
-__device__ __forceinline__ void prims_point(const Phys& ph, const df64 q[5], float* __restrict__ F, int n, int c) {
+__device__ __forceinline__ void prims_values(const Phys& ph, const df64 q[5], float v[10]) {
     float rp = to_f32(q[0]);
     float Ep = to_f32(q[4]);
     float m0 = to_f32(q[1]), m1 = to_f32(q[2]), m2 = to_f32(q[3]);
     float inv = 1.0f / to_f32(q[0] + df64(1.0f, 0.0f));
-    float u = m0 * inv, v = m1 * inv, w = m2 * inv;
-    float pp = ph.gm1_w.hi * fmx(-0.5f, fmx(m0, u, fmx(m1, v, m2 * w)), Ep);
+    float u = m0 * inv, v_ = m1 * inv, w = m2 * inv;
+    float pp = ph.gm1_w.hi * fmx(-0.5f, fmx(m0, u, fmx(m1, v_, m2 * w)), Ep);
     float Tp = fmx(ph.gM2_w.hi, pp, -rp) * inv;
-    F[c] = rp;
-    F[n + c] = m0;
-    F[2 * n + c] = m1;
-    F[3 * n + c] = m2;
-    F[4 * n + c] = Ep;
-    F[5 * n + c] = u;
-    F[6 * n + c] = v;
-    F[7 * n + c] = w;
-    F[8 * n + c] = pp;
-    F[9 * n + c] = Tp;
+    v[0] = rp;
+    v[1] = m0;
+    v[2] = m1;
+    v[3] = m2;
+    v[4] = Ep;
+    v[5] = u;
+    v[6] = v_;
+    v[7] = w;
+    v[8] = pp;
+    v[9] = Tp;
+}
+__device__ __forceinline__ void prims_point(const Phys& ph, const df64 q[5], float* __restrict__ F, int n, int c) {
+    float v[10];
+    prims_values(ph, q, v);
+#pragma unroll
+    for (int f = 0; f < 10; ++f) F[(size_t)f * n + c] = v[f];
+}
+
+// Ghost-padded layout of the binary32 working fields of the TMA-staged
+// recompute-all kernel: each field is an (nx + 8) x (ny + 4) x nz array that
+// holds x = -4 .. nx+3 and y = -2 .. ny+1, and the cells x = -2, -1, nx, nx+1
+// and y = -2, -1, ny, ny+1 hold the periodic images, written by whoever writes
+// the point they copy.  Every TMA box is then inside the array (the columns
+// x = -4, -3, nx+2, nx+3 only pad the rows to 16-byte boundaries and are never
+// read), and no tile needs a special case at the periodic boundary.
+struct PadLayout {
+    int nx, ny, px, py;
+    long long np;  // points per padded field
+    __device__ __forceinline__ long long at(int x, int y, int z) const {
+        return ((long long)z * py + (y + 2)) * px + (x + 4);
+    }
+};
+__host__ __device__ __forceinline__ PadLayout pad_layout(const Grid& g) {
+    PadLayout L;
+    L.nx = g.nx;
+    L.ny = g.ny;
+    L.px = g.nx + 8;
+    L.py = g.ny + 4;
+    L.np = (long long)L.px * L.py * g.nz;
+    return L;
+}
+// Write the ten values of point (x, y, z) and its periodic images.
+__device__ __forceinline__ void put_padded(const PadLayout& L, float* __restrict__ F, int x, int y, int z,
+                                           const float v[10]) {
+    const int x2 = x < 2 ? x + L.nx : (x >= L.nx - 2 ? x - L.nx : x);
+    const int y2 = y < 2 ? y + L.ny : (y >= L.ny - 2 ? y - L.ny : y);
+    const int xs[2] = {x, x2}, ys[2] = {y, y2};
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        if (b == 1 && y2 == y) break;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            if (a == 1 && x2 == x) break;
+            const long long i = L.at(xs[a], ys[b], z);
+#pragma unroll
+            for (int f = 0; f < 10; ++f) F[f * L.np + i] = v[f];
+        }
+    }
 }
 
 // Double-word perturbation fields from the double-word state, which is itself
@@ -216,6 +266,20 @@ __global__ void __launch_bounds__(256) k_prims(Grid g, Phys ph, const state_t<T>
 #pragma unroll
     for (int f = 0; f < 5; ++f) q[f] = Q[f * n + idx];
     prims_point(ph, q, W, n, idx);
+}
+
+// The same, into the ghost-padded layout (TMA-staged binary32 recompute-all).
+__global__ void __launch_bounds__(256) k_prims_padded(Grid g, Phys ph, const df64* __restrict__ Q,
+                                                      float* __restrict__ F) {
+    int idx = grid_index();
+    if (idx >= g.n) return;
+    const int n = g.n;
+    df64 q[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) q[f] = Q[f * n + idx];
+    float v[10];
+    prims_values(ph, q, v);
+    put_padded(pad_layout(g), F, idx % g.nx, (idx / g.nx) % g.ny, idx / (g.nx * g.ny), v);
 }
 
 // RK update from a preloaded saved register qs (Q_in at stage 0, else Qs):
@@ -458,13 +522,15 @@ __global__ void __launch_bounds__(128) k_ra(Grid g, Coef<T> k, Phys ph, RKStage 
 constexpr int kTX = 32, kTY = 8, kSX = kTX + 4, kSY = kTY + 4, kPlane = kSX * kSY, kRing = 5, kNF = 10;
 constexpr int kZChunk = 64;
 
-template <class T>
-struct SmemAcc {
+// Shared-memory accessor over a ring of staged planes: plane slot s, field f,
+// row ty + OY + dy, column tx + OX + dx of an SX x SY array per field.
+template <class T, int SX, int SY, int OX, int OY>
+struct SmemAccT {
     const T* sm;
     int slot[5];  // ring slots of planes z-2 .. z+2
     int tx, ty;
     __device__ __forceinline__ T at(int f, int dz, int dy, int dx) const {
-        return sm[((slot[dz + 2] * kNF + f) * kSY + (ty + 2 + dy)) * kSX + (tx + 2 + dx)];
+        return sm[((slot[dz + 2] * kNF + f) * SY + (ty + OY + dy)) * SX + (tx + OX + dx)];
     }
     __device__ __forceinline__ static int d(int a) { return a < 2 ? a - 2 : a - 1; }
     __device__ __forceinline__ T center(int f) const { return at(f, 0, 0, 0); }
@@ -483,6 +549,8 @@ struct SmemAcc {
         }
     }
 };
+template <class T>
+using SmemAcc = SmemAccT<T, kSX, kSY, 2, 2>;
 
 // One tile (x0, y0) and z-chunk starting at zbeg, by one block of kTX x kTY
 // threads, with `sm` the block's ring of staged planes.
@@ -558,6 +626,227 @@ __global__ void __launch_bounds__(kTX* kTY, sizeof(T) == 4 ? 2 : 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ra_tiled_block<T, RESID>(reinterpret_cast<T*>(smem_raw), g, k, ph, rk, Qf, Wf, Q64, out, Qs, Wnext,
                              blockIdx.x * kTX, blockIdx.y * kTY, blockIdx.z * kZChunk);
+}
+
+// Recompute-all, binary32, with the planes staged by the Tensor Memory
+// Accelerator.  The ten working fields are one ghost-padded array (PadLayout)
+// [10][nz][ny+4][nx+8]; one four-dimensional TMA copy moves a 40 x 12 box of
+// all ten fields of one plane (the 32 x 8 tile, a two-point halo in y, and in
+// x a four-point halo so that the box starts on a 16-byte boundary) into a
+// ring of six plane slots, each with its own mbarrier.  While plane z is
+// evaluated, plane z+3 is already in flight, so no thread issues a staging
+// load and the copy latency is hidden behind the stencil arithmetic.  The
+// padding holds the periodic images, so boxes at the domain edge need nothing
+// special.  Every wait is bounded: a wait that runs out sets *err, drains the
+// copies in flight (again bounded) and ends the block.
+constexpr int kMX = 32, kMY = 8, kMThreads = kMX * kMY;
+constexpr int kBX = kMX + 8, kBY = kMY + 4, kBPlane = kBX * kBY;
+constexpr int kMSlots = 6, kMZChunk = 64;
+constexpr unsigned kMSlotBytes = kNF * kBPlane * 4;  // 19200, a multiple of 128
+// All of a block's shared memory is dynamic: the ring (6 x 19200 bytes, first,
+// so that it starts on the 128-byte boundary the TMA destination needs), the
+// six mbarriers, and in the batched kernel the staged instance record: two
+// blocks per SM, 2 x (115200 + 48 + 456 + 1024 reserved) <= 228 KB.
+constexpr long long kMWaitLimit = 1LL << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+    for (long long it = 0; it < kMWaitLimit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mbar_init_ring(unsigned bar0) {
+    for (int s = 0; s < kMSlots; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * s));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One (tile, z-chunk) work item of the TMA-staged kernel: tile origin (x0, y0),
+// planes zbeg .. min(nz, zbeg + kMZChunk) - 1.  `phase` holds the parity of the
+// next completion of each ring slot (bit s) and carries over between the work
+// items of a persistent block; every plane issued is waited for exactly once,
+// so it stays the same in every thread.  Returns false when a wait ran out;
+// the block has then drained its copies and must end.
+template <bool RESID>
+__device__ __forceinline__ bool ra_tma_item(float* sm, unsigned bar0, unsigned& phase, const CUtensorMap* map,
+                                            const Grid& g, const Coef<float>& k, const Phys& ph, const RKStage& rk,
+                                            const df64* __restrict__ Q64, df64* __restrict__ out,
+                                            df64* __restrict__ Qs, float* __restrict__ Wnext,
+                                            int* __restrict__ err, int x0, int y0, int zbeg) {
+    const int tid = threadIdx.x, tx = tid % kMX, ty = tid / kMX;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, n = g.n;
+    const int zend = min(nz, zbeg + kMZChunk);
+    const int zlast = zend + 1;  // last plane the item reads
+    const unsigned sm0 = smem_u32(sm);
+    const PadLayout L = pad_layout(g);
+    auto slot_of = [&](int p) { return (p - zbeg + 2) % kMSlots; };
+    auto issue = [&](int p) {  // one thread; padded coordinates of (x0 - 4, y0 - 2) are (x0, y0)
+        const int s = slot_of(p);
+        const unsigned bar = bar0 + 8 * s, dst = sm0 + s * kMSlotBytes;
+        const int zz = ((p % nz) + nz) % nz;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kMSlotBytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4, %5}], [%6];" ::"r"(dst),
+            "l"(reinterpret_cast<unsigned long long>(map)), "r"(x0), "r"(y0), "r"(zz), "r"(0), "r"(bar)
+            : "memory");
+    };
+    int consumed = zbeg - 3;  // planes up to here have been waited for (in order, with success)
+    auto wait = [&](int p) {
+        const int s = slot_of(p);
+        if (!mbar_wait(bar0 + 8 * s, (phase >> s) & 1u)) return false;
+        phase ^= 1u << s;
+        consumed = p;
+        return true;
+    };
+    // After a wait ran out: record it, wait (bounded) for every copy still in flight, end.
+    auto fail = [&](int issued) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            for (int p = consumed + 1; p <= issued; ++p) {
+                const int s = slot_of(p);
+                mbar_wait(bar0 + 8 * s, (phase >> s) & 1u);
+                phase ^= 1u << s;
+            }
+        }
+        __syncthreads();
+        return false;
+    };
+
+    int issued = zbeg + 2;
+    if (tid == 0)
+        for (int p = zbeg - 2; p <= issued; ++p) issue(p);
+    {
+        bool ok = true;
+        for (int p = zbeg - 2; p <= zbeg + 1 && ok; ++p) ok = wait(p);
+        if (__syncthreads_or(!ok)) return fail(issued);
+    }
+    const int x = x0 + tx, y = y0 + ty;
+    const bool inside = x < nx && y < ny;
+    for (int z = zbeg; z < zend; ++z) {
+        const int c = (z * ny + y) * nx + x;
+        if (z + 3 <= zlast) {
+            if (tid == 0) issue(z + 3);
+            issued = z + 3;
+        }
+        df64 qs[5];
+        if (!RESID && inside) {
+            const df64* src = rk.stage == 0 ? Q64 : Qs;
+#pragma unroll
+            for (int f = 0; f < 5; ++f) qs[f] = ld(src + (size_t)f * n, c);
+        }
+        if (__syncthreads_or(!wait(z + 2))) return fail(issued);
+        if (inside) {
+            SmemAccT<float, kBX, kBY, 4, 2> A{
+                sm, {slot_of(z - 2), slot_of(z - 1), slot_of(z), slot_of(z + 1), slot_of(z + 2)}, tx, ty};
+            float R[5];
+            fused_residual<float, false>(A, k, R);
+            if (RESID) {
+#pragma unroll
+                for (int f = 0; f < 5; ++f) out[(size_t)f * n + c] = to_state(R[f]);
+            } else {  // stage_update, with the next-stage fields into the padded layout
+                df64 qn[5];
+#pragma unroll
+                for (int f = 0; f < 5; ++f) {
+                    qn[f] = upd(rk_a(rk, df64()), R[f], qs[f]);
+                    out[(size_t)f * n + c] = qn[f];
+                    if (rk.stage < 2) Qs[(size_t)f * n + c] = upd(rk_b(rk, df64()), R[f], qs[f]);
+                }
+                float v[10];
+                prims_values(ph, qn, v);
+                put_padded(L, Wnext, x, y, z, v);
+            }
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// The ring must start on a 128-byte boundary (the TMA destination rule); the
+// dynamic shared window is declared so aligned, and a block that finds it
+// otherwise reports it (*err = 2) and issues no copy.
+__device__ __forceinline__ bool tma_ring_aligned(const unsigned char* raw, int* err) {
+    if ((smem_u32(raw) & 127) == 0) return true;
+    if (threadIdx.x == 0) atomicExch(err, 2);
+    return false;
+}
+
+template <bool RESID>
+__global__ void __launch_bounds__(kMThreads, 2)
+    k_ra_tma(const __grid_constant__ CUtensorMap map, Grid g, Coef<float> k, Phys ph, RKStage rk,
+             const df64* __restrict__ Q64, df64* __restrict__ out, df64* __restrict__ Qs,
+             float* __restrict__ Wnext, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    if (!tma_ring_aligned(smem_raw, err)) return;
+    const unsigned bar0 = smem_u32(smem_raw + kMSlots * kMSlotBytes);
+    if (threadIdx.x == 0) mbar_init_ring(bar0);
+    __syncthreads();
+    unsigned phase = 0;
+    ra_tma_item<RESID>(reinterpret_cast<float*>(smem_raw), bar0, phase, &map, g, k, ph, rk, Q64, out, Qs, Wnext,
+                       err, blockIdx.x * kMX, blockIdx.y * kMY, blockIdx.z * kMZChunk);
+}
+
+// Batched form: a persistent grid walks the (tile, z-chunk) items of the
+// binary32 recompute-all instances, numbered as tma_work_items counts them;
+// each instance record carries the tensor maps of its two working-field
+// buffers, which the copies read from global memory.  Only what an item needs
+// of the record is staged in shared memory (two blocks per SM leave 512 bytes
+// beside the two rings, for the barriers and this record).
+struct TmaItem {
+    Grid g;
+    Coef<float> k;
+    Phys ph;
+    RKStage rk;
+    const df64* Q64;
+    df64* out;
+    df64* Qs;
+    float* Wnext;
+};
+
+template <bool RESID>
+__global__ void __launch_bounds__(kMThreads, 2)
+    k_batch_ra_tma(const BatchInst<float>* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
+                   int stage, int parity, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TmaItem& it = *reinterpret_cast<TmaItem*>(smem_raw + kMSlots * kMSlotBytes + 8 * kMSlots);
+    if (!tma_ring_aligned(smem_raw, err)) return;
+    const unsigned bar0 = smem_u32(smem_raw + kMSlots * kMSlotBytes);
+    if (threadIdx.x == 0) mbar_init_ring(bar0);
+    unsigned phase = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const BatchInst<float>& I = insts[tl.inst];
+            it.g = I.g;
+            it.k = I.k;
+            it.ph = I.ph;
+            it.rk = I.rk[stage];
+            it.Q64 = I.Q[parity];
+            it.out = I.Q[1 - parity];
+            it.Qs = I.Qs;
+            it.Wnext = I.W[1 - parity];
+        }
+        __syncthreads();
+        const int ntx = (it.g.nx + kMX - 1) / kMX, nty = (it.g.ny + kMY - 1) / kMY;
+        const int zc = tl.start / (ntx * nty), r = tl.start % (ntx * nty);
+        if (!ra_tma_item<RESID>(reinterpret_cast<float*>(smem_raw), bar0, phase, &insts[tl.inst].fmap[parity],
+                                it.g, it.k, it.ph, it.rk, it.Q64, it.out, it.Qs, it.Wnext, err,
+                                (r % ntx) * kMX, (r / ntx) * kMY, zc * kMZChunk))
+            return;
+    }
 }
 
 // ------------------------------------------------------------------ SS
@@ -1072,6 +1361,15 @@ __global__ void __launch_bounds__(256) k_batch_prims(const BatchInst<T>* __restr
             state_t<T> q[5];
 #pragma unroll
             for (int f = 0; f < 5; ++f) q[f] = I.Q[parity][f * n + c];
+            if constexpr (sizeof(T) == sizeof(float)) {
+                if (I.padded) {  // TMA-staged recompute-all instance: ghost-padded fields
+                    float v[10];
+                    prims_values(I.ph, q, v);
+                    put_padded(pad_layout(I.g), I.W[parity], c % I.g.nx, (c / I.g.nx) % I.g.ny,
+                               c / (I.g.nx * I.g.ny), v);
+                    continue;
+                }
+            }
             prims_point(I.ph, q, I.W[parity], n, c);
         }
     }
@@ -1323,6 +1621,90 @@ cudaError_t launch_ra_tiled(const Grid& g, const Coef<T>& k, const Phys& ph, con
             return e;
         k_ra_tiled<T, false><<<grid, kTX * kTY, smem, st>>>(g, k, ph, rk, Qf, Wf, Q64, out, Qs, Wnext);
     }
+    return cudaGetLastError();
+}
+
+bool tma_staging_ok(const Grid& g) { return g.nx % 4 == 0 && g.nx >= 8 && g.ny >= 4; }
+
+size_t padded_field_points(const Grid& g) { return (size_t)pad_layout(g).np; }
+
+cudaError_t launch_prims_padded(const Grid& g, const Phys& ph, const df64* Q, float* F, cudaStream_t st) {
+    k_prims_padded<<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, Q, F);
+    return cudaGetLastError();
+}
+
+size_t tma_smem_bytes() { return (size_t)kMSlots * kMSlotBytes + 8 * kMSlots; }
+size_t batch_tma_smem_bytes() { return tma_smem_bytes() + sizeof(TmaItem); }
+
+cudaError_t launch_ra_tma(const CUtensorMap& map, const Grid& g, const Coef<float>& k, const Phys& ph,
+                          const RKStage& rk, bool resid, const df64* Q64, df64* out, df64* Qs, float* Wnext,
+                          int* err, cudaStream_t st) {
+    const dim3 grid((g.nx + kMX - 1) / kMX, (g.ny + kMY - 1) / kMY, (g.nz + kMZChunk - 1) / kMZChunk);
+    const size_t smem = tma_smem_bytes();
+    if (resid) {
+        k_ra_tma<true><<<grid, kMThreads, smem, st>>>(map, g, k, ph, rk, Q64, out, Qs, Wnext, err);
+    } else {
+        k_ra_tma<false><<<grid, kMThreads, smem, st>>>(map, g, k, ph, rk, Q64, out, Qs, Wnext, err);
+    }
+    return cudaGetLastError();
+}
+
+// Tensor map of the ten ghost-padded binary32 working fields (PadLayout) with
+// the box the kernel copies; the encoder is the driver's, looked up once.
+cudaError_t encode_field_map(CUtensorMap* map, const float* F, const Grid& g) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<Encode>(p);
+    }();
+    if (!encode) return cudaErrorNotSupported;
+    if (!tma_staging_ok(g) || (reinterpret_cast<uintptr_t>(F) & 15)) return cudaErrorInvalidValue;
+    const PadLayout L = pad_layout(g);
+    const cuuint64_t dims[4] = {(cuuint64_t)L.px, (cuuint64_t)L.py, (cuuint64_t)g.nz, (cuuint64_t)kNF};
+    const cuuint64_t strides[3] = {(cuuint64_t)L.px * 4, (cuuint64_t)L.px * L.py * 4, (cuuint64_t)L.np * 4};
+    const cuuint32_t box[4] = {kBX, kBY, 1, kNF};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(F), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t prepare_ra_tma() {
+    const int smem = (int)tma_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_ra_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ra_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_ra_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)batch_tma_smem_bytes());
+    return e;
+}
+
+int batch_tma_blocks_per_sm() {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_ra_tma<false>, kMThreads, batch_tma_smem_bytes()) !=
+            cudaSuccess ||
+        b < 1)
+        b = 1;
+    return b;
+}
+
+int tma_work_items(int nx, int ny, int nz) {
+    return ((nx + kMX - 1) / kMX) * ((ny + kMY - 1) / kMY) * ((nz + kMZChunk - 1) / kMZChunk);
+}
+
+cudaError_t launch_batch_ra_tma(const BatchInst<float>* insts, const BatchTile* tiles, int ntiles, int stage,
+                                int parity, int grid, int* err, cudaStream_t st) {
+    if (ntiles == 0) return cudaSuccess;
+    k_batch_ra_tma<false><<<grid, kMThreads, batch_tma_smem_bytes(), st>>>(insts, tiles, ntiles, stage, parity, err);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <deque>
@@ -94,13 +95,19 @@ class Arena {
 
 struct Layout {
     size_t q0, q1, qs, w0, w1, g, total;
+    bool padded;  // binary32 RA staged by TMA: ghost-padded working fields
 };
 
-Layout layout_of(const fd_request& r) {
+// tma: whether TMA staging may be used (a binary32 RA solve on a grid that
+// allows it then gets the ghost-padded working-field layout, a little larger).
+Layout layout_of(const fd_request& r, bool tma) {
     const size_t n = (size_t)r.nx * r.ny * r.nz;
     const size_t t = r.dtype == FD_F64 ? sizeof(double) : sizeof(float);
     const size_t wf = r.dtype == FD_F64 ? 5 : 10;
     Layout L{};
+    const fd::Grid g = fd::make_grid(r.nx, r.ny, r.nz);
+    L.padded = tma && r.dtype != FD_F64 && r.algorithm == FD_RECOMPUTE_ALL && fd::tma_staging_ok(g);
+    const size_t wpts = L.padded ? fd::padded_field_points(g) : n;
     size_t off = 0;
     auto take = [&](size_t b) {
         size_t at = off;
@@ -110,8 +117,8 @@ Layout layout_of(const fd_request& r) {
     L.q0 = take(5 * n * sizeof(double));
     L.q1 = take(5 * n * sizeof(double));
     L.qs = take(5 * n * sizeof(double));
-    L.w0 = take(wf * n * t);
-    L.w1 = take(wf * n * t);
+    L.w0 = take(wf * wpts * t);
+    L.w1 = take(wf * wpts * t);
     L.g = r.algorithm == FD_STORE_SOME ? take(9 * n * t) : (size_t)-1;
     L.total = off;
     return L;
@@ -152,6 +159,9 @@ struct fd_server {
     size_t fixed_bytes = 0;
     double* partial = nullptr;
     double* results = nullptr;  // 2 * max_active
+    int* kerr = nullptr;        // set by a kernel whose bounded wait ran out
+    bool tma_allowed = true;    // FDGB300_NO_TMA=1 at creation turns TMA staging off
+    int tma_blocks = 1;         // resident TMA-staged blocks per SM
     // growable buffers for tables and tiles
     void* tab = nullptr;
     size_t tab_bytes = 0;
@@ -163,8 +173,9 @@ struct fd_server {
     long long submitted = 0, completed = 0, ticks = 0;
     // current device views (valid after a rebuild)
     void* inst[2] = {nullptr, nullptr};  // [0] double table, [1] float table
-    fd::BatchTile* tiles[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [dtype][family: 0 SS, 1 RA]
-    int ntiles[2][2] = {{0, 0}, {0, 0}};
+    // [dtype][family: 0 SS, 1 RA, 2 RA staged by TMA (binary32, padded layout)]
+    fd::BatchTile* tiles[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int ntiles[2][3] = {{0, 0, 0}, {0, 0, 0}};
     fd::BatchTile* fresh_tiles[2] = {nullptr, nullptr};
     int nfresh[2] = {0, 0};
     std::string err;
@@ -215,13 +226,14 @@ fd::BatchInst<T> record(const fd_server* s, const Active& a) {
     I.W[0] = reinterpret_cast<T*>(b + a.L.w0);
     I.W[1] = reinterpret_cast<T*>(b + a.L.w1);
     I.G = a.L.g == (size_t)-1 ? nullptr : reinterpret_cast<T*>(b + a.L.g);
+    I.padded = a.L.padded ? 1 : 0;
     for (int st = 0; st < 3; ++st) I.rk[st] = fd::make_stage(st, a.r.dt);
     return I;
 }
 
-void append_tiles(const Active& a, std::vector<fd::BatchTile>& v, bool tiled = false) {
+void append_tiles(const Active& a, std::vector<fd::BatchTile>& v, bool tiled = false, bool tma = false) {
     if (tiled) {  // x-y tile / z-chunk work items of the shared-memory recompute-all kernel
-        const int m = fd::tiled_work_items(a.r.nx, a.r.ny, a.r.nz);
+        const int m = tma ? fd::tma_work_items(a.r.nx, a.r.ny, a.r.nz) : fd::tiled_work_items(a.r.nx, a.r.ny, a.r.nz);
         for (int t = 0; t < m; ++t) v.push_back({a.slot, t, 0});
         return;
     }
@@ -234,7 +246,8 @@ void append_tiles(const Active& a, std::vector<fd::BatchTile>& v, bool tiled = f
 cudaError_t rebuild(fd_server* s) {
     std::vector<fd::BatchInst<double>> I64;
     std::vector<fd::BatchInst<float>> I32;
-    std::vector<fd::BatchTile> t[2][2], f[2];
+    std::vector<fd::BatchTile> t[2][3], f[2];
+    cudaError_t e;
     for (auto& a : s->active) {
         const int d = a.r.dtype == FD_F64 ? 0 : 1;
         if (d == 0) {
@@ -243,9 +256,13 @@ cudaError_t rebuild(fd_server* s) {
         } else {
             a.slot = (int)I32.size();
             I32.push_back(record<float>(s, a));
+            if (a.L.padded)
+                for (int w = 0; w < 2; ++w)
+                    if ((e = fd::encode_field_map(&I32.back().fmap[w], I32.back().W[w], I32.back().g)) != cudaSuccess)
+                        return e;
         }
         const bool ss = a.r.algorithm == FD_STORE_SOME;
-        append_tiles(a, t[d][ss ? 0 : 1], !ss && d == 1);
+        append_tiles(a, t[d][ss ? 0 : (a.L.padded ? 2 : 1)], !ss && d == 1, a.L.padded);
         if (a.fresh) append_tiles(a, f[d]);
     }
     size_t off = 0;
@@ -256,12 +273,11 @@ cudaError_t rebuild(fd_server* s) {
     };
     size_t o64 = take(I64.size() * sizeof(fd::BatchInst<double>));
     size_t o32 = take(I32.size() * sizeof(fd::BatchInst<float>));
-    size_t ot[2][2], of[2];
+    size_t ot[2][3], of[2];
     for (int d = 0; d < 2; ++d) {
-        for (int k = 0; k < 2; ++k) ot[d][k] = take(t[d][k].size() * sizeof(fd::BatchTile));
+        for (int k = 0; k < 3; ++k) ot[d][k] = take(t[d][k].size() * sizeof(fd::BatchTile));
         of[d] = take(f[d].size() * sizeof(fd::BatchTile));
     }
-    cudaError_t e;
     if (off > s->tab_bytes) {
         if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return e;
         s->dev_free(s->tab, s->tab_bytes);
@@ -280,7 +296,7 @@ cudaError_t rebuild(fd_server* s) {
     s->inst[0] = b + o64;
     s->inst[1] = b + o32;
     for (int d = 0; d < 2; ++d) {
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < 3; ++k) {
             if ((e = up(ot[d][k], t[d][k].data(), t[d][k].size() * sizeof(fd::BatchTile))) != cudaSuccess) return e;
             s->tiles[d][k] = reinterpret_cast<fd::BatchTile*>(b + ot[d][k]);
             s->ntiles[d][k] = (int)t[d][k].size();
@@ -303,9 +319,10 @@ cudaError_t run_group(fd_server* s, int d) {
             cudaSuccess)
             return e;
     }
-    const bool tiled = sizeof(T) == sizeof(float);  // binary32 RA: shared-memory kernel
+    const bool tiled = sizeof(T) == sizeof(float);  // binary32 RA: shared-memory kernels
     const int gs = s->sms * fd::batch_blocks_per_sm<T>(true, true);
     const int gr = s->sms * (tiled ? fd::batch_tiled_blocks_per_sm<T>() : fd::batch_blocks_per_sm<T>(true, false));
+    const int gt = s->sms * s->tma_blocks;
     for (int st = 0, p = s->parity; st < 3; ++st, p ^= 1) {
         if (s->ntiles[d][0]) {
             if ((e = fd::launch_batch_grad<T>(I, s->tiles[d][0], s->ntiles[d][0], p, gg, s->stream)) != cudaSuccess)
@@ -315,9 +332,17 @@ cudaError_t run_group(fd_server* s, int d) {
                 return e;
         }
         if (s->ntiles[d][1]) {
-            e = tiled ? fd::launch_batch_ra_tiled<T>(I, s->tiles[d][1], s->ntiles[d][1], st, p, gr, s->stream)
-                      : fd::launch_batch_fused<T>(I, s->tiles[d][1], s->ntiles[d][1], false, st, p, gr, s->stream);
+            if constexpr (sizeof(T) == sizeof(float))
+                e = fd::launch_batch_ra_tiled<T>(I, s->tiles[d][1], s->ntiles[d][1], st, p, gr, s->stream);
+            else
+                e = fd::launch_batch_fused<T>(I, s->tiles[d][1], s->ntiles[d][1], false, st, p, gr, s->stream);
             if (e != cudaSuccess) return e;
+        }
+        if constexpr (sizeof(T) == sizeof(float)) {
+            if (s->ntiles[d][2]) {
+                e = fd::launch_batch_ra_tma(I, s->tiles[d][2], s->ntiles[d][2], st, p, gt, s->kerr, s->stream);
+                if (e != cudaSuccess) return e;
+            }
         }
     }
     return cudaSuccess;
@@ -335,7 +360,7 @@ void release_all(fd_server* s) {
 
 extern "C" {
 
-size_t fd_server_footprint(const fd_request* req) { return check_request(req) ? 0 : layout_of(*req).total; }
+size_t fd_server_footprint(const fd_request* req) { return check_request(req) ? 0 : layout_of(*req, true).total; }
 
 int fd_server_create(fd_server** out, size_t arena_bytes, int max_active, const fd_alloc* alloc, void* cuda_stream) {
     if (!out) return fail_global(FD_EINVAL, "fd_server_create: out is NULL");
@@ -362,7 +387,8 @@ int fd_server_create(fd_server** out, size_t arena_bytes, int max_active, const 
         return fail_global(FD_ENOMEM, "fd_server_create: arena of %zu bytes could not be allocated", arena_bytes);
     }
     s->arena = Arena(arena_bytes);
-    s->fixed_bytes = align256(2 * fd::kDiagBlocks * sizeof(double)) + align256(2 * (size_t)max_active * sizeof(double));
+    s->fixed_bytes = align256(2 * fd::kDiagBlocks * sizeof(double)) + align256(2 * (size_t)max_active * sizeof(double)) +
+                     align256(sizeof(int));
     s->fixed = s->dev_alloc(s->fixed_bytes);
     if (!s->fixed) {
         release_all(s);
@@ -371,6 +397,20 @@ int fd_server_create(fd_server** out, size_t arena_bytes, int max_active, const 
     }
     s->partial = static_cast<double*>(s->fixed);
     s->results = reinterpret_cast<double*>(static_cast<char*>(s->fixed) + align256(2 * fd::kDiagBlocks * sizeof(double)));
+    s->kerr = reinterpret_cast<int*>(reinterpret_cast<char*>(s->results) + align256(2 * (size_t)max_active * sizeof(double)));
+    const char* off_env = std::getenv("FDGB300_NO_TMA");
+    s->tma_allowed = !(off_env && off_env[0] == '1');
+    cudaError_t e = cudaMemsetAsync(s->kerr, 0, sizeof(int), s->stream);
+    if (e == cudaSuccess && s->tma_allowed) {
+        e = fd::prepare_ra_tma();
+        s->tma_blocks = fd::batch_tma_blocks_per_sm();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        release_all(s);
+        delete s;
+        return fail_global(FD_ECUDA, "fd_server_create: set-up: %s", cudaGetErrorString(e));
+    }
     *out = s;
     return FD_OK;
 }
@@ -378,7 +418,7 @@ int fd_server_create(fd_server** out, size_t arena_bytes, int max_active, const 
 int fd_server_submit(fd_server* s, const fd_request* req) {
     if (!s) return fail_global(FD_EINVAL, "fd_server_submit: NULL server");
     if (const char* why = check_request(req)) return s->fail(FD_EINVAL, "fd_server_submit: %s", why);
-    size_t need = layout_of(*req).total;
+    size_t need = layout_of(*req, s->tma_allowed).total;
     if (need > s->arena.capacity())
         return s->fail(FD_EBUSY, "fd_server_submit: footprint %zu bytes exceeds the arena (%zu)", need,
                        s->arena.capacity());
@@ -421,7 +461,7 @@ int fd_server_tick(fd_server* s, int* active_out) {
     }
     // 2. admission: first fit in submission order
     for (auto it = s->queue.begin(); it != s->queue.end() && (int)s->active.size() < s->max_active;) {
-        Layout L = layout_of(*it);
+        Layout L = layout_of(*it, s->tma_allowed);
         size_t off = 0;
         if (!s->arena.alloc(L.total, &off)) {
             ++it;
@@ -443,6 +483,11 @@ int fd_server_tick(fd_server* s, int* active_out) {
         if (e == cudaSuccess && a.r.dtype != FD_F64)
             e = fd::launch_to_df64(ic, reinterpret_cast<fd::df64*>(Q), a.n, fd::Shift5{{1.0, 0.0, 0.0, 0.0, ph.rhoE0}},
                                    s->stream);
+        if (L.padded) {  // padding columns no point writes are copied but never read: zero them
+            const size_t bytes = 10 * fd::padded_field_points(g) * sizeof(float);
+            if (e == cudaSuccess) e = cudaMemsetAsync(s->base() + off + L.w0, 0, bytes, s->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(s->base() + off + L.w1, 0, bytes, s->stream);
+        }
         if (e != cudaSuccess) {
             s->arena.release(off, L.total);
             return s->cuda_fail(e, "fd_server_tick: initial condition");
@@ -493,6 +538,15 @@ int fd_server_tick(fd_server* s, int* active_out) {
         e = cudaMemcpyAsync(res.data(), s->results, res.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "fd_server_tick");
+    if (s->ntiles[1][2]) {
+        int v = 0;
+        e = cudaMemcpyAsync(&v, s->kerr, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return s->cuda_fail(e, "fd_server_tick");
+        if (v)
+            return s->fail(FD_ECUDA, "fd_server_tick: %s; the states are not valid",
+                           v == 2 ? "the TMA ring was not 128-byte aligned" : "a staging wait in a kernel ran out");
+    }
     for (size_t k = fin.size(); k-- > 0;) {
         Active& a = s->active[fin[k]];
         double ke = res[2 * k], en = res[2 * k + 1];
