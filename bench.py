@@ -525,6 +525,72 @@ def run_mixed512(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- size sweep
+
+
+def run_sweep(args):
+    """Roofline sweep over grid sizes (128^3, 256^3, 384^3 by default): every family in
+    binary64 and the fastest binary32 / df64 families, each timed in three windows of K steps
+    after a warm-up (CUDA events on the solver's stream; the median window is reported), with
+    the dominant kernel placed on its roofline as in the single-grid line."""
+    import numpy as np
+    import torch
+
+    import paper_1610_09146_gb300 as fd
+    from paper_1610_09146_gb300 import native
+    torch.cuda.set_device(0)
+    fd.build()
+    hbm_peak, hbm_src = measured_peaks()
+    stream = torch.cuda.Stream()
+    cases = [("f64", a) for a in VARIANTS] + [("f32", "recompute_all"), ("f32", "store_some"),
+                                              ("df64", "store_some"), ("df64", "store_none")]
+    out = {}
+    for n in args.sizes:
+        npts = n**3
+        steps = max(2, int(round(args.steps * (256 / n) ** 3)))
+        res = {}
+        for dtype, alg in cases:
+            with fd.Solver(n, Re=RE, Mach=MACH, Pr=PR, gamma=GAMMA, dt=fd.dt_for_grid(n), algorithm=alg,
+                           dtype=dtype, stream=stream) as s:
+                s.step(args.warmup)
+                windows, kerns = [], []
+                for _ in range(3):
+                    torch.cuda.synchronize()
+                    native.fd_profile(s.h, 1)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    s.step(steps)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    windows.append(e0.elapsed_time(e1) / steps)
+                    kern = {}
+                    for c, name in enumerate(native.KERNEL_CLASS_NAMES):
+                        tot, cnt = native.fd_profile_read(s.h, c)
+                        if cnt:
+                            kern[name] = {"ms_total": tot, "launches": cnt, "ms_avg": tot / cnt}
+                    native.fd_profile(s.h, 0)
+                    kerns.append(kern)
+                finite = s.check_finite()
+            i = int(np.argsort(windows)[1])  # the median window
+            ms = windows[i]
+            rl = roofline_of("f64" if dtype == "df64" else dtype, alg, kerns[i], npts, hbm_peak, hbm_src)
+            res[f"{dtype}:{SHORT[alg]}"] = {
+                "ms_per_step": round(ms, 4), "point_updates_per_s": npts / (ms / 1e3), "finite": finite,
+                "windows_ms": [round(w, 4) for w in windows],
+                "kernels_ms": {k: round(v["ms_avg"], 4) for k, v in kerns[i].items()},
+                "roofline": {k: rl[k] for k in ("kernel", "bound", "achieved", "unit", "frac", "share")}
+                            | ({"fp64_pipe_frac": rl["fp64_pipe_frac"], "hbm_frac": rl["hbm_frac"]}
+                               if dtype == "f64" else {}),
+            }
+        out[str(n)] = {"steps_per_window": steps, "results": res}
+    line = {"workload": "roofline sweep over grid sizes, Taylor-Green vortex, every family", "metric": METRIC,
+            "unit": METRIC, "sizes": args.sizes, "hbm_peak_gbs": hbm_peak,
+            "fp64_peak_tflops": round(FP64_PEAK_TFLOPS, 4),
+            "note": "df64 rooflines count the binary64 algorithm's flops against the FP64 peak", "sweep": out}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------ long-time history
 
 
@@ -714,9 +780,11 @@ def main():
     ap.add_argument("--variants", nargs="+", default=VARIANTS, choices=VARIANTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-df64", action="store_true", help="skip the double-word (df64) families")
-    ap.add_argument("--workload", choices=["single", "batched", "serve", "mixed512", "history"], default="single",
+    ap.add_argument("--workload", choices=["single", "batched", "serve", "mixed512", "history", "sweep"],
+                    default="single",
                     help="single: the 256^3 line (default); batched / serve / mixed512: the ensemble, "
-                         "serving and 512^3 mixed-precision runs; history: KE / enstrophy to --t-end")
+                         "serving and 512^3 mixed-precision runs; history: KE / enstrophy to --t-end; "
+                         "sweep: every family at --sizes")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--solve-steps", type=int, default=100)
     ap.add_argument("--requests", type=int, default=120)
@@ -724,6 +792,7 @@ def main():
     ap.add_argument("--arena-gb", type=int, default=64)
     ap.add_argument("--max-active", type=int, default=256)
     ap.add_argument("--t-end", type=float, default=20.0)
+    ap.add_argument("--sizes", type=int, nargs="+", default=[128, 256, 384])
     ap.add_argument("--sample-dt", type=float, default=0.1)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -740,6 +809,10 @@ def main():
         if args.solve_steps == 100:
             args.solve_steps = 200
         run_mixed512(args)
+    elif args.workload == "sweep":
+        if args.steps == 100:
+            args.steps = 10
+        run_sweep(args)
     elif args.workload == "history":
         if args.variants == VARIANTS:
             args.variants = ["recompute_all" if args.dtype == "f32" else "store_some"]

@@ -73,6 +73,7 @@ struct fd_batch {
     double* diag = nullptr;
     int* kerr = nullptr;  // set by a kernel whose bounded wait ran out
     bool ra_tma = false;  // binary32 RA instances staged by TMA (all of them qualify)
+    int tma_zlen = 64;    // planes per TMA work item
     int parity = 0;
     bool wvalid = false;
     cudaStream_t cap[2] = {nullptr, nullptr};      // capture streams
@@ -146,7 +147,7 @@ void make_tiles(const fd_batch* b, int family, bool tiled, std::vector<fd::Batch
         const InstHost& h = b->inst[i];
         if (family >= 0 && h.d.algorithm != family) continue;
         if (tiled) {
-            const int m = b->ra_tma ? fd::tma_work_items(h.d.nx, h.d.ny, h.d.nz)
+            const int m = b->ra_tma ? fd::tma_work_items(h.d.nx, h.d.ny, h.d.nz, b->tma_zlen)
                                     : fd::tiled_work_items(h.d.nx, h.d.ny, h.d.nz);
             for (int t = 0; t < m; ++t) out.push_back({i, t, 0});
             continue;
@@ -174,7 +175,8 @@ cudaError_t enqueue_family(fd_batch* b, bool ss, int s, int p, cudaStream_t st) 
     return b->prof.timed(st, FD_KERNEL_FUSED, [&] {
         if constexpr (sizeof(T) == sizeof(float)) {  // binary32: fields staged through shared memory
             if (b->ra_tma)
-                return fd::launch_batch_ra_tma(I, b->d_ra, b->n_ra, s, p, b->grid_ra_fused, b->kerr, st);
+                return fd::launch_batch_ra_tma(I, b->d_ra, b->n_ra, s, p, b->grid_ra_fused, b->tma_zlen, b->kerr,
+                                               st);
             return fd::launch_batch_ra_tiled<T>(I, b->d_ra, b->n_ra, s, p, b->grid_ra_fused, st);
         }
         return fd::launch_batch_fused<T>(I, b->d_ra, b->n_ra, false, s, p, b->grid_ra_fused, st);
@@ -314,6 +316,15 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
             if (desc[i].algorithm == FD_RECOMPUTE_ALL &&
                 !fd::tma_staging_ok(fd::make_grid(desc[i].nx, desc[i].ny, desc[i].nz)))
                 b->ra_tma = false;
+        if (b->ra_tma) {  // work-item length for the persistent grid (two blocks per SM)
+            std::vector<int> dims;
+            for (int i = 0; i < count; ++i)
+                if (desc[i].algorithm == FD_RECOMPUTE_ALL) dims.insert(dims.end(), {desc[i].nx, desc[i].ny, desc[i].nz});
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            b->tma_zlen = fd::tma_batch_zchunk(dims.data(), (int)dims.size() / 3, 2 * (sms > 0 ? sms : 152));
+        }
     }
     cudaError_t e = cudaGetDevice(&b->device);
     if (e != cudaSuccess) {

@@ -115,14 +115,16 @@ int tiled_work_items(int nx, int ny, int nz);
 template <class T>
 int batch_tiled_blocks_per_sm();
 // Batched binary32 recompute-all with TMA-staged planes: work items are the
-// (32 x 8 tile, 64-plane z-chunk) pairs of an instance, numbered 0 ..
+// (32 x 8 tile, zlen-plane z-chunk) pairs of an instance, numbered 0 ..
 // tma_work_items-1 in BatchTile::start; two blocks per SM where they fit
 // (each ring takes 115 KB of shared memory); prepare_ra_tma must have run on
-// the device.
-int tma_work_items(int nx, int ny, int nz);
+// the device.  tma_batch_zchunk picks zlen for instances of the given grid
+// sizes (nx, ny, nz per instance) and a persistent grid of `blocks`.
+int tma_work_items(int nx, int ny, int nz, int zlen);
+int tma_batch_zchunk(const int* dims, int count, int blocks);
 int batch_tma_blocks_per_sm();  // after prepare_ra_tma
 cudaError_t launch_batch_ra_tma(const BatchInst<float>* insts, const BatchTile* tiles, int ntiles, int stage,
-                                int parity, int grid, int* err, cudaStream_t st);
+                                int parity, int grid, int zlen, int* err, cudaStream_t st);
 template <class T>
 cudaError_t launch_batch_ra_tiled(const BatchInst<T>* insts, const BatchTile* tiles, int ntiles, int stage,
                                   int parity, int grid, cudaStream_t st);

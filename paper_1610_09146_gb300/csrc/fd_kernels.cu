@@ -20,6 +20,8 @@
 // stencil taps are read through the read-only data cache.
 #include <cuda.h>
 
+#include <cstdlib>
+
 #include "fd_core.cuh"
 #include "fd_internal.h"
 
@@ -673,7 +675,7 @@ __device__ __forceinline__ void mbar_init_ring(unsigned bar0) {
 }
 
 // One (tile, z-chunk) work item of the TMA-staged kernel: tile origin (x0, y0),
-// planes zbeg .. min(nz, zbeg + kMZChunk) - 1.  `phase` holds the parity of the
+// planes zbeg .. min(nz, zbeg + zlen) - 1.  `phase` holds the parity of the
 // next completion of each ring slot (bit s) and carries over between the work
 // items of a persistent block; every plane issued is waited for exactly once,
 // so it stays the same in every thread.  Returns false when a wait ran out;
@@ -683,10 +685,10 @@ __device__ __forceinline__ bool ra_tma_item(float* sm, unsigned bar0, unsigned& 
                                             const Grid& g, const Coef<float>& k, const Phys& ph, const RKStage& rk,
                                             const df64* __restrict__ Q64, df64* __restrict__ out,
                                             df64* __restrict__ Qs, float* __restrict__ Wnext,
-                                            int* __restrict__ err, int x0, int y0, int zbeg) {
+                                            int* __restrict__ err, int x0, int y0, int zbeg, int zlen) {
     const int tid = threadIdx.x, tx = tid % kMX, ty = tid / kMX;
     const int nx = g.nx, ny = g.ny, nz = g.nz, n = g.n;
-    const int zend = min(nz, zbeg + kMZChunk);
+    const int zend = min(nz, zbeg + zlen);
     const int zlast = zend + 1;  // last plane the item reads
     const unsigned sm0 = smem_u32(sm);
     const PadLayout L = pad_layout(g);
@@ -787,7 +789,7 @@ template <bool RESID>
 __global__ void __launch_bounds__(kMThreads, 2)
     k_ra_tma(const __grid_constant__ CUtensorMap map, Grid g, Coef<float> k, Phys ph, RKStage rk,
              const df64* __restrict__ Q64, df64* __restrict__ out, df64* __restrict__ Qs,
-             float* __restrict__ Wnext, int* __restrict__ err) {
+             float* __restrict__ Wnext, int* __restrict__ err, int zlen) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     if (!tma_ring_aligned(smem_raw, err)) return;
     const unsigned bar0 = smem_u32(smem_raw + kMSlots * kMSlotBytes);
@@ -795,7 +797,7 @@ __global__ void __launch_bounds__(kMThreads, 2)
     __syncthreads();
     unsigned phase = 0;
     ra_tma_item<RESID>(reinterpret_cast<float*>(smem_raw), bar0, phase, &map, g, k, ph, rk, Q64, out, Qs, Wnext,
-                       err, blockIdx.x * kMX, blockIdx.y * kMY, blockIdx.z * kMZChunk);
+                       err, blockIdx.x * kMX, blockIdx.y * kMY, blockIdx.z * zlen, zlen);
 }
 
 // Batched form: a persistent grid walks the (tile, z-chunk) items of the
@@ -818,7 +820,7 @@ struct TmaItem {
 template <bool RESID>
 __global__ void __launch_bounds__(kMThreads, 2)
     k_batch_ra_tma(const BatchInst<float>* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
-                   int stage, int parity, int* __restrict__ err) {
+                   int stage, int parity, int* __restrict__ err, int zlen) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TmaItem& it = *reinterpret_cast<TmaItem*>(smem_raw + kMSlots * kMSlotBytes + 8 * kMSlots);
     if (!tma_ring_aligned(smem_raw, err)) return;
@@ -844,7 +846,7 @@ __global__ void __launch_bounds__(kMThreads, 2)
         const int zc = tl.start / (ntx * nty), r = tl.start % (ntx * nty);
         if (!ra_tma_item<RESID>(reinterpret_cast<float*>(smem_raw), bar0, phase, &insts[tl.inst].fmap[parity],
                                 it.g, it.k, it.ph, it.rk, it.Q64, it.out, it.Qs, it.Wnext, err,
-                                (r % ntx) * kMX, (r / ntx) * kMY, zc * kMZChunk))
+                                (r % ntx) * kMX, (r / ntx) * kMY, zc * zlen, zlen))
             return;
     }
 }
@@ -1628,6 +1630,29 @@ bool tma_staging_ok(const Grid& g) { return g.nx % 4 == 0 && g.nx >= 8 && g.ny >
 
 size_t padded_field_points(const Grid& g) { return (size_t)pad_layout(g).np; }
 
+// Planes per block of the single-instance TMA kernel: the longest chunk (of
+// 64, 32, 16) that still gives at least twelve waves of two blocks per SM,
+// else 8.  Shorter chunks re-read more halo planes (four per chunk) but even
+// out the last wave; measured on GB300 (binary32 step, ms): 128^3 chunk 8 /
+// 16 / 64: 0.326 / 0.351 / 0.437; 256^3 16 / 32 / 64: 2.15 / 2.20 / 2.27;
+// 384^3 16 / 32 / 64: 7.13 / 7.12 / 7.16.  FDGB300_TMA_ZCHUNK overrides it
+// (a tuning knob; any value from 4 to 256).
+int tma_zchunk(const Grid& g) {
+    static const int forced = [] {
+        const char* v = std::getenv("FDGB300_TMA_ZCHUNK");
+        const int z = v ? std::atoi(v) : 0;
+        return z >= 4 && z <= 256 ? z : 0;
+    }();
+    if (forced) return forced;
+    int sms = 152;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long tiles = (long long)((g.nx + kMX - 1) / kMX) * ((g.ny + kMY - 1) / kMY);
+    for (int z : {64, 32, 16})
+        if (tiles * ((g.nz + z - 1) / z) >= 12LL * 2 * sms) return z;
+    return 8;
+}
+
 cudaError_t launch_prims_padded(const Grid& g, const Phys& ph, const df64* Q, float* F, cudaStream_t st) {
     k_prims_padded<<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, Q, F);
     return cudaGetLastError();
@@ -1639,12 +1664,13 @@ size_t batch_tma_smem_bytes() { return tma_smem_bytes() + sizeof(TmaItem); }
 cudaError_t launch_ra_tma(const CUtensorMap& map, const Grid& g, const Coef<float>& k, const Phys& ph,
                           const RKStage& rk, bool resid, const df64* Q64, df64* out, df64* Qs, float* Wnext,
                           int* err, cudaStream_t st) {
-    const dim3 grid((g.nx + kMX - 1) / kMX, (g.ny + kMY - 1) / kMY, (g.nz + kMZChunk - 1) / kMZChunk);
+    const int zlen = tma_zchunk(g);
+    const dim3 grid((g.nx + kMX - 1) / kMX, (g.ny + kMY - 1) / kMY, (g.nz + zlen - 1) / zlen);
     const size_t smem = tma_smem_bytes();
     if (resid) {
-        k_ra_tma<true><<<grid, kMThreads, smem, st>>>(map, g, k, ph, rk, Q64, out, Qs, Wnext, err);
+        k_ra_tma<true><<<grid, kMThreads, smem, st>>>(map, g, k, ph, rk, Q64, out, Qs, Wnext, err, zlen);
     } else {
-        k_ra_tma<false><<<grid, kMThreads, smem, st>>>(map, g, k, ph, rk, Q64, out, Qs, Wnext, err);
+        k_ra_tma<false><<<grid, kMThreads, smem, st>>>(map, g, k, ph, rk, Q64, out, Qs, Wnext, err, zlen);
     }
     return cudaGetLastError();
 }
@@ -1697,14 +1723,24 @@ int batch_tma_blocks_per_sm() {
     return b;
 }
 
-int tma_work_items(int nx, int ny, int nz) {
-    return ((nx + kMX - 1) / kMX) * ((ny + kMY - 1) / kMY) * ((nz + kMZChunk - 1) / kMZChunk);
+int tma_work_items(int nx, int ny, int nz, int zlen) {
+    return ((nx + kMX - 1) / kMX) * ((ny + kMY - 1) / kMY) * ((nz + zlen - 1) / zlen);
+}
+
+int tma_batch_zchunk(const int* dims, int count, int blocks) {
+    for (int z : {64, 32, 16}) {
+        long long items = 0;
+        for (int i = 0; i < count; ++i) items += tma_work_items(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], z);
+        if (items >= 12LL * blocks) return z;
+    }
+    return 8;
 }
 
 cudaError_t launch_batch_ra_tma(const BatchInst<float>* insts, const BatchTile* tiles, int ntiles, int stage,
-                                int parity, int grid, int* err, cudaStream_t st) {
+                                int parity, int grid, int zlen, int* err, cudaStream_t st) {
     if (ntiles == 0) return cudaSuccess;
-    k_batch_ra_tma<false><<<grid, kMThreads, batch_tma_smem_bytes(), st>>>(insts, tiles, ntiles, stage, parity, err);
+    k_batch_ra_tma<false><<<grid, kMThreads, batch_tma_smem_bytes(), st>>>(insts, tiles, ntiles, stage, parity, err,
+                                                                          zlen);
     return cudaGetLastError();
 }
 

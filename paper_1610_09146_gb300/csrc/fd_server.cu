@@ -162,6 +162,7 @@ struct fd_server {
     int* kerr = nullptr;        // set by a kernel whose bounded wait ran out
     bool tma_allowed = true;    // FDGB300_NO_TMA=1 at creation turns TMA staging off
     int tma_blocks = 1;         // resident TMA-staged blocks per SM
+    int tma_zlen = 64;          // planes per TMA work item (set by rebuild)
     // growable buffers for tables and tiles
     void* tab = nullptr;
     size_t tab_bytes = 0;
@@ -231,9 +232,10 @@ fd::BatchInst<T> record(const fd_server* s, const Active& a) {
     return I;
 }
 
-void append_tiles(const Active& a, std::vector<fd::BatchTile>& v, bool tiled = false, bool tma = false) {
+void append_tiles(const Active& a, std::vector<fd::BatchTile>& v, bool tiled = false, int tma_zlen = 0) {
     if (tiled) {  // x-y tile / z-chunk work items of the shared-memory recompute-all kernel
-        const int m = tma ? fd::tma_work_items(a.r.nx, a.r.ny, a.r.nz) : fd::tiled_work_items(a.r.nx, a.r.ny, a.r.nz);
+        const int m = tma_zlen ? fd::tma_work_items(a.r.nx, a.r.ny, a.r.nz, tma_zlen)
+                               : fd::tiled_work_items(a.r.nx, a.r.ny, a.r.nz);
         for (int t = 0; t < m; ++t) v.push_back({a.slot, t, 0});
         return;
     }
@@ -248,6 +250,12 @@ cudaError_t rebuild(fd_server* s) {
     std::vector<fd::BatchInst<float>> I32;
     std::vector<fd::BatchTile> t[2][3], f[2];
     cudaError_t e;
+    {  // work-item length of the TMA-staged solves for this active set
+        std::vector<int> dims;
+        for (auto& a : s->active)
+            if (a.L.padded) dims.insert(dims.end(), {a.r.nx, a.r.ny, a.r.nz});
+        s->tma_zlen = fd::tma_batch_zchunk(dims.data(), (int)dims.size() / 3, s->sms * s->tma_blocks);
+    }
     for (auto& a : s->active) {
         const int d = a.r.dtype == FD_F64 ? 0 : 1;
         if (d == 0) {
@@ -262,7 +270,7 @@ cudaError_t rebuild(fd_server* s) {
                         return e;
         }
         const bool ss = a.r.algorithm == FD_STORE_SOME;
-        append_tiles(a, t[d][ss ? 0 : (a.L.padded ? 2 : 1)], !ss && d == 1, a.L.padded);
+        append_tiles(a, t[d][ss ? 0 : (a.L.padded ? 2 : 1)], !ss && d == 1, a.L.padded ? s->tma_zlen : 0);
         if (a.fresh) append_tiles(a, f[d]);
     }
     size_t off = 0;
@@ -340,7 +348,8 @@ cudaError_t run_group(fd_server* s, int d) {
         }
         if constexpr (sizeof(T) == sizeof(float)) {
             if (s->ntiles[d][2]) {
-                e = fd::launch_batch_ra_tma(I, s->tiles[d][2], s->ntiles[d][2], st, p, gt, s->kerr, s->stream);
+                e = fd::launch_batch_ra_tma(I, s->tiles[d][2], s->ntiles[d][2], st, p, gt, s->tma_zlen, s->kerr,
+                                            s->stream);
                 if (e != cudaSuccess) return e;
             }
         }
