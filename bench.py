@@ -342,6 +342,18 @@ def run_ours(args):
                                 "dominant_kernel": name, "kernels": {kk: round(vv["ms_avg"], 4) for kk, vv in kern.items()},
                                 "binary64_equivalent_tflops": round(eq, 4),
                                 "vs_fp64_peak": round(eq / FP64_PEAK_TFLOPS, 4), "ke": diag[0]}
+    # binary32-stencil mode (FD_F32_ACCDW) families, beside the binary64 line
+    f32 = {}
+    if args.dtype == "f64" and not args.no_df64:
+        for alg in args.variants:
+            s, ms, kern, finite, diag = time_family(fd, torch, alg, "f32", n, args.steps, args.warmup, stream,
+                                                    barrier, clocks)
+            s.close()
+            value, ms = aggregate_over_ranks(ms, npts, args.steps, dist, "cuda")
+            f32[SHORT[alg]] = {"value": value, "ms_per_step": ms / args.steps, "finite": finite,
+                               "kernels": {kk: round(vv["ms_avg"], 4) for kk, vv in kern.items()},
+                               "roofline": roofline_of("f32", alg, kern, npts, hbm_peak, hbm_src),
+                               "ke_rel_vs_binary64": abs(diag[0] - results[alg]["ke"]) / results[alg]["ke"]}
     cl = clocks.stop()
     e2e = e2e_run(fd, torch, keep, n, max(3, min(args.steps, 10)), stream.cuda_stream)
     e2e["value"], _ = aggregate_over_ranks(1e3 * npts * e2e["steps"] / e2e["value"], npts, e2e["steps"], dist,
@@ -364,6 +376,9 @@ def run_ours(args):
             "kernels": {kk: round(vv["ms_avg"], 4) for kk, vv in results[a]["kernels"].items()}}
             for a in results},
         "variants_df64": df64,
+        "variants_f32": f32,
+        "variants_f32_note": "dtype f32: binary32 stencils on perturbation fields, compensated (double-word) state "
+                             "and RK update; roofline against the measured HBM copy rate",
         "variants_df64_note": "dtype df64: double-word arithmetic on the binary32 pipe, parity 1e-12 vs the "
                               "binary64 oracle; binary64_equivalent_tflops counts the binary64 algorithm's flops",
     }
@@ -779,7 +794,7 @@ def main():
     ap.add_argument("--dtype", choices=["f64", "f32", "df64"], default="f64")
     ap.add_argument("--variants", nargs="+", default=VARIANTS, choices=VARIANTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-df64", action="store_true", help="skip the double-word (df64) families")
+    ap.add_argument("--no-df64", action="store_true", help="skip the df64 and binary32 families beside the line")
     ap.add_argument("--workload", choices=["single", "batched", "serve", "mixed512", "history", "sweep"],
                     default="single",
                     help="single: the 256^3 line (default); batched / serve / mixed512: the ensemble, "
