@@ -348,6 +348,19 @@ const char* fd_server_last_error(const fd_server* s);
 int fd_residual_noalloc(const double* Q, double* R, int nx, int ny, int nz, double Re, double Mach,
                         double Pr, double gamma, void* cuda_stream);
 
+/* ---- failure-detection test hook ------------------------------------------
+ * Every wait inside a kernel of this library is bounded.  This call makes one
+ * run out on purpose, so that tests can check what a caller then sees, without
+ * a fault or a hang: it creates a 32 x 8 x 8 binary32 recompute-all solver on
+ * the current device (default stream), and launches one stage of the
+ * TMA-staged kernel with the copy of one plane left out, so the wait for it
+ * gives up after 0.5 s; the kernel records that in its error word, waits
+ * (bounded) for its other copies and ends.  *err_word receives the word (1
+ * when the wait ran out, as designed); the solver is then destroyed.  The
+ * paper has no counterpart.  Errors: FD_EINVAL (err_word NULL, or TMA staging
+ * turned off by FDGB300_NO_TMA=1), FD_ENOMEM, FD_ECUDA. */
+int fd_selftest_wait_timeout(int* err_word);
+
 /* Free every device buffer of the handle and the handle itself.  NULL is a
  * no-op.  Synchronises the handle's stream first. */
 int fd_destroy(fd_handle* h);

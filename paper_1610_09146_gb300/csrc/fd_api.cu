@@ -598,6 +598,29 @@ int fd_check_finite(fd_handle* h) {
     return FD_OK;
 }
 
+int fd_selftest_wait_timeout(int* err_word) {
+    if (!err_word) return fail_global(FD_EINVAL, "fd_selftest_wait_timeout: err_word is NULL");
+    *err_word = 0;
+    fd_handle* h = nullptr;
+    int rc = fd_create(&h, 32, 8, 8, 1600.0, 0.1, 0.71, 1.4, 1e-3, FD_RECOMPUTE_ALL, FD_F32_ACCDW, nullptr, nullptr);
+    if (rc != FD_OK) return rc;
+    if (!h->use_tma) {
+        fd_destroy(h);
+        return fail_global(FD_EINVAL, "fd_selftest_wait_timeout: TMA staging is turned off");
+    }
+    const fd::df64* Qin = reinterpret_cast<const fd::df64*>(h->Q[h->cur]);
+    fd::df64* Qout = reinterpret_cast<fd::df64*>(h->Q[1 - h->cur]);
+    cudaError_t e = fd::launch_prims_padded(h->grid, h->phys, Qin, h->Wf[h->wcur], h->stream);
+    if (e == cudaSuccess)  // plane 2 of the single z-chunk is never copied
+        e = fd::launch_ra_tma(h->fmap[h->wcur], h->grid, h->kf, h->phys, fd::make_stage(0, h->dt), false, Qin, Qout,
+                              reinterpret_cast<fd::df64*>(h->Qs), h->Wf[1 - h->wcur], h->kerr, h->stream, 2);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(err_word, h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    fd_destroy(h);
+    if (e != cudaSuccess) return fail_global(FD_ECUDA, "fd_selftest_wait_timeout: %s", cudaGetErrorString(e));
+    return FD_OK;
+}
+
 size_t fd_device_bytes(const fd_handle* h) { return h ? h->block_bytes : 0; }
 
 int fd_profile(fd_handle* h, int enable) {

@@ -44,16 +44,18 @@ cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const Phys& ph, const RKS
 // writes it from a state, and the kernel writes the next stage's fields in it.
 // `map` describes one such buffer (box 40 x 12 x 1 x 10, made by
 // encode_field_map); usable when tma_staging_ok(g).  prepare_ra_tma sets the
-// kernels' shared-memory size (host set-up, once per device).  A bounded wait
-// that runs out sets *err to 1 (2: the shared ring was misaligned).
+// kernels' shared-memory size (host set-up, once per device).  A wait that
+// runs out (0.5 s) sets *err to 1 (2: the shared ring was misaligned).
 bool tma_staging_ok(const Grid& g);
 size_t padded_field_points(const Grid& g);
 cudaError_t launch_prims_padded(const Grid& g, const Phys& ph, const df64* Q, float* F, cudaStream_t st);
 cudaError_t encode_field_map(CUtensorMap* map, const float* F, const Grid& g);
 cudaError_t prepare_ra_tma();
+// skip_plane >= 0 is a failure-detection test hook: the copy of that plane is
+// never issued, so the wait for it runs out (0.5 s) and *err is set.
 cudaError_t launch_ra_tma(const CUtensorMap& map, const Grid& g, const Coef<float>& k, const Phys& ph,
                           const RKStage& rk, bool resid, const df64* Q64, df64* out, df64* Qs, float* Wnext,
-                          int* err, cudaStream_t st);
+                          int* err, cudaStream_t st, int skip_plane = -1000000);
 template <class T>
 cudaError_t launch_ra_tiled(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid,
                             const T* Qf, const T* Wf, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext,

@@ -639,8 +639,8 @@ __global__ void __launch_bounds__(kTX* kTY, sizeof(T) == 4 ? 2 : 1)
 // evaluated, plane z+3 is already in flight, so no thread issues a staging
 // load and the copy latency is hidden behind the stencil arithmetic.  The
 // padding holds the periodic images, so boxes at the domain edge need nothing
-// special.  Every wait is bounded: a wait that runs out sets *err, drains the
-// copies in flight (again bounded) and ends the block.
+// special.  Every wait is bounded (0.5 s of wall time): a wait that runs out
+// sets *err, drains the copies in flight (again bounded) and ends the block.
 constexpr int kMX = 32, kMY = 8, kMThreads = kMX * kMY;
 constexpr int kBX = kMX + 8, kBY = kMY + 4, kBPlane = kBX * kBY;
 constexpr int kMSlots = 6, kMZChunk = 64;
@@ -649,14 +649,23 @@ constexpr unsigned kMSlotBytes = kNF * kBPlane * 4;  // 19200, a multiple of 128
 // so that it starts on the 128-byte boundary the TMA destination needs), the
 // six mbarriers, and in the batched kernel the staged instance record: two
 // blocks per SM, 2 x (115200 + 48 + 456 + 1024 reserved) <= 228 KB.
-constexpr long long kMWaitLimit = 1LL << 22;
+constexpr unsigned long long kMWaitNs = 500000000ull;  // a wait gives up after 0.5 s
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the completion of the phase of parity `parity` of an mbarrier,
+// polling for at most kMWaitNs of wall time.
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-    for (long long it = 0; it < kMWaitLimit; ++it) {
+    const unsigned long long t0 = global_ns();
+    for (;;) {
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -664,8 +673,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
+        if (global_ns() - t0 > kMWaitNs) return false;
     }
-    return false;
 }
 
 __device__ __forceinline__ void mbar_init_ring(unsigned bar0) {
@@ -685,7 +694,8 @@ __device__ __forceinline__ bool ra_tma_item(float* sm, unsigned bar0, unsigned& 
                                             const Grid& g, const Coef<float>& k, const Phys& ph, const RKStage& rk,
                                             const df64* __restrict__ Q64, df64* __restrict__ out,
                                             df64* __restrict__ Qs, float* __restrict__ Wnext,
-                                            int* __restrict__ err, int x0, int y0, int zbeg, int zlen) {
+                                            int* __restrict__ err, int x0, int y0, int zbeg, int zlen,
+                                            int skip_plane = -1000000) {
     const int tid = threadIdx.x, tx = tid % kMX, ty = tid / kMX;
     const int nx = g.nx, ny = g.ny, nz = g.nz, n = g.n;
     const int zend = min(nz, zbeg + zlen);
@@ -694,6 +704,7 @@ __device__ __forceinline__ bool ra_tma_item(float* sm, unsigned bar0, unsigned& 
     const PadLayout L = pad_layout(g);
     auto slot_of = [&](int p) { return (p - zbeg + 2) % kMSlots; };
     auto issue = [&](int p) {  // one thread; padded coordinates of (x0 - 4, y0 - 2) are (x0, y0)
+        if (p == skip_plane) return;  // failure-detection test: this plane never arrives
         const int s = slot_of(p);
         const unsigned bar = bar0 + 8 * s, dst = sm0 + s * kMSlotBytes;
         const int zz = ((p % nz) + nz) % nz;
@@ -789,7 +800,7 @@ template <bool RESID>
 __global__ void __launch_bounds__(kMThreads, 2)
     k_ra_tma(const __grid_constant__ CUtensorMap map, Grid g, Coef<float> k, Phys ph, RKStage rk,
              const df64* __restrict__ Q64, df64* __restrict__ out, df64* __restrict__ Qs,
-             float* __restrict__ Wnext, int* __restrict__ err, int zlen) {
+             float* __restrict__ Wnext, int* __restrict__ err, int zlen, int skip_plane) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     if (!tma_ring_aligned(smem_raw, err)) return;
     const unsigned bar0 = smem_u32(smem_raw + kMSlots * kMSlotBytes);
@@ -797,7 +808,7 @@ __global__ void __launch_bounds__(kMThreads, 2)
     __syncthreads();
     unsigned phase = 0;
     ra_tma_item<RESID>(reinterpret_cast<float*>(smem_raw), bar0, phase, &map, g, k, ph, rk, Q64, out, Qs, Wnext,
-                       err, blockIdx.x * kMX, blockIdx.y * kMY, blockIdx.z * zlen, zlen);
+                       err, blockIdx.x * kMX, blockIdx.y * kMY, blockIdx.z * zlen, zlen, skip_plane);
 }
 
 // Batched form: a persistent grid walks the (tile, z-chunk) items of the
@@ -1663,14 +1674,14 @@ size_t batch_tma_smem_bytes() { return tma_smem_bytes() + sizeof(TmaItem); }
 
 cudaError_t launch_ra_tma(const CUtensorMap& map, const Grid& g, const Coef<float>& k, const Phys& ph,
                           const RKStage& rk, bool resid, const df64* Q64, df64* out, df64* Qs, float* Wnext,
-                          int* err, cudaStream_t st) {
+                          int* err, cudaStream_t st, int skip_plane) {
     const int zlen = tma_zchunk(g);
     const dim3 grid((g.nx + kMX - 1) / kMX, (g.ny + kMY - 1) / kMY, (g.nz + zlen - 1) / zlen);
     const size_t smem = tma_smem_bytes();
     if (resid) {
-        k_ra_tma<true><<<grid, kMThreads, smem, st>>>(map, g, k, ph, rk, Q64, out, Qs, Wnext, err, zlen);
+        k_ra_tma<true><<<grid, kMThreads, smem, st>>>(map, g, k, ph, rk, Q64, out, Qs, Wnext, err, zlen, skip_plane);
     } else {
-        k_ra_tma<false><<<grid, kMThreads, smem, st>>>(map, g, k, ph, rk, Q64, out, Qs, Wnext, err, zlen);
+        k_ra_tma<false><<<grid, kMThreads, smem, st>>>(map, g, k, ph, rk, Q64, out, Qs, Wnext, err, zlen, skip_plane);
     }
     return cudaGetLastError();
 }

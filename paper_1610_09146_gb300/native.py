@@ -108,6 +108,7 @@ _SIGS = {
     "fd_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "fd_residual_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp]),
+    "fd_selftest_wait_timeout": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
     "fd_destroy": (ctypes.c_int, [_vp]),
     "fd_last_error": (ctypes.c_char_p, [_vp]),
     "fd_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(FdInstanceDesc), ctypes.c_int,
@@ -241,6 +242,14 @@ def fd_residual_noalloc(Q, R, nx, ny, nz, Re, Mach, Pr, gamma, stream=0):
     """Q, R: device addresses (ints) of caller-owned float64 arrays.  Returns the status
     code as is (no message is set by this entry point)."""
     return load().fd_residual_noalloc(Q, R, nx, ny, nz, Re, Mach, Pr, gamma, _vp(stream or None))
+
+
+def fd_selftest_wait_timeout():
+    """Make one bounded wait inside a kernel run out (see the header); returns the
+    kernel's error word (1 when the wait gave up, as designed)."""
+    w = ctypes.c_int(0)
+    _check(load().fd_selftest_wait_timeout(ctypes.byref(w)), None)
+    return w.value
 
 
 def fd_destroy(h):

@@ -98,3 +98,23 @@ def test_malformed_requests_are_rejected_before_any_launch():
         with pytest.raises(fd.FdError):
             fd.fd_set_state(s.h, np.zeros(3))
         assert np.array_equal(s.state(), Q)
+
+
+def test_kernel_wait_that_runs_out_is_reported_and_the_context_survives():
+    """A wait inside the TMA-staged kernel that never completes (the copy of one
+    plane is left out on purpose) gives up after 0.5 s, records it in the
+    kernel's error word and ends the block; nothing faults or hangs, and the
+    device stays usable for the next solver."""
+    import os
+    import time
+    if os.environ.get("FDGB300_NO_TMA") == "1":
+        pytest.skip("TMA staging turned off")
+    t0 = time.perf_counter()
+    word = native.fd_selftest_wait_timeout()
+    elapsed = time.perf_counter() - t0
+    assert word == 1
+    assert elapsed < 30.0
+    with fd.Solver(32, algorithm="recompute_all", dtype="f32") as s:
+        s.step(2)
+        assert s.check_finite()
+        assert np.isfinite(s.diagnostics()[0])
