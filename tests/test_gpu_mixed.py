@@ -86,3 +86,46 @@ def test_mixed_variants_agree():
     for alg in VARIANTS[1:]:
         assert rel_l2(out[alg], out["store_all"]) <= 1e-7, alg
 
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("alg", ["recompute_all", "store_some"])
+def test_full_size_512_one_step_sampled(alg):
+    """The 512^3 Taylor-Green configuration of the binary32 mode, in the launch
+    configuration bench.py times: the one-step increment Q1 - Q0 at sampled
+    points (random, plus points next to every face of the periodic box) against
+    the oracle's, computed on a block around each point.
+
+    Bound, from the arithmetic: a first difference of binary32 tap values of
+    magnitude F errs by at most 18 F 2^-24 (taps rounded to 2^-24 relative,
+    weights 8, 8, 1, 1), times 1/(12h) once scaled; the residual of variable v
+    adds such derivatives with weights W_v (|u| <= 1 sets the scale of the
+    divergence terms; in the perturbation form the energy residual carries
+    (rhoE0 + p0) div, so W_E is 3 (rhoE0 + p0) plus the O(1) terms), and one
+    step multiplies by dt.  The test allows that bound plus 2e-5 of the largest
+    increment (the binary32 residual bound of the small-grid test above)."""
+    from tests.sampled import oracle_one_step_at
+    n = 512
+    dt = fd.dt_for_grid(n)
+    Q0 = O.tgv_ic(n, n, n, 1.4, 0.1)
+    rng = np.random.default_rng(512)
+    pts = [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(16)]
+    pts += [(0, 0, 0), (n - 1, n - 1, n - 1), (1, n - 2, 0), (n - 2, 0, 1), (255, 256, 511)]
+    h = (2 * np.pi / n,) * 3
+    ref = oracle_one_step_at(Q0, pts, dt, h)
+    with fd.Solver(n, dt=dt, algorithm=alg, dtype="f32") as s:
+        s.step(1)
+        Q = s.state()
+    got = np.array([Q[:, z, y, x] for (z, y, x) in pts])
+    base = np.array([Q0[:, z, y, x] for (z, y, x) in pts])
+    dref, dgot = ref - base, got - base
+    gamma, mach = 1.4, 0.1
+    p0 = 1.0 / (gamma * mach**2)
+    rhoE0 = p0 / (gamma - 1.0)
+    W = [4.0, 6.0, 6.0, 6.0, 3.0 * (rhoE0 + p0) + 10.0]
+    per_derivative = 18.0 * 2.0**-24 / (12.0 * h[0])
+    for v in range(5):
+        err = np.abs(dgot[:, v] - dref[:, v]).max()
+        tol = 2e-5 * np.abs(dref[:, v]).max() + dt * per_derivative * W[v]
+        print(f"{alg} v{v}: err {err:.3e} tol {tol:.3e} max increment {np.abs(dref[:, v]).max():.3e}")
+        assert err <= tol, v

@@ -14,6 +14,7 @@ import pytest
 
 import oracle as O
 from tests.inputs import rough_state, smooth_state
+from tests.sampled import oracle_one_step_at
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -150,28 +151,6 @@ def test_initial_kinetic_energy_closed_form_on_gpu():
 
 
 # ------------------------------------------------- full size, sampled points
-
-
-def _block(Q, z, y, x, r):
-    nz, ny, nx = Q.shape[1:]
-    iz = (np.arange(z - r, z + r + 1)) % nz
-    iy = (np.arange(y - r, y + r + 1)) % ny
-    ix = (np.arange(x - r, x + r + 1)) % nx
-    return np.ascontiguousarray(Q[:, iz][:, :, iy][:, :, :, ix])
-
-
-def oracle_one_step_at(Q0, pts, dt, h):
-    """The oracle's one-step result at sample points, each computed on a periodic
-    17^3 block cut around the point with the parent grid spacing.  The scheme's
-    dependency radius is 2 points per stage (6 per step), so the centre of the
-    block is unaffected by the block's own wrap-around."""
-    r = 8
-    out = []
-    for (z, y, x) in pts:
-        B = _block(Q0, z, y, x, r)
-        B1 = O.run(B, 1, dt=dt, h=h)
-        out.append(B1[:, r, r, r])
-    return np.array(out)
 
 
 @pytest.mark.slow
