@@ -141,6 +141,19 @@ int fd_get_state(fd_handle* h, double* dst, size_t n_elems, int dst_is_device);
  * fd_get_state); checkpoint / resume at a step boundary.  Synchronises. */
 int fd_set_state(fd_handle* h, const double* src, size_t n_elems, int src_is_device);
 
+/* Stream-ordered forms of fd_get_state / fd_set_state: the copy (and, in the
+ * binary32 and df64 modes, the conversion to or from the double-word state) is
+ * enqueued on the handle's stream after the work already there, and the call
+ * returns without waiting.  The caller keeps the host buffer alive and
+ * unchanged (set) or unread (get) until the stream has reached the copy, for
+ * example by synchronising the stream or an event recorded after the call;
+ * only page-locked host memory gives a copy that overlaps other work.  With
+ * two handles on two streams, the copies of one solve overlap the steps of
+ * the other.  A kernel error word is not checked here (the synchronising
+ * calls check it).  Errors: FD_EINVAL, FD_ECUDA (enqueue failure). */
+int fd_get_state_async(fd_handle* h, double* dst, size_t n_elems, int dst_is_device);
+int fd_set_state_async(fd_handle* h, const double* src, size_t n_elems, int src_is_device);
+
 /* Kinetic energy and enstrophy of the current state (Section 3, Fig. 3):
  *   ke  = (1/N) sum rho |u|^2 / 2,
  *   ens = (1/N) sum rho |omega|^2 / 2, omega = curl u with the 4th-order

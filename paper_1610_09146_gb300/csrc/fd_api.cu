@@ -490,7 +490,7 @@ int fd_step(fd_handle* h, int n) {
     return FD_OK;
 }
 
-int fd_get_state(fd_handle* h, double* dst, size_t n_elems, int dst_is_device) {
+int fd_get_state_async(fd_handle* h, double* dst, size_t n_elems, int dst_is_device) {
     if (!h) return fail_global(FD_EINVAL, "fd_get_state: NULL handle");
     if (!dst) return h->fail(FD_EINVAL, "fd_get_state: dst is NULL");
     if (n_elems != 5 * (size_t)h->n)
@@ -505,12 +505,19 @@ int fd_get_state(fd_handle* h, double* dst, size_t n_elems, int dst_is_device) {
     if (e == cudaSuccess && src != dst)
         e = cudaMemcpyAsync(dst, src, n_elems * sizeof(double),
                             dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "fd_get_state");
+    return FD_OK;
+}
+
+int fd_get_state(fd_handle* h, double* dst, size_t n_elems, int dst_is_device) {
+    int rc = fd_get_state_async(h, dst, n_elems, dst_is_device);
+    if (rc != FD_OK) return rc;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "fd_get_state");
     return check_kernel_error(h, "fd_get_state");
 }
 
-int fd_set_state(fd_handle* h, const double* src, size_t n_elems, int src_is_device) {
+int fd_set_state_async(fd_handle* h, const double* src, size_t n_elems, int src_is_device) {
     if (!h) return fail_global(FD_EINVAL, "fd_set_state: NULL handle");
     if (!src) return h->fail(FD_EINVAL, "fd_set_state: src is NULL");
     if (n_elems != 5 * (size_t)h->n)
@@ -521,7 +528,14 @@ int fd_set_state(fd_handle* h, const double* src, size_t n_elems, int src_is_dev
                                     src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess && dw_state(h->dtype))
         e = fd::launch_to_df64(h->Qs, reinterpret_cast<fd::df64*>(h->Q[h->cur]), h->n, state_shift(h), h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "fd_set_state");
+    return FD_OK;
+}
+
+int fd_set_state(fd_handle* h, const double* src, size_t n_elems, int src_is_device) {
+    int rc = fd_set_state_async(h, src, n_elems, src_is_device);
+    if (rc != FD_OK) return rc;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "fd_set_state");
     return FD_OK;
 }

@@ -100,6 +100,8 @@ _SIGS = {
     "fd_step": (ctypes.c_int, [_vp, ctypes.c_int]),
     "fd_get_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int]),
     "fd_set_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int]),
+    "fd_get_state_async": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int]),
+    "fd_set_state_async": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int]),
     "fd_diagnostics": (ctypes.c_int, [_vp, _dp, _dp]),
     "fd_residual": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int]),
     "fd_check_finite": (ctypes.c_int, [_vp]),
@@ -203,6 +205,16 @@ def fd_set_state(h, src, n_elems=None, src_is_device=None):
     if isinstance(src, np.ndarray):
         return _check(load().fd_set_state(h, _hostptr(src), src.size, 0), h)
     return _check(load().fd_set_state(h, src, n_elems, 1 if src_is_device is None else src_is_device), h)
+
+
+def fd_get_state_async(h, dst, n_elems, dst_is_device):
+    """Stream-ordered copy of the state to the address dst (int); returns without waiting."""
+    return _check(load().fd_get_state_async(h, dst, n_elems, dst_is_device), h)
+
+
+def fd_set_state_async(h, src, n_elems, src_is_device):
+    """Stream-ordered replacement of the state from the address src (int)."""
+    return _check(load().fd_set_state_async(h, src, n_elems, src_is_device), h)
 
 
 def fd_diagnostics(h):

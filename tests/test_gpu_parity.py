@@ -255,3 +255,35 @@ def test_bad_sizes_are_rejected():
         assert e.value.code == fd.FD_EINVAL
         with pytest.raises(fd.FdError):
             fd.fd_step(s.h, -1)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "df64"])
+def test_async_state_copies_match_the_synchronising_calls(dtype):
+    """fd_set_state_async / fd_get_state_async through pinned host buffers, with
+    two solvers on two streams taking steps in turn, give the same bits as the
+    synchronising calls on one solver."""
+    from paper_1610_09146_gb300 import native
+    shape = (20, 24, 28)
+    Q0 = smooth_state(shape, seed=51)
+    nel = Q0.size
+    with solver(shape, "store_some", dtype=dtype) as s:
+        s.set_state(Q0)
+        s.step(1)
+        want = s.state()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    hin = torch.from_numpy(Q0.reshape(-1).copy()).pin_memory()
+    outs = [torch.empty(nel, dtype=torch.float64, pin_memory=True) for _ in streams]
+    sols = [fd.Solver(shape[::-1], Re=RE, Mach=MACH, Pr=PR, gamma=GAMMA, dt=1e-3, algorithm="store_some",
+                      dtype=dtype, stream=st) for st in streams]
+    try:
+        for k in range(4):
+            sv, o = sols[k % 2], outs[k % 2]
+            native.fd_set_state_async(sv.h, hin.data_ptr(), nel, 0)
+            native.fd_step(sv.h, 1)
+            native.fd_get_state_async(sv.h, o.data_ptr(), nel, 0)
+        torch.cuda.synchronize()
+        for o in outs:
+            assert np.array_equal(o.numpy().reshape(Q0.shape), want)
+    finally:
+        for sv in sols:
+            sv.close()
