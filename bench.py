@@ -242,10 +242,11 @@ def roofline_of(dtype, alg, kern, n, hbm_peak, hbm_src):
     return entry
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of a 256^3 launch, from one ncu
-# capture of the current kernel on a 160^3 grid (two launches, 287 B per point) scaled by
-# the point count; None where no capture of the current kernel version exists.
-TRAFFIC = {("f64", "store_some", "fused"): 4.82e9}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch at 256^3, from ncu captures of the
+# current kernels: binary64 SS fused on a 160^3 grid (two launches, 287 B per point) scaled by
+# the point count; binary32 RA (TMA-staged) at 256^3 itself (mean of the three stages'
+# launches: 3.44, 3.43, 2.76 GB).  None where no capture of the current kernel exists.
+TRAFFIC = {("f64", "store_some", "fused"): 4.82e9, ("f32", "recompute_all", "fused"): 3.21e9}
 
 
 def e2e_run(fd, torch, alg, dtype, n, steps):
