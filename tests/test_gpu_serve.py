@@ -95,3 +95,34 @@ def test_too_large_request_is_refused_and_cancel_works():
         assert res[2]["status"] == fd.FD_EBUSY and res[2]["steps"] == 1
         with pytest.raises(fd.FdError):
             srv.cancel(99)
+
+
+def test_tma_and_thread_staged_binary32_solves_share_a_tick():
+    """Binary32 recompute-all solves whose x extent is a multiple of 4 are staged by
+    TMA (ghost-padded fields), the others by threads; both kinds advance in the same
+    ticks, join and leave at different times, and each equals its solve alone."""
+    reqs = [
+        dict(tag=21, n=(18, 20, 22), steps=6, Re=1600.0, Mach=0.1, dtype="f32", algorithm="recompute_all", dt=1e-3),
+        dict(tag=22, n=(32, 24, 40), steps=4, Re=900.0, Mach=0.2, dtype="f32", algorithm="recompute_all", dt=1e-3),
+        dict(tag=23, n=(21, 16, 16), steps=3, Re=2500.0, Mach=0.3, dtype="f32", algorithm="recompute_all", dt=2e-3),
+        dict(tag=24, n=(64, 8, 72), steps=5, Re=1200.0, Mach=0.15, dtype="f32", algorithm="recompute_all", dt=1e-3),
+    ]
+    got = {}
+    with fd.Server(1 << 30, max_active=8) as srv:
+        srv.submit(reqs[0])
+        srv.submit(reqs[1])
+        srv.tick()
+        srv.submit(reqs[2])
+        srv.tick()
+        srv.submit(reqs[3])
+        for _ in range(40):
+            srv.tick()
+            for r in srv.poll():
+                got[r["tag"]] = r
+            if len(got) == len(reqs):
+                break
+    assert set(got) == {r["tag"] for r in reqs}
+    for r in reqs:
+        ke, en = alone(r)
+        assert got[r["tag"]]["status"] == fd.FD_OK
+        assert got[r["tag"]]["ke"] == ke and got[r["tag"]]["enstrophy"] == en, r["tag"]
