@@ -143,7 +143,22 @@ struct Active {
     bool fresh = true;  // initial state written this tick, primitives pending
     bool cancelled = false;
     int slot = -1;      // index in its dtype's instance table
+    int k = 1;          // steps per tick (odd; see plan_steps)
 };
+
+// Time slicing.  A tick advances every active solve by an odd number of steps
+// k: the dearest step of the active set gets one, and a cheaper solve gets as
+// many as fit in that step's time (at most kMaxSteps, never past its request),
+// so a small solve is not held to the pace of the largest one.  Odd counts
+// flip every solve's ping-pong parity once per tick, so all solves keep one
+// parity; round r of a tick advances the solves with k > r, which are a prefix
+// of tile lists ordered by k.  Step costs are estimated from the measured
+// rates of the two precisions (binary64 ~6e8, binary32 ~6e9 point-steps/s).
+constexpr int kMaxSteps = 31;
+
+double step_cost(const fd_request& r) {
+    return (double)r.nx * r.ny * r.nz * (r.dtype == FD_F64 ? 1.7e-9 : 1.6e-10);
+}
 
 }  // namespace
 
@@ -174,9 +189,11 @@ struct fd_server {
     long long submitted = 0, completed = 0, ticks = 0;
     // current device views (valid after a rebuild)
     void* inst[2] = {nullptr, nullptr};  // [0] double table, [1] float table
-    // [dtype][family: 0 SS, 1 RA, 2 RA staged by TMA (binary32, padded layout)]
+    // [dtype][family: 0 SS, 1 RA, 2 RA staged by TMA (binary32, padded layout)], ordered by k
     fd::BatchTile* tiles[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
-    int ntiles[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    // ntiles[d][f][r]: tiles of the solves with k > r (a prefix of tiles[d][f])
+    int ntiles[2][3][kMaxSteps] = {};
+    int rounds = 1;  // max k over the active set
     fd::BatchTile* fresh_tiles[2] = {nullptr, nullptr};
     int nfresh[2] = {0, 0};
     std::string err;
@@ -256,7 +273,14 @@ cudaError_t rebuild(fd_server* s) {
             if (a.L.padded) dims.insert(dims.end(), {a.r.nx, a.r.ny, a.r.nz});
         s->tma_zlen = fd::tma_batch_zchunk(dims.data(), (int)dims.size() / 3, s->sms * s->tma_blocks);
     }
-    for (auto& a : s->active) {
+    // tiles in order of decreasing k, so that the solves a round advances are a prefix
+    std::vector<Active*> order;
+    for (auto& a : s->active) order.push_back(&a);
+    std::stable_sort(order.begin(), order.end(), [](const Active* x, const Active* y) { return x->k > y->k; });
+    int count[2][3][kMaxSteps] = {};
+    s->rounds = 1;
+    for (Active* ap : order) {
+        Active& a = *ap;
         const int d = a.r.dtype == FD_F64 ? 0 : 1;
         if (d == 0) {
             a.slot = (int)I64.size();
@@ -270,7 +294,10 @@ cudaError_t rebuild(fd_server* s) {
                         return e;
         }
         const bool ss = a.r.algorithm == FD_STORE_SOME;
-        append_tiles(a, t[d][ss ? 0 : (a.L.padded ? 2 : 1)], !ss && d == 1, a.L.padded ? s->tma_zlen : 0);
+        const int fam = ss ? 0 : (a.L.padded ? 2 : 1);
+        append_tiles(a, t[d][fam], !ss && d == 1, a.L.padded ? s->tma_zlen : 0);
+        for (int r = 0; r < a.k; ++r) count[d][fam][r] = (int)t[d][fam].size();
+        s->rounds = std::max(s->rounds, a.k);
         if (a.fresh) append_tiles(a, f[d]);
     }
     size_t off = 0;
@@ -307,7 +334,7 @@ cudaError_t rebuild(fd_server* s) {
         for (int k = 0; k < 3; ++k) {
             if ((e = up(ot[d][k], t[d][k].data(), t[d][k].size() * sizeof(fd::BatchTile))) != cudaSuccess) return e;
             s->tiles[d][k] = reinterpret_cast<fd::BatchTile*>(b + ot[d][k]);
-            s->ntiles[d][k] = (int)t[d][k].size();
+            for (int r = 0; r < kMaxSteps; ++r) s->ntiles[d][k][r] = count[d][k][r];
         }
         if ((e = up(of[d], f[d].data(), f[d].size() * sizeof(fd::BatchTile))) != cudaSuccess) return e;
         s->fresh_tiles[d] = reinterpret_cast<fd::BatchTile*>(b + of[d]);
@@ -318,11 +345,12 @@ cudaError_t rebuild(fd_server* s) {
 }
 
 template <class T>
-cudaError_t run_group(fd_server* s, int d) {
+cudaError_t run_group(fd_server* s, int d, int round) {
     auto* I = static_cast<const fd::BatchInst<T>*>(s->inst[d]);
     cudaError_t e;
     const int gg = s->sms * fd::batch_blocks_per_sm<T>(false, false);
-    if (s->nfresh[d]) {
+    const int* nt[3] = {&s->ntiles[d][0][round], &s->ntiles[d][1][round], &s->ntiles[d][2][round]};
+    if (round == 0 && s->nfresh[d]) {
         if ((e = fd::launch_batch_prims<T>(I, s->fresh_tiles[d], s->nfresh[d], s->parity, gg, s->stream)) !=
             cudaSuccess)
             return e;
@@ -331,25 +359,23 @@ cudaError_t run_group(fd_server* s, int d) {
     const int gs = s->sms * fd::batch_blocks_per_sm<T>(true, true);
     const int gr = s->sms * (tiled ? fd::batch_tiled_blocks_per_sm<T>() : fd::batch_blocks_per_sm<T>(true, false));
     const int gt = s->sms * s->tma_blocks;
-    for (int st = 0, p = s->parity; st < 3; ++st, p ^= 1) {
-        if (s->ntiles[d][0]) {
-            if ((e = fd::launch_batch_grad<T>(I, s->tiles[d][0], s->ntiles[d][0], p, gg, s->stream)) != cudaSuccess)
-                return e;
-            if ((e = fd::launch_batch_fused<T>(I, s->tiles[d][0], s->ntiles[d][0], true, st, p, gs, s->stream)) !=
-                cudaSuccess)
+    // round r starts at parity parity ^ (r & 1): every solve it advances has taken r steps this tick
+    for (int st = 0, p = s->parity ^ (round & 1); st < 3; ++st, p ^= 1) {
+        if (*nt[0]) {
+            if ((e = fd::launch_batch_grad<T>(I, s->tiles[d][0], *nt[0], p, gg, s->stream)) != cudaSuccess) return e;
+            if ((e = fd::launch_batch_fused<T>(I, s->tiles[d][0], *nt[0], true, st, p, gs, s->stream)) != cudaSuccess)
                 return e;
         }
-        if (s->ntiles[d][1]) {
+        if (*nt[1]) {
             if constexpr (sizeof(T) == sizeof(float))
-                e = fd::launch_batch_ra_tiled<T>(I, s->tiles[d][1], s->ntiles[d][1], st, p, gr, s->stream);
+                e = fd::launch_batch_ra_tiled<T>(I, s->tiles[d][1], *nt[1], st, p, gr, s->stream);
             else
-                e = fd::launch_batch_fused<T>(I, s->tiles[d][1], s->ntiles[d][1], false, st, p, gr, s->stream);
+                e = fd::launch_batch_fused<T>(I, s->tiles[d][1], *nt[1], false, st, p, gr, s->stream);
             if (e != cudaSuccess) return e;
         }
         if constexpr (sizeof(T) == sizeof(float)) {
-            if (s->ntiles[d][2]) {
-                e = fd::launch_batch_ra_tma(I, s->tiles[d][2], s->ntiles[d][2], st, p, gt, s->tma_zlen, s->kerr,
-                                            s->stream);
+            if (*nt[2]) {
+                e = fd::launch_batch_ra_tma(I, s->tiles[d][2], *nt[2], st, p, gt, s->tma_zlen, s->kerr, s->stream);
                 if (e != cudaSuccess) return e;
             }
         }
@@ -507,20 +533,34 @@ int fd_server_tick(fd_server* s, int* active_out) {
     }
     if (active_out) *active_out = (int)s->active.size();
     if (s->active.empty()) return FD_OK;
-    // 3. tables, then one RK3 step of every active solve
+    // 3. steps per solve, tables, then k RK3 steps of every active solve
+    double dearest = 0;
+    for (auto& a : s->active) dearest = std::max(dearest, step_cost(a.r));
     bool any_fresh = false;
-    for (auto& a : s->active) any_fresh |= a.fresh;
+    for (auto& a : s->active) {
+        any_fresh |= a.fresh;
+        const int left = a.r.steps - a.done;
+        int k = (int)std::min<double>({(double)kMaxSteps, (double)left, std::floor(dearest / step_cost(a.r))});
+        k = std::max(1, k);
+        if (k % 2 == 0) --k;
+        if (k != a.k) {
+            a.k = k;
+            s->dirty = true;
+        }
+    }
     if (s->dirty || any_fresh) {
         if ((e = rebuild(s)) != cudaSuccess) return s->cuda_fail(e, "fd_server_tick: tables");
         s->dirty = false;
     }
-    if ((e = run_group<double>(s, 0)) != cudaSuccess) return s->cuda_fail(e, "fd_server_tick: binary64 group");
-    if ((e = run_group<float>(s, 1)) != cudaSuccess) return s->cuda_fail(e, "fd_server_tick: binary32 group");
+    for (int r = 0; r < s->rounds; ++r) {
+        if ((e = run_group<double>(s, 0, r)) != cudaSuccess) return s->cuda_fail(e, "fd_server_tick: binary64 group");
+        if ((e = run_group<float>(s, 1, r)) != cudaSuccess) return s->cuda_fail(e, "fd_server_tick: binary32 group");
+    }
     s->parity ^= 1;
     s->nfresh[0] = s->nfresh[1] = 0;
     for (auto& a : s->active) {
         a.fresh = false;
-        a.done++;
+        a.done += a.k;
     }
     // 4. diagnostics of finished solves (scratch: the working fields the next
     //    stage would overwrite), then synchronise and retire them
@@ -547,7 +587,7 @@ int fd_server_tick(fd_server* s, int* active_out) {
         e = cudaMemcpyAsync(res.data(), s->results, res.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "fd_server_tick");
-    if (s->ntiles[1][2]) {
+    if (s->ntiles[1][2][0]) {
         int v = 0;
         e = cudaMemcpyAsync(&v, s->kerr, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
