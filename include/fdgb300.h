@@ -265,11 +265,15 @@ const char* fd_batch_last_error(const fd_batch* b);
  * above: requests queue in submission order; each fd_server_tick admits the
  * queued requests whose device footprint fits the free arena space (first
  * fit, later requests may pass one that does not fit yet) up to max_active
- * solves, advances every active solve by one RK3 step (all of them in the
- * same launches, grouped by dtype and family), and retires the solves that
- * reached their step count: their kinetic energy and enstrophy become results
- * for fd_server_poll and their memory returns to the arena.  Results are
- * those of the same solve run alone (same per-point arithmetic and
+ * solves, advances every active solve (all of them in the same launches,
+ * grouped by dtype and family), and retires the solves that reached their
+ * step count: their kinetic energy and enstrophy become results for
+ * fd_server_poll and their memory returns to the arena.  Ticks are
+ * time-sliced: a solve advances by an odd number of RK3 steps per tick, one
+ * for the solve with the dearest step of the active set and, for a cheaper
+ * solve, as many as fit in that step's time (at most 31, never past its
+ * request), so small solves do not move at the pace of the largest.  Results
+ * are those of the same solve run alone (same per-point arithmetic and
  * reduction order). */
 typedef struct fd_request {
     int nx, ny, nz;                  /* grid, as for fd_create */
@@ -312,9 +316,10 @@ size_t fd_server_footprint(const fd_request* req);
  * with status FD_EBUSY.  Errors: FD_EINVAL if no such request is pending. */
 int fd_server_cancel(fd_server* s, long long tag);
 
-/* Admit, advance every active solve one RK3 step, retire finished solves.
- * Synchronises the server's stream.  *active_out (may be NULL) receives the
- * number of solves active during this tick.  Errors: FD_ECUDA. */
+/* Admit, advance every active solve by its steps for this tick (time-sliced,
+ * see above), retire finished solves.  Synchronises the server's stream.
+ * *active_out (may be NULL) receives the number of solves active during this
+ * tick.  Errors: FD_ECUDA. */
 int fd_server_tick(fd_server* s, int* active_out);
 
 /* Move up to max finished results into out[]; *n_out receives the count. */
