@@ -111,7 +111,8 @@ typedef struct fd_handle fd_handle;
  * initial condition (Section 3): u = sin x cos y cos z, v = -cos x sin y cos z,
  * w = 0, p = 1/(gamma M^2) + (cos 2x + cos 2y)(cos 2z + 2)/16, rho = gamma M^2 p.
  *   nx, ny, nz  grid points per axis, each >= 5 (the 5-point stencil needs
- *               distinct neighbours) and nx*ny*nz < 2^31;
+ *               distinct neighbours) and nx*ny*nz <= 214748364 (598^3:
+ *               ten fields of one grid are addressed with 32-bit offsets);
  *   Re, Mach, Pr, gamma  flow constants (Eqs. 4-7): Re, Mach, Pr > 0,
  *               gamma > 1; dt > 0 is the time step of every fd_step;
  *   algorithm   FD_STORE_ALL, FD_STORE_SOME, FD_RECOMPUTE_ALL,
@@ -215,7 +216,7 @@ int fd_profile_read(fd_handle* h, int kernel_class, double* total_ms, long long*
  * same family and dtype.  Steps are replayed from CUDA graphs captured on the
  * first fd_batch_step. */
 typedef struct fd_instance_desc {
-    int nx, ny, nz;                     /* grid, each axis >= 5, nx*ny*nz < 2^31 */
+    int nx, ny, nz;                     /* grid, each axis >= 5, nx*ny*nz <= 214748364 */
     double Re, Mach, Pr, gamma, dt;     /* as for fd_create */
     int algorithm;                      /* FD_STORE_SOME or FD_RECOMPUTE_ALL */
     int tile_points;                    /* points per work item, >= 32; 0 = 1024 (binary32

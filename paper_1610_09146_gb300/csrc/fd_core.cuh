@@ -14,9 +14,13 @@ namespace fd {
 // Grid of the periodic cube [0, 2*pi]^3 (Section 3); h_a = 2*pi / n_a.
 // Division is avoided on the device: 1/(12 h) and 1/(12 h^2) are precomputed
 // on the host (Section 2 evaluates such rationals once at start-up).
+// Largest grid: ten fields of one instance must be addressable with 32-bit
+// offsets (10 * n <= 2^31 - 1).
+constexpr long long kMaxPoints = 214748364;
+
 struct Grid {
     int nx, ny, nz;
-    int n;               // nx * ny * nz, < 2^31
+    int n;               // nx * ny * nz, <= kMaxPoints
     double inv12h[3];    // 1 / (12 h_a)
     double inv12h2[3];   // 1 / (12 h_a^2)
     float inv12hf[3];

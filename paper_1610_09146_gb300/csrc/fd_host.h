@@ -96,7 +96,9 @@ Coef<T> make_coef(const Grid& g, const Phys& ph, bool shifted) {
 inline const char* check_instance(int nx, int ny, int nz, double Re, double Mach, double Pr, double gamma,
                                   double dt) {
     if (nx < 5 || ny < 5 || nz < 5) return "every axis needs at least 5 points";
-    if ((long long)nx * ny * nz >= (1LL << 31)) return "nx*ny*nz must be below 2^31";
+    // the kernels address the ten working fields of an instance with 32-bit
+    // offsets (f n + c, f <= 9); the store-all work arrays use 64-bit ones
+    if ((long long)nx * ny * nz > kMaxPoints) return "nx*ny*nz must be at most 214748364 (598^3)";
     if (!(Re > 0) || !(Mach > 0) || !(Pr > 0) || !(dt > 0) || !std::isfinite(Re) || !std::isfinite(Mach) ||
         !std::isfinite(Pr) || !std::isfinite(dt))
         return "Re, Mach, Pr and dt must be positive and finite";

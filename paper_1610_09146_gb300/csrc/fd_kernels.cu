@@ -910,7 +910,7 @@ __global__ void __launch_bounds__(256) k_bl_prod(Grid g, const T* __restrict__ Q
                                                  T* __restrict__ P) {
     int idx = grid_index();
     if (idx >= g.n) return;
-    const int n = g.n;
+    const long long n = g.n;  // work arrays index up to 45 n
     T u[3] = {Wf[idx], Wf[n + idx], Wf[2 * n + idx]};
     T p = Wf[3 * n + idx];
 #pragma unroll
@@ -928,7 +928,7 @@ __global__ void __launch_bounds__(256) k_bl_d1(Grid g, const T* __restrict__ Qf,
                                                const T* __restrict__ P, T* __restrict__ D1) {
     int idx = grid_index();
     if (idx >= g.n) return;
-    const int n = g.n;
+    const long long n = g.n;  // work arrays index up to 45 n
     const Nbr s = make_nbr(g, idx);
     const int c = s.c;
 #pragma unroll
@@ -956,7 +956,7 @@ __global__ void __launch_bounds__(256) k_bl_d2(Grid g, const T* __restrict__ Wf,
                                                T* __restrict__ D2) {
     int idx = grid_index();
     if (idx >= g.n) return;
-    const int n = g.n;
+    const long long n = g.n;  // work arrays index up to 45 n
     const Nbr s = make_nbr(g, idx);
     const int c = s.c;
 #pragma unroll
@@ -989,7 +989,7 @@ __global__ void __launch_bounds__(256) k_bl_res(Grid g, Phys ph, RKStage rk, con
                                                 T* __restrict__ Wnext) {
     int idx = grid_index();
     if (idx >= g.n) return;
-    const int n = g.n;
+    const long long n = g.n;  // work arrays index up to 45 n
     const int c = idx;
     Terms<T> t;
     T uc[3], q[5];
@@ -1499,8 +1499,8 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial_f64(Grid g, const
                                                                     double* __restrict__ partial) {
     const int n = g.n;
     double ke = 0.0, en = 0.0;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-        const Nbr s = make_nbr(g, idx);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const Nbr s = make_nbr(g, (int)i);
         const int c = s.c;
         double G[3][3];
 #pragma unroll

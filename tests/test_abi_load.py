@@ -56,6 +56,7 @@ def test_binding_covers_every_declared_symbol():
     ((16, 16, 16, 1600, 0.1, 0.71, 1.4, 1e-3, 7, 0), fd.FD_EINVAL),         # unknown algorithm
     ((16, 16, 16, 1600, 0.1, 0.71, 1.4, 1e-3, 0, 9), fd.FD_EINVAL),         # unknown dtype
     ((2048, 2048, 1024, 1600, 0.1, 0.71, 1.4, 1e-3, 0, 0), fd.FD_EINVAL),   # >= 2^31 points
+    ((600, 600, 600, 1600, 0.1, 0.71, 1.4, 1e-3, 0, 0), fd.FD_EINVAL),      # above 214748364 points
 ])
 def test_create_rejects_bad_arguments(lib, args, code):
     h = ctypes.c_void_p()

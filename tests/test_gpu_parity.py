@@ -287,3 +287,25 @@ def test_async_state_copies_match_the_synchronising_calls(dtype):
     finally:
         for sv in sols:
             sv.close()
+
+
+@pytest.mark.slow
+def test_store_all_beyond_32bit_work_array_offsets():
+    """At 384^3 the store-all work arrays span 45 n > 2^31 values, so their
+    offsets need 64 bits: one BL step against the oracle at sampled points
+    (random, and next to every face of the box), as the 256^3 test does."""
+    n = 384
+    dt = fd.dt_for_grid(n)
+    Q0 = O.tgv_ic(n, n, n, GAMMA, MACH)
+    rng = np.random.default_rng(384)
+    pts = [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(12)]
+    pts += [(0, 0, 0), (n - 1, n - 1, n - 1), (n - 1, 0, 191), (0, n - 2, n - 1)]
+    ref = oracle_one_step_at(Q0, pts, dt, (2 * np.pi / n,) * 3)
+    scale = np.abs(Q0).reshape(5, -1).max(axis=1)
+    scale[3] = np.abs(ref[:, 3]).max()
+    with solver((n, n, n), "store_all", dt=dt) as s:
+        s.step(1)
+        Q = s.state()
+    got = np.array([Q[:, z, y, x] for (z, y, x) in pts])
+    for v in range(5):
+        assert np.abs(got[:, v] - ref[:, v]).max() <= 1e-12 * scale[v], v
