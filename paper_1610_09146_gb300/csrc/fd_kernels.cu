@@ -1,19 +1,29 @@
-// fd_kernels.cu -- kernels of one Runge-Kutta stage for the three algorithm
-// families of Section 2 (BL store-all, SS store-some, RA recompute-all), the
-// Taylor-Green initial condition and the kinetic-energy / enstrophy
-// reduction (Section 3).
+// fd_kernels.cu -- kernels of one Runge-Kutta stage for the five algorithm
+// families of Section 2 (BL store-all, SS store-some, RA recompute-all, RS
+// recompute-some, SN store-none), the Taylor-Green initial condition and the
+// kinetic-energy / enstrophy reduction (Section 3), and the batched forms.
 //
 // Layout: every field is a grid-sized array [z][y][x] (x fastest).  The
 // conserved state Q (rho, rho u, rho v, rho w, rho E) and the saved RK
-// register Qs are always binary64.  The stencils read ten "working" fields:
-//   Qf = five conserved-like fields, Wf = five primitive-like fields.
+// register Qs are binary64, or shifted double-words (rho - 1, rho u_i,
+// rho E - rhoE0) in the binary32 and df64 modes.  The stencils read ten
+// "working" fields:  Qf = five conserved-like fields, Wf = five
+// primitive-like fields.
 //   binary64 mode (T = double): Qf = Q itself, Wf = (u, v, w, p, T).
-//   binary32 mode (T = float) : Qf = (rho-1, rho u, rho v, rho w, rho E - rhoE0),
-//                               Wf = (u, v, w, p - p0, T - 1),
+//   binary32 / df64 (T = float / df64):
+//                       Qf = (rho-1, rho u, rho v, rho w, rho E - rhoE0),
+//                       Wf = (u, v, w, p - p0, T - 1),
 // the shifted (perturbation) fields avoid the loss of digits that the large
-// mean pressure and energy (p0 = 1/(gamma M^2)) would cause in binary32
-// differences.  One thread evaluates one grid point; periodic boundaries
-// (Section 3) are the wrapped neighbour offsets of fd::Nbr.
+// mean pressure and energy (p0 = 1/(gamma M^2)) would cause in the
+// differences.  One thread evaluates one grid point (RS: one thread per point
+// and equation); periodic boundaries (Section 3) are the wrapped neighbour
+// offsets of fd::Nbr, or a ghost-padded field layout for the TMA-staged
+// binary32 recompute-all kernel.
+//
+// Sections: initial condition; primitives and the RK update; the fused
+// residual (RA, SS) and its accessors; RA (global memory, shared-memory
+// tiled, TMA-staged); SS; BL; SN and RS; the batched kernels; diagnostics;
+// launchers.
 //
 // On GB300 binary64 issues at 1/64 of the binary32 rate, so the binary64
 // kernels are bound by FP64 instructions per point, not by memory traffic;
