@@ -205,9 +205,10 @@ class Server:
 class Solver:
     """One Taylor-Green instance on an nx x ny x nz periodic grid.
 
-    algorithm: "store_all" | "store_some" | "recompute_all" (or "BL" | "SS" | "RA")
-    dtype: "f64" | "f32" (binary32 stencils, binary64 state and reductions) | "df64"
-           (double-word arithmetic on the binary32 pipe, binary64-accurate)
+    algorithm: "store_all" | "store_some" | "recompute_all" | "recompute_some" | "store_none"
+               (or "BL" | "SS" | "RA" | "RS" | "SN")
+    dtype: "f64" | "f32" (binary32 stencils, compensated double-word state, binary64
+           reductions) | "df64" (double-word arithmetic on the binary32 pipe, binary64-accurate)
     stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (current torch stream)
     """
 

@@ -9,11 +9,14 @@
 //   W[2]  primitives u, v, w, p, T (stored in every family, Section 2),
 //         ping-pong: the last kernel of a stage writes the primitives of the
 //         new state into W[1-wcur] while the stage reads W[wcur];
-//   work  SS: 9 velocity-gradient arrays; BL: 18 product + 45 first- and 18
-//         second-derivative arrays;
+//   work  SS, RS: 9 velocity-gradient arrays; BL: 18 product + 45 first- and
+//         18 second-derivative arrays;
 //   Wf[2] binary32 mode: the ten perturbation fields, ping-pong likewise
-//         (W[0] then only serves as scratch of the diagnostics);
-//   and the reduction scratch.
+//         (ghost-padded for the TMA-staged recompute-all kernel; W[0] then
+//         only serves as scratch of the diagnostics and the residual);
+//   Wd[2] df64 mode: the ten perturbation fields as double-words;
+//   and the reduction scratch.  In the binary32 and df64 modes Q[2] and Qs
+//   hold shifted double-words, converted to and from binary64 at the API.
 #include <cuda_runtime.h>
 
 #include <cmath>

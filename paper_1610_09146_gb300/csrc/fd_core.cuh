@@ -1,7 +1,7 @@
-// fd_core.cuh -- device building blocks shared by the three algorithm
-// families: grid/physics constants, periodic neighbour offsets, the
-// fourth-order central stencils (Section 2) and the assembly of the residual
-// of Eqs. 1-5 from its derivative terms.
+// fd_core.cuh -- device building blocks shared by the algorithm families:
+// grid/physics constants, periodic neighbour offsets, the fourth-order
+// central stencils (Section 2), the precision modes and the assembly of the
+// residual of Eqs. 1-5 from its derivative terms.
 #pragma once
 
 #include <cuda_runtime.h>

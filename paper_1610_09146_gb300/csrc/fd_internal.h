@@ -26,14 +26,16 @@ cudaError_t launch_prims_df64(const Grid& g, const Phys& ph, const df64* Q, df64
 cudaError_t launch_to_df64(const double* src, df64* dst, long long n, const Shift5& sh, cudaStream_t st);
 cudaError_t launch_from_df64(const df64* src, double* dst, long long n, const Shift5& sh, cudaStream_t st);
 
-// Kernels of one stage in precision T (double or float), one launch each.
-// Qf / Wf are the five conserved-like and five primitive-like working
-// fields, Q64 the binary64 state the stage starts from, out the next state
-// (or R when resid), Qs the saved register, Wnext the working fields of `out`
-// for the next stage (written by the last kernel of a stage unless resid).
-//   RA: launch_ra
+// Kernels of one stage in precision T (double, float or df64), one launch
+// each.  Qf / Wf are the five conserved-like and five primitive-like working
+// fields, Q64 the state the stage starts from (state_t<T>: binary64, or
+// shifted double-words), out the next state (or R when resid), Qs the saved
+// register, Wnext the working fields of `out` for the next stage (written by
+// the last kernel of a stage unless resid).
+//   RA: launch_ra (binary32: launch_ra_tiled / launch_ra_tma)
 //   SS: launch_ss_grad, launch_ss
 //   BL: launch_bl_prod, launch_bl_d1, launch_bl_d2, launch_bl_res
+//   SN: launch_sn;  RS: launch_ss_grad, launch_rs
 template <class T>
 cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid, const T* Qf,
                       const T* Wf, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext, cudaStream_t st);
