@@ -349,10 +349,10 @@ const char* fd_server_last_error(const fd_server* s);
  * for a FD_STORE_SOME / FD_F64 handle holding Q.  The work is enqueued on
  * cuda_stream (NULL = default stream) and the call returns without waiting.
  *
- * Scratch: a fixed device array inside the library holds the primitives and
- * the nine velocity gradients of at most FD_NOALLOC_MAX_POINTS grid points
- * (29.4 MB, kept by every GPU that loads the library until the process
- * exits).  All calls share it and it keeps the last call's contents, which
+ * Scratch: a fixed device array inside the library holds the primitives,
+ * the nine velocity gradients and three sums of them for at most
+ * FD_NOALLOC_MAX_POINTS grid points (35.7 MB, kept by every GPU that loads
+ * the library until the process exits).  All calls share it and it keeps the last call's contents, which
  * no call reads before overwriting; two calls whose work overlaps on the GPU
  * (different streams, or host threads racing on one device) race on it and
  * must be ordered by the caller.  The first call on each device looks up the

@@ -9,8 +9,9 @@
 //   W[2]  primitives u, v, w, p, T (stored in every family, Section 2),
 //         ping-pong: the last kernel of a stage writes the primitives of the
 //         new state into W[1-wcur] while the stage reads W[wcur];
-//   work  SS, RS: 9 velocity-gradient arrays; BL: 18 product + 45 first- and
-//         18 second-derivative arrays;
+//   work  SS, RS: 9 velocity-gradient arrays (binary64: and the 3 pair sums
+//         of the diagonal ones); BL: 18 product + 45 first- and 18
+//         second-derivative arrays;
 //   Wf[2] binary32 mode: the ten perturbation fields, ping-pong likewise
 //         (ghost-padded for the TMA-staged recompute-all kernel; W[0] then
 //         only serves as scratch of the diagnostics and the residual);
@@ -164,7 +165,7 @@ Layout plan(long long n, int algorithm, int dtype, size_t wf_points) {
         // state Q[2], Qs hold double-words (8 bytes per value, like binary64)
         L.wd0 = take(10 * n * sizeof(fd::df64));
         L.wd1 = take(10 * n * sizeof(fd::df64));
-        if (stores_g(algorithm)) L.gd = take(9 * n * sizeof(fd::df64));
+        if (stores_g(algorithm)) L.gd = take(fd::kGradArrays<fd::df64> * n * sizeof(fd::df64));
         if (algorithm == FD_STORE_ALL) {
             L.p = take(18 * n * sizeof(fd::df64));
             L.d1 = take(45 * n * sizeof(fd::df64));
@@ -172,7 +173,7 @@ Layout plan(long long n, int algorithm, int dtype, size_t wf_points) {
         }
     } else if (dtype == FD_F64) {
         L.w1 = take(f5);
-        if (stores_g(algorithm)) L.g = take(9 * n * sizeof(double));
+        if (stores_g(algorithm)) L.g = take(fd::kGradArrays<double> * n * sizeof(double));
         if (algorithm == FD_STORE_ALL) {
             L.p = take(18 * n * sizeof(double));
             L.d1 = take(45 * n * sizeof(double));
@@ -181,7 +182,7 @@ Layout plan(long long n, int algorithm, int dtype, size_t wf_points) {
     } else {
         L.wf0 = take(10 * wf_points * sizeof(float));
         L.wf1 = take(10 * wf_points * sizeof(float));
-        if (stores_g(algorithm)) L.gf = take(9 * n * sizeof(float));
+        if (stores_g(algorithm)) L.gf = take(fd::kGradArrays<float> * n * sizeof(float));
         if (algorithm == FD_STORE_ALL) {
             L.p = take(18 * n * sizeof(float));
             L.d1 = take(45 * n * sizeof(float));

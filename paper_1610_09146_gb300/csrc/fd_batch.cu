@@ -354,7 +354,8 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
         const size_t wpts = h.padded ? fd::padded_field_points(fd::make_grid(h.d.nx, h.d.ny, h.d.nz)) : (size_t)h.n;
         h.w0 = take(wfields * wpts * tsize);
         h.w1 = take(wfields * wpts * tsize);
-        h.g = desc[i].algorithm == FD_STORE_SOME ? take(9 * (size_t)h.n * tsize) : (size_t)-1;
+        const size_t garrays = dtype == FD_F64 ? fd::kGradArrays<double> : fd::kGradArrays<float>;
+        h.g = desc[i].algorithm == FD_STORE_SOME ? take(garrays * (size_t)h.n * tsize) : (size_t)-1;
     }
     std::vector<fd::BatchTile> t_ss, t_ra, t_all;
     make_tiles(b, FD_STORE_SOME, false, t_ss);

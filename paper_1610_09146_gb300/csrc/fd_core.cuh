@@ -67,6 +67,15 @@ struct Shift5 {
 // instruction is issued in a step.
 template <class T>
 struct Prec;
+// Whether the store-some gradient arrays carry the three pair sums of their
+// diagonal (binary64 only; see the store-some kernels).
+template <class T>
+constexpr bool kStoresPairSums = false;
+template <>
+constexpr bool kStoresPairSums<double> = true;
+// Gradient arrays of the store-some / recompute-some families per precision.
+template <class T>
+constexpr int kGradArrays = kStoresPairSums<T> ? 12 : 9;
 template <>
 struct Prec<double> {
     using S = double;

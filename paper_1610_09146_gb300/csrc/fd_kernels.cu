@@ -31,6 +31,7 @@
 #include <cuda.h>
 
 #include <cstdlib>
+#include <type_traits>
 
 #include "fd_core.cuh"
 #include "fd_internal.h"
@@ -377,12 +378,18 @@ struct GlobalAcc {
 #pragma unroll
         for (int a = 0; a < 4; ++a) t[a] = ld(p, s.c + s.o[i][a]);
     }
-    // taps along i of G_aa + G_bb
+    // taps along i of G_aa + G_bb, summed at each tap
     __device__ __forceinline__ void grad_pair_taps(int ga, int gb, int i, T t[4]) const {
         const T* pa = Gw + (3 * ga + ga) * n;
         const T* pb = Gw + (3 * gb + gb) * n;
 #pragma unroll
         for (int a = 0; a < 4; ++a) t[a] = ld(pa, s.c + s.o[i][a]) + ld(pb, s.c + s.o[i][a]);
+    }
+    // taps along i of the stored pair sum P_i = G_jj + G_kk (j, k the other axes)
+    __device__ __forceinline__ void pair_taps(int i, T t[4]) const {
+        const T* p = Gw + 9 * (size_t)n + (size_t)i * n;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) t[a] = ld(p, s.c + s.o[i][a]);
     }
 };
 
@@ -395,8 +402,9 @@ struct GlobalAcc {
 // with G_ij = D_j u_i.  The convective pair of each direction is one
 // difference of the product Q_f (u_j + u_j(centre)) formed at the taps, equal
 // to D_j(Q_f u_j) + u_j D_j Q_f by linearity of the stencil.  STORED_G: SS
-// reads G from the nine gradient arrays and differences G_jj + G_kk for the
-// mixed derivatives; otherwise (RA) G and D_i(D_k u_k) come from u taps.
+// reads G from the nine gradient arrays and differences the stored pair sums
+// P_i = G_jj + G_kk for the mixed derivatives; otherwise (RA) G and
+// D_i(D_k u_k) come from u taps.
 template <class T, bool STORED_G, class Acc>
 __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T R[5]) {
     constexpr int U = 5, P = 8, TT = 9;  // field indices of u_0, p, T
@@ -467,7 +475,10 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
         const int j1 = i == 0 ? 1 : 0, j2 = i == 2 ? 1 : 2;  // the two axes other than i
         if constexpr (STORED_G) {
             T t[4];
-            A.grad_pair_taps(j1, j2, i, t);
+            if constexpr (kStoresPairSums<T>)
+                A.pair_taps(i, t);
+            else
+                A.grad_pair_taps(j1, j2, i, t);
             vi = fmx(k.vmix1[i], delta1_taps(t), vi);
         } else {
 #pragma unroll
@@ -876,34 +887,73 @@ __global__ void __launch_bounds__(kMThreads, 2)
 // Store-some (Section 2, paragraph SS): the nine velocity gradients
 // du_i/dx_j go to global work arrays; every other derivative is evaluated
 // into thread-local registers in the fused kernel.  The mixed derivatives
-// D_i(D_k u_k) difference the stored gradients.
+// D_i(D_k u_k) difference the stored gradients.  In binary64, where FP64
+// instructions are the limit, the gradient pass also stores the three pair
+// sums P_i = G_jj + G_kk (j, k the axes other than i), the sum the fused
+// kernel otherwise forms at each of the four taps (same operands, same order,
+// same result; 9 fewer FP64 instructions per point).  The binary32 and df64
+// kernels are bound by memory and latency, where the three extra arrays cost
+// more than they save, so they keep forming the sums.
+template <class T>
+__device__ __forceinline__ void store_pair_sums(const T G[3][3], T* __restrict__ P, int n, int c) {
+    if constexpr (kStoresPairSums<T>) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int j1 = i == 0 ? 1 : 0, j2 = i == 2 ? 1 : 2;
+            P[i * n + c] = G[j1][j1] + G[j2][j2];
+        }
+    }
+}
 template <class T>
 __global__ void __launch_bounds__(256) k_ss_grad(Grid g, Coef<T> k, const T* __restrict__ Wf, T* __restrict__ Gw) {
     int idx = grid_index();
     if (idx >= g.n) return;
     const int n = g.n;
     const Nbr s = make_nbr(g, idx);
+    T G[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             T t[4];
             taps(Wf + i * n, s.c, s.o[j], t);
-            Gw[(3 * i + j) * n + s.c] = k.s1[j] * delta1_taps(t);
+            G[i][j] = k.s1[j] * delta1_taps(t);
+            Gw[(3 * i + j) * n + s.c] = G[i][j];
         }
+    store_pair_sums(G, Gw + 9 * (size_t)n, n, s.c);
 }
 
 template <class T, bool RESID>
-__global__ void __launch_bounds__(128) k_ss(Grid g, Coef<T> k, Phys ph, RKStage rk, const T* __restrict__ Qf,
-                                            const T* __restrict__ Wf, const T* __restrict__ Gw,
-                                            const state_t<T>* __restrict__ Q64, state_t<T>* __restrict__ out,
-                                            state_t<T>* __restrict__ Qs, T* __restrict__ Wnext) {
+__device__ __forceinline__ void ss_point(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk,
+                                         const T* __restrict__ Qf, const T* __restrict__ Wf,
+                                         const T* __restrict__ Gw, const state_t<T>* __restrict__ Q64,
+                                         state_t<T>* __restrict__ out, state_t<T>* __restrict__ Qs,
+                                         T* __restrict__ Wnext) {
     int idx = grid_index();
     if (idx >= g.n) return;
     const Nbr s = make_nbr(g, idx);
     T R[5];
     fused_residual<T, true>(GlobalAcc<T>{s, g.n, Qf, Wf, Gw}, k, R);
     stage_write<T, RESID>(rk, ph, g.n, s.c, Q64, R, out, Qs, Wnext);
+}
+
+// binary64 and df64: registers capped for four blocks (16 warps) per SM; the
+// binary32 form keeps the compiler's own register choice (fewer, no cap).
+template <class T, bool RESID>
+__global__ void __launch_bounds__(128, 4) k_ss(Grid g, Coef<T> k, Phys ph, RKStage rk, const T* __restrict__ Qf,
+                                            const T* __restrict__ Wf, const T* __restrict__ Gw,
+                                            const state_t<T>* __restrict__ Q64, state_t<T>* __restrict__ out,
+                                            state_t<T>* __restrict__ Qs, T* __restrict__ Wnext) {
+    ss_point<T, RESID>(g, k, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
+}
+
+template <bool RESID>
+__global__ void __launch_bounds__(128) k_ss_f32(Grid g, Coef<float> k, Phys ph, RKStage rk,
+                                                const float* __restrict__ Qf, const float* __restrict__ Wf,
+                                                const float* __restrict__ Gw, const df64* __restrict__ Q64,
+                                                df64* __restrict__ out, df64* __restrict__ Qs,
+                                                float* __restrict__ Wnext) {
+    ss_point<float, RESID>(g, k, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
 }
 
 // ------------------------------------------------------------------ BL
@@ -1357,14 +1407,17 @@ __global__ void __launch_bounds__(256) k_batch_grad(const BatchInst<T>* __restri
         const T* Wf = sizeof(T) == sizeof(double) ? Wc : Wc + 5 * (size_t)n;
         for (int p = threadIdx.x; p < tl.count; p += blockDim.x) {
             const Nbr s = make_nbr(I.g, tl.start + p);
+            T G[3][3];
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     T tp[4];
                     taps(Wf + i * n, s.c, s.o[j], tp);
-                    I.G[(3 * i + j) * n + s.c] = I.k.s1[j] * delta1_taps(tp);
+                    G[i][j] = I.k.s1[j] * delta1_taps(tp);
+                    I.G[(3 * i + j) * n + s.c] = G[i][j];
                 }
+            store_pair_sums(G, I.G + 9 * (size_t)n, n, s.c);
         }
     }
 }
@@ -1775,10 +1828,17 @@ template <class T>
 cudaError_t launch_ss(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid, const T* Qf,
                       const T* Wf, const T* Gw, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext,
                       cudaStream_t st) {
-    if (resid)
-        k_ss<T, true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
-    else
-        k_ss<T, false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
+    if constexpr (std::is_same<T, float>::value) {
+        if (resid)
+            k_ss_f32<true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
+        else
+            k_ss_f32<false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
+    } else {
+        if (resid)
+            k_ss<T, true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
+        else
+            k_ss<T, false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
+    }
     return cudaGetLastError();
 }
 

@@ -9,10 +9,11 @@
 // another framework's pool).  fd_residual needs a handle, and fd_create
 // allocates; this entry point needs neither.
 //
-// The scratch holds the primitives u, v, w, p, T (5 arrays) and the nine
-// velocity gradients (9 arrays) of at most FD_NOALLOC_MAX_POINTS points.  It
-// is a file-scope __device__ array, so every GPU that loads the library keeps
-// it (14 x 262144 x 8 bytes = 29.4 MB) until the process exits.
+// The scratch holds the primitives u, v, w, p, T (5 arrays), the nine
+// velocity gradients and the three pair sums of the diagonal ones (12 arrays)
+// of at most FD_NOALLOC_MAX_POINTS points.  It is a file-scope __device__
+// array, so every GPU that loads the library keeps it (17 x 262144 x 8 bytes
+// = 35.7 MB) until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -22,7 +23,7 @@
 
 namespace {
 
-constexpr int kScratchArrays = 14;  // u, v, w, p, T + nine du_i/dx_j
+constexpr int kScratchArrays = 17;  // u, v, w, p, T + nine du_i/dx_j + three pair sums
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchArrays * (size_t)FD_NOALLOC_MAX_POINTS];
@@ -103,7 +104,7 @@ extern "C" int fd_residual_noalloc(const double* Q, double* R, int nx, int ny, i
     // in it has to start at zero; what the previous call left there is unused.
     const size_t n = (size_t)g.n;
     double* W = scratch;          // u, v, w, p, T
-    double* G = scratch + 5 * n;  // du_i/dx_j at (3 i + j) * n
+    double* G = scratch + 5 * n;  // du_i/dx_j at (3 i + j) * n, pair sums at (9 + i) * n
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const fd::RKStage rk{0.0, 0.0, 0};
     if (fd::launch_prims_f64(g, ph, Q, W, st) != cudaSuccess) return FD_ECUDA;

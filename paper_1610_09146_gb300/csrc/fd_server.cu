@@ -119,7 +119,8 @@ Layout layout_of(const fd_request& r, bool tma) {
     L.qs = take(5 * n * sizeof(double));
     L.w0 = take(wf * wpts * t);
     L.w1 = take(wf * wpts * t);
-    L.g = r.algorithm == FD_STORE_SOME ? take(9 * n * t) : (size_t)-1;
+    const size_t garrays = r.dtype == FD_F64 ? fd::kGradArrays<double> : fd::kGradArrays<float>;
+    L.g = r.algorithm == FD_STORE_SOME ? take(garrays * n * t) : (size_t)-1;
     L.total = off;
     return L;
 }
