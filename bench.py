@@ -57,8 +57,10 @@ HBM_FALLBACK_GBS = 6800.0
 # design notes); the fused kernels include the primitives of the next stage, which they
 # write with the update (so "prims" runs only after a state is set).
 COST = {
-    ("f64", "store_some", "fused"): (409.7, 285.3, 273.7),
-    ("f64", "store_some", "grad"): (45, 96, 36),
+    # binary64 SS: the gradient pass also stores the three pair sums of the diagonal
+    # gradients (ncu at 160^3: fused 260/260/255 FP64 instructions by stage, grad 39)
+    ("f64", "store_some", "fused"): (406.7, 309.3, 258.3),
+    ("f64", "store_some", "grad"): (48, 120, 39),
     ("f64", "recompute_all", "fused"): (556.7, 213.3, 377.7),
     ("f64", "store_all", "fused"): (177, 701.3, 140),
     ("f64", "store_all", "deriv1"): (225, 576, 180),
@@ -70,7 +72,7 @@ COST = {
     # the six mixed derivatives at the shifted taps; same bytes as SS / RA.  Flops and
     # instructions are ncu's DADD + DMUL + 2 DFMA (resp. their sum) per point, 64^3 grid
     ("f64", "recompute_some", "fused"): (669.7, 285.3, 518.3),
-    ("f64", "recompute_some", "grad"): (45, 96, 36),
+    ("f64", "recompute_some", "grad"): (48, 120, 39),
     ("f64", "store_none", "fused"): (710.7, 213.3, 553.3),
     # binary32 mode: the state and its RK update are double-words (no FP64 instructions)
     ("f32", "store_some", "fused"): (415.7, 222.7, 0),
@@ -243,10 +245,10 @@ def roofline_of(dtype, alg, kern, n, hbm_peak, hbm_src):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch at 256^3, from ncu captures of the
-# current kernels: binary64 SS fused on a 160^3 grid (two launches, 287 B per point) scaled by
-# the point count; binary32 RA (TMA-staged) at 256^3 itself (mean of the three stages'
-# launches: 3.44, 3.43, 2.76 GB).  None where no capture of the current kernel exists.
-TRAFFIC = {("f64", "store_some", "fused"): 4.82e9, ("f32", "recompute_all", "fused"): 3.21e9}
+# current kernels: binary64 SS fused on a 160^3 grid (three launches, 291 / 332 / 294 B per
+# point by stage) scaled by the point count; binary32 RA (TMA-staged) at 256^3 itself (mean
+# of the three stages' launches: 3.44, 3.43, 2.76 GB).  None where no capture exists.
+TRAFFIC = {("f64", "store_some", "fused"): 5.12e9, ("f32", "recompute_all", "fused"): 3.21e9}
 
 
 def e2e_run(fd, torch, alg, dtype, n, steps):
