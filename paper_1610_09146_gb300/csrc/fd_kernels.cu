@@ -352,6 +352,7 @@ __device__ __forceinline__ void taps(const T* __restrict__ f, int c, const int* 
 // staged ring of planes.  Both feed the same arithmetic below.
 template <class T>
 struct GlobalAcc {
+    static constexpr bool kZQueue = false;
     const Nbr& s;
     int n;
     const T* __restrict__ Qf;
@@ -481,8 +482,16 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
                 A.grad_pair_taps(j1, j2, i, t);
             vi = fmx(k.vmix1[i], delta1_taps(t), vi);
         } else {
+            bool queued = false;
+            if constexpr (Acc::kZQueue) {
+                if (i == 2) {  // D_z(D_x u_x + D_y u_y) from the queued planes
+                    const T t[4] = {A.zq[0], A.zq[1], A.zq[3], A.zq[4]};
+                    vi = fmx(k.vmix1[2], delta1_taps(t), vi);
+                    queued = true;
+                }
+            }
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < (queued ? 0 : 2); ++q) {
                 const int kk = q == 0 ? j1 : j2;
                 T t[4];
 #pragma unroll
@@ -547,11 +556,16 @@ constexpr int kZChunk = 64;
 
 // Shared-memory accessor over a ring of staged planes: plane slot s, field f,
 // row ty + OY + dy, column tx + OX + dx of an SX x SY array per field.
-template <class T, int SX, int SY, int OX, int OY>
+template <class T, int SX, int SY, int OX, int OY, bool ZQ = false>
 struct SmemAccT {
+    // ZQ: the z-marching kernels keep A = D_x u_x + D_y u_y of planes z-2 .. z+2
+    // of the thread's column in registers (zq), so D_z(D_x u_x + D_y u_y) is one
+    // difference of five queued values instead of 32 shared-memory taps.
+    static constexpr bool kZQueue = ZQ;
     const T* sm;
     int slot[5];  // ring slots of planes z-2 .. z+2
     int tx, ty;
+    const T* zq = nullptr;
     __device__ __forceinline__ T at(int f, int dz, int dy, int dx) const {
         return sm[((slot[dz + 2] * kNF + f) * SY + (ty + OY + dy)) * SX + (tx + OX + dx)];
     }
@@ -571,9 +585,19 @@ struct SmemAccT {
             t[b] = at(f, o[2], o[1], o[0]);
         }
     }
+    // D_x u_x + D_y u_y at the thread's column, plane z + dz (fields 5, 6: u, v)
+    __device__ __forceinline__ T gxx_gyy(int dz, const Coef<T>& k) const {
+        T tu[4], tv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            tu[a] = at(5, dz, 0, d(a));
+            tv[a] = at(6, dz, d(a), 0);
+        }
+        return fmx(k.s1[0], delta1_taps(tu), k.s1[1] * delta1_taps(tv));
+    }
 };
 template <class T>
-using SmemAcc = SmemAccT<T, kSX, kSY, 2, 2>;
+using SmemAcc = SmemAccT<T, kSX, kSY, 2, 2, true>;
 
 // One tile (x0, y0) and z-chunk starting at zbeg, by one block of kTX x kTY
 // threads, with `sm` the block's ring of staged planes.
@@ -614,6 +638,7 @@ __device__ __forceinline__ void ra_tiled_block(T* sm, const Grid& g, const Coef<
     for (int dz = -2; dz <= 1; ++dz) stage_plane(zbeg + dz, dz + 2);
     const int x = x0 + tx, y = y0 + ty;
     const bool inside = x < nx && y < ny;
+    T aq[5];  // D_x u_x + D_y u_y of planes z-2 .. z+2 at (x, y)
     for (int z = zbeg; z < zend; ++z) {
         const int r0 = z - zbeg;  // ring slot of plane z + dz is (r0 + dz + 2) % 5
         const int c = (z * ny + y) * nx + x;
@@ -628,8 +653,16 @@ __device__ __forceinline__ void ra_tiled_block(T* sm, const Grid& g, const Coef<
         if (inside) {
             SmemAcc<T> A{sm, {r0 % kRing, (r0 + 1) % kRing, (r0 + 2) % kRing, (r0 + 3) % kRing, (r0 + 4) % kRing},
                          tx, ty};
+            if (z == zbeg) {
+#pragma unroll
+                for (int dz = -2; dz <= 1; ++dz) aq[dz + 2] = A.gxx_gyy(dz, k);
+            }
+            aq[4] = A.gxx_gyy(2, k);
+            A.zq = aq;
             T R[5];
             fused_residual<T, false>(A, k, R);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) aq[q] = aq[q + 1];
             if (RESID) {
 #pragma unroll
                 for (int f = 0; f < 5; ++f) out[(size_t)f * n + c] = to_state(R[f]);
@@ -769,6 +802,7 @@ __device__ __forceinline__ bool ra_tma_item(float* sm, unsigned bar0, unsigned& 
     }
     const int x = x0 + tx, y = y0 + ty;
     const bool inside = x < nx && y < ny;
+    float aq[5];  // D_x u_x + D_y u_y of planes z-2 .. z+2 at (x, y)
     for (int z = zbeg; z < zend; ++z) {
         const int c = (z * ny + y) * nx + x;
         if (z + 3 <= zlast) {
@@ -783,10 +817,18 @@ __device__ __forceinline__ bool ra_tma_item(float* sm, unsigned bar0, unsigned& 
         }
         if (__syncthreads_or(!wait(z + 2))) return fail(issued);
         if (inside) {
-            SmemAccT<float, kBX, kBY, 4, 2> A{
+            SmemAccT<float, kBX, kBY, 4, 2, true> A{
                 sm, {slot_of(z - 2), slot_of(z - 1), slot_of(z), slot_of(z + 1), slot_of(z + 2)}, tx, ty};
+            if (z == zbeg) {
+#pragma unroll
+                for (int dz = -2; dz <= 1; ++dz) aq[dz + 2] = A.gxx_gyy(dz, k);
+            }
+            aq[4] = A.gxx_gyy(2, k);
+            A.zq = aq;
             float R[5];
             fused_residual<float, false>(A, k, R);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) aq[q] = aq[q + 1];
             if (RESID) {
 #pragma unroll
                 for (int f = 0; f < 5; ++f) out[(size_t)f * n + c] = to_state(R[f]);
