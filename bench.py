@@ -58,10 +58,12 @@ HBM_FALLBACK_GBS = 6800.0
 # write with the update (so "prims" runs only after a state is set).
 COST = {
     # binary64 SS: the gradient pass also stores the three pair sums of the diagonal
-    # gradients (ncu at 160^3: fused 260/260/255 FP64 instructions by stage, grad 39)
-    ("f64", "store_some", "fused"): (406.7, 309.3, 258.3),
+    # gradients; the fused residual weights every tap through one FMA (ncu at 160^3:
+    # fused 229/229/224 FP64 instructions and 405/405/395 flops by stage, grad 39)
+    ("f64", "store_some", "fused"): (401.7, 309.3, 227.3),
     ("f64", "store_some", "grad"): (48, 120, 39),
-    ("f64", "recompute_all", "fused"): (556.7, 213.3, 377.7),
+    # binary64 RA, tap-weighted (ncu at 160^3: 347/347/342 instructions, 562/562/552 flops)
+    ("f64", "recompute_all", "fused"): (558.7, 213.3, 345.3),
     ("f64", "store_all", "fused"): (177, 701.3, 140),
     ("f64", "store_all", "deriv1"): (225, 576, 180),
     ("f64", "store_all", "deriv2"): (114, 200, 84),
@@ -368,7 +370,7 @@ def run_ours(args):
                                "roofline": roofline_of("f32", alg, kern, npts, hbm_peak, hbm_src),
                                "ke_rel_vs_binary64": abs(diag[0] - results[alg]["ke"]) / results[alg]["ke"]}
     cl = clocks.stop()
-    e2e = e2e_run(fd, torch, best, args.dtype, n, max(4, min(args.steps, 10)))
+    e2e = e2e_run(fd, torch, best, args.dtype, n, max(4, min(args.steps, 40)))
     e2e["value"], _ = aggregate_over_ranks(1e3 * npts * e2e["steps"] / e2e["value"], npts, e2e["steps"], dist,
                                            "cuda")
     r = results[best]

@@ -73,6 +73,15 @@ template <class T>
 constexpr bool kStoresPairSums = false;
 template <>
 constexpr bool kStoresPairSums<double> = true;
+// Whether the fused residual weights each tap value separately (binary64,
+// bound by FP64 instruction issue: one FMA per tap instead of a difference,
+// a scale and an accumulate per pair) or forms the unscaled differences of the
+// stencil first (binary32 and double-word: the error analysis of the binary32
+// mode and the exact power-of-two scalings of the double-word helpers).
+template <class T>
+constexpr bool kTapWeighted = false;
+template <>
+constexpr bool kTapWeighted<double> = true;
 // Gradient arrays of the store-some / recompute-some families per precision.
 template <class T>
 constexpr int kGradArrays = kStoresPairSums<T> ? 12 : 9;
@@ -186,6 +195,12 @@ __device__ __forceinline__ df64 delta2_taps(const df64 t[4], df64 f0) {
 //   vmix1[i]   = nu/3 / (12 h_i)          SS: D_i of the stored gradients G_kk
 //   ks2[j]     = kappa / (12 h_j^2)       heat flux (Eq. 5)
 //   c_rho, c_E = -1, -(rhoE0 + p0) in the binary32 perturbation form, 0 otherwise
+// and the per-tap weights of the binary64 form (kTapWeighted), where every tap
+// value enters the residual through one fused multiply-add:
+//   c8[j]      = 8 c1[j]                  convective taps -1, +1 (c1[j]: taps -2, +2)
+//   v16[i][j]  = 16 vs2[i][j]             Laplacian taps -1, +1 (vs2: taps -2, +2)
+//   vc[i]      = -30 sum_j vs2[i][j]      Laplacian centre
+//   k16[j], kc = 16 ks2[j], -30 sum_j ks2[j]   heat flux
 template <class T>
 struct Coef {
     T s1[3];
@@ -197,6 +212,11 @@ struct Coef {
     T ks2[3];
     T nu;
     T c_rho, c_E;
+    T c8[3];
+    T v16[3][3];
+    T vc[3];
+    T k16[3];
+    T kc;
 };
 
 // Derivative terms that enter the residual at one point (physical units).

@@ -402,7 +402,10 @@ struct GlobalAcc {
 //                + nu [ 2 sum_i G_ii^2 + sum_{i<j} (G_ij + G_ji)^2 - 2/3 div^2 ]  (Eqs. 3-5)
 // with G_ij = D_j u_i.  The convective pair of each direction is one
 // difference of the product Q_f (u_j + u_j(centre)) formed at the taps, equal
-// to D_j(Q_f u_j) + u_j D_j Q_f by linearity of the stencil.  STORED_G: SS
+// to D_j(Q_f u_j) + u_j D_j Q_f by linearity of the stencil.  In binary64
+// (kTapWeighted) the stencil weight of each tap is folded into that product's
+// velocity factor and every tap value enters through one FMA (the same sums,
+// associated per tap instead of per difference).  STORED_G: SS
 // reads G from the nine gradient arrays and differences the stored pair sums
 // P_i = G_jj + G_kk for the mixed derivatives; otherwise (RA) G and
 // D_i(D_k u_k) come from u taps.
@@ -435,31 +438,76 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
     for (int f = 0; f < 5; ++f) R[f] = A.center(f) * hd;
 
     // convective sums, pressure gradient and pressure work, direction by direction
+    if constexpr (kTapWeighted<T>) {
+        // w_a (u_j(tap a) + u_j(centre)) with the stencil weight w_a of tap a
+        // folded in once per direction; each of the five fields then adds
+        // Q_f(tap a) times it, one FMA per tap.  The pressure work sums
+        // p(tap a) w_a u_j(tap a) (c1 = cp / 2, doubled at the end).
+        T pw = 0;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        T ut[4], st[4], pt[4];
-        A.taps(U + j, j, ut);
-        A.taps(P, j, pt);
+        for (int j = 0; j < 3; ++j) {
+            T ut[4], pt[4], wu[4], ws[4];
+            A.taps(U + j, j, ut);
+            A.taps(P, j, pt);
+            const T w[4] = {k.c1[j], -k.c8[j], k.c8[j], -k.c1[j]};
 #pragma unroll
-        for (int a = 0; a < 4; ++a) st[a] = ut[a] + uc[j];
+            for (int a = 0; a < 4; ++a) {
+                wu[a] = w[a] * ut[a];
+                ws[a] = fmx(w[a], uc[j], wu[a]);
+            }
 #pragma unroll
-        for (int f = 0; f < 5; ++f) {
-            T qt[4];
-            A.taps(f, j, qt);
-            R[f] = fmx(k.c1[j], delta1_prod(qt, st), R[f]);
+            for (int f = 0; f < 5; ++f) {
+                T qt[4];
+                A.taps(f, j, qt);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) R[f] = fmx(qt[a], ws[a], R[f]);
+            }
+            R[1 + j] = fmx(k.cp[j], delta1_taps(pt), R[1 + j]);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) pw = fmx(pt[a], wu[a], pw);
         }
-        R[1 + j] = fmx(k.cp[j], delta1_taps(pt), R[1 + j]);
-        R[4] = fmx(k.cp[j], delta1_prod(pt, ut), R[4]);
+        R[4] = fmx(T(2), pw, R[4]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T ut[4], st[4], pt[4];
+            A.taps(U + j, j, ut);
+            A.taps(P, j, pt);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) st[a] = ut[a] + uc[j];
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                T qt[4];
+                A.taps(f, j, qt);
+                R[f] = fmx(k.c1[j], delta1_prod(qt, st), R[f]);
+            }
+            R[1 + j] = fmx(k.cp[j], delta1_taps(pt), R[1 + j]);
+            R[4] = fmx(k.cp[j], delta1_prod(pt, ut), R[4]);
+        }
     }
 
     // heat flux
     {
         const T T0 = A.center(TT);
+        if constexpr (kTapWeighted<T>) {
+            T h = fmx(k.kc, T0, R[4]);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            T t[4];
-            A.taps(TT, j, t);
-            R[4] = fmx(k.ks2[j], delta2_taps(t, T0), R[4]);
+            for (int j = 0; j < 3; ++j) {
+                T t[4];
+                A.taps(TT, j, t);
+                h = fmx(k.k16[j], t[1], h);
+                h = fmx(k.k16[j], t[2], h);
+                h = fmx(-k.ks2[j], t[0], h);
+                h = fmx(-k.ks2[j], t[3], h);
+            }
+            R[4] = h;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                T t[4];
+                A.taps(TT, j, t);
+                R[4] = fmx(k.ks2[j], delta2_taps(t, T0), R[4]);
+            }
         }
     }
 
@@ -467,11 +515,24 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         T vi = 0;
+        if constexpr (kTapWeighted<T>) {
+            vi = k.vc[i] * uc[i];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            T t[4];
-            A.taps(U + i, j, t);
-            vi = fmx(k.vs2[i][j], delta2_taps(t, uc[i]), vi);
+            for (int j = 0; j < 3; ++j) {
+                T t[4];
+                A.taps(U + i, j, t);
+                vi = fmx(k.v16[i][j], t[1], vi);
+                vi = fmx(k.v16[i][j], t[2], vi);
+                vi = fmx(-k.vs2[i][j], t[0], vi);
+                vi = fmx(-k.vs2[i][j], t[3], vi);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                T t[4];
+                A.taps(U + i, j, t);
+                vi = fmx(k.vs2[i][j], delta2_taps(t, uc[i]), vi);
+            }
         }
         const int j1 = i == 0 ? 1 : 0, j2 = i == 2 ? 1 : 2;  // the two axes other than i
         if constexpr (STORED_G) {

@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "../../include/fdgb300.h"
+#include "fd_host.h"
 #include "fd_internal.h"
 
 namespace {
@@ -61,43 +62,9 @@ extern "C" int fd_residual_noalloc(const double* Q, double* R, int nx, int ny, i
     double* scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) return FD_ECUDA;
 
-    const double kPi = 3.14159265358979323846;
-    fd::Grid g{};
-    g.nx = nx;
-    g.ny = ny;
-    g.nz = nz;
-    g.n = nx * ny * nz;
-    const int ns[3] = {nx, ny, nz};
-    for (int a = 0; a < 3; ++a) {
-        double h = 2.0 * kPi / ns[a];
-        g.inv12h[a] = 1.0 / (12.0 * h);
-        g.inv12h2[a] = 1.0 / (12.0 * h * h);
-        g.inv12hf[a] = (float)g.inv12h[a];
-        g.inv12h2f[a] = (float)g.inv12h2[a];
-    }
-    fd::Phys ph{};
-    ph.gamma = gamma;
-    ph.gm1 = gamma - 1.0;
-    ph.gM2 = gamma * Mach * Mach;
-    ph.nu = 1.0 / Re;
-    ph.kappa = 1.0 / ((gamma - 1.0) * Mach * Mach * Pr * Re);
-    ph.p0 = 1.0 / (gamma * Mach * Mach);
-    ph.rhoE0 = ph.p0 / (gamma - 1.0);
-    fd::Coef<double> k{};
-    for (int j = 0; j < 3; ++j) {
-        double s1 = g.inv12h[j], s2 = g.inv12h2[j];
-        k.s1[j] = s1;
-        k.c1[j] = -0.5 * s1;
-        k.cp[j] = -s1;
-        k.ks2[j] = ph.kappa * s2;
-        k.vmix1[j] = ph.nu / 3.0 * s1;
-    }
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            k.vs2[i][j] = ph.nu * g.inv12h2[j] * (i == j ? 4.0 / 3.0 : 1.0);
-            k.vmix[i][j] = ph.nu / 3.0 * g.inv12h[i] * g.inv12h[j];
-        }
-    k.nu = ph.nu;
+    const fd::Grid g = fd::make_grid(nx, ny, nz);
+    const fd::Phys ph = fd::make_phys(Re, Mach, Pr, gamma);
+    const fd::Coef<double> k = fd::make_coef<double>(g, ph, false);
 
     // The scratch is rewritten in full before it is read on every call (the
     // primitives from Q, then the gradients from the primitives), so nothing
