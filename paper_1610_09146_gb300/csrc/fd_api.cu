@@ -227,9 +227,10 @@ cudaError_t stage_kernels(fd_handle* h, const fd::RKStage& rk, bool resid, const
     cudaError_t e;
     switch (h->algorithm) {
         case FD_RECOMPUTE_ALL:
-            // binary32: fields staged through shared memory (the global-memory
-            // kernel is latency-bound on its tap loads); binary64 is bound by FP64
-            // issue, where staging does not help.
+            // binary32 and df64: fields staged through shared memory (the
+            // global-memory kernel is latency-bound on its tap loads; df64 256^3
+            // step 16.2 -> 11.0 ms); binary64 is bound by FP64 issue, where staging
+            // does not help.
             return timed(h, FD_KERNEL_FUSED, [&] {
                 if constexpr (std::is_same<T, float>::value) {
                     if (h->use_tma)  // Qf is the first of the ten fields of Wf[0] or Wf[1]
@@ -237,8 +238,10 @@ cudaError_t stage_kernels(fd_handle* h, const fd::RKStage& rk, bool resid, const
                                                  reinterpret_cast<S*>(h->Qs), Wnext, h->kerr, st);
                     return fd::launch_ra_tiled<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, reinterpret_cast<S*>(h->Qs),
                                                   Wnext, st);
-                }
-                else
+                } else if constexpr (std::is_same<T, fd::df64>::value) {
+                    return fd::launch_ra_tiled<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, reinterpret_cast<S*>(h->Qs),
+                                                  Wnext, st);
+                } else
                     return fd::launch_ra<T>(g, k, ph, rk, resid, Qf, Wf, Qin, Qout, reinterpret_cast<S*>(h->Qs),
                                             Wnext, st);
             });

@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(128) k_ra(Grid g, Coef<T> k, Phys ph, RKStage 
     stage_write<T, RESID>(rk, ph, g.n, s.c, Q64, R, out, Qs, Wnext);
 }
 
-// Recompute-all with shared-memory staging (binary32 mode).  A block of
+// Recompute-all with shared-memory staging (binary32 and df64 modes).  A block of
 // kTX x kTY threads owns that x-y tile and marches a chunk of z-planes; the
 // ten working fields of planes z-2 .. z+2, each with a two-point x-y halo
 // (periodic, by modulo index), sit in a ring of five shared-memory planes.
@@ -693,7 +693,7 @@ __device__ __forceinline__ void ra_tiled_block(T* sm, const Grid& g, const Coef<
             const T* src = f < 5 ? Qf + (size_t)f * n : Wf + (size_t)(f - 5) * n;
 #pragma unroll
             for (int r = 0; r < 2; ++r)
-                if (has[r]) dst[f * kPlane + tid + r * kTX * kTY] = __ldg(src + base + off[r]);
+                if (has[r]) dst[f * kPlane + tid + r * kTX * kTY] = ld(src + base, off[r]);
         }
     };
     for (int dz = -2; dz <= 1; ++dz) stage_plane(zbeg + dz, dz + 2);
@@ -2022,6 +2022,9 @@ template cudaError_t launch_ra_tiled<double>(const Grid&, const Coef<double>&, c
                                              cudaStream_t);
 template cudaError_t launch_ra_tiled<float>(const Grid&, const Coef<float>&, const Phys&, const RKStage&, bool,
                                             const float*, const float*, const df64*, df64*, df64*, float*,
+                                            cudaStream_t);
+template cudaError_t launch_ra_tiled<df64>(const Grid&, const Coef<df64>&, const Phys&, const RKStage&, bool,
+                                            const df64*, const df64*, const df64*, df64*, df64*, df64*,
                                             cudaStream_t);
 
 cudaError_t launch_diagnostics_f64(const Grid& g, const double* Q, double* Wv, double* partial, double* out,
