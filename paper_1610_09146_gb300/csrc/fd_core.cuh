@@ -185,6 +185,25 @@ __device__ __forceinline__ df64 delta2_taps(const df64 t[4], df64 f0) {
     return (scale2(t[2] + t[1], 16.0f) - (t[3] + t[0])) - times_fp(f0, 30.0f);
 }
 
+// Per-tap weights of the binary64 fused residual (kTapWeighted), where every
+// tap value enters the residual through one fused multiply-add:
+//   c8[j]      = 8 c1[j]                  convective taps -1, +1 (c1[j]: taps -2, +2)
+//   v16[i][j]  = 16 vs2[i][j]             Laplacian taps -1, +1 (vs2: taps -2, +2)
+//   vc[i]      = -30 sum_j vs2[i][j]      Laplacian centre
+//   k16[j], kc = 16 ks2[j], -30 sum_j ks2[j]   heat flux
+// Empty in the other precisions, so their coefficient records keep their size
+// (the batched TMA kernel holds one per block in shared memory beside its ring).
+template <class T>
+struct TapWeights {};
+template <>
+struct TapWeights<double> {
+    double c8[3];
+    double v16[3][3];
+    double vc[3];
+    double k16[3];
+    double kc;
+};
+
 // Coefficients of the fused residual (RA and SS), precomputed on the host so
 // that every derivative enters the residual through one multiply-add:
 //   c1[j]      = -1/2 / (12 h_j)      skew convective sums (Eq. skewscalar)
@@ -195,14 +214,9 @@ __device__ __forceinline__ df64 delta2_taps(const df64 t[4], df64 f0) {
 //   vmix1[i]   = nu/3 / (12 h_i)          SS: D_i of the stored gradients G_kk
 //   ks2[j]     = kappa / (12 h_j^2)       heat flux (Eq. 5)
 //   c_rho, c_E = -1, -(rhoE0 + p0) in the binary32 perturbation form, 0 otherwise
-// and the per-tap weights of the binary64 form (kTapWeighted), where every tap
-// value enters the residual through one fused multiply-add:
-//   c8[j]      = 8 c1[j]                  convective taps -1, +1 (c1[j]: taps -2, +2)
-//   v16[i][j]  = 16 vs2[i][j]             Laplacian taps -1, +1 (vs2: taps -2, +2)
-//   vc[i]      = -30 sum_j vs2[i][j]      Laplacian centre
-//   k16[j], kc = 16 ks2[j], -30 sum_j ks2[j]   heat flux
+// and, through TapWeights, the per-tap weights of the binary64 form (kTapWeighted).
 template <class T>
-struct Coef {
+struct Coef : TapWeights<T> {
     T s1[3];
     T c1[3];
     T cp[3];
@@ -212,11 +226,6 @@ struct Coef {
     T ks2[3];
     T nu;
     T c_rho, c_E;
-    T c8[3];
-    T v16[3][3];
-    T vc[3];
-    T k16[3];
-    T kc;
 };
 
 // Derivative terms that enter the residual at one point (physical units).

@@ -87,19 +87,21 @@ Coef<T> make_coef(const Grid& g, const Phys& ph, bool shifted) {
         }
     // tap weights of the binary64 residual (exact multiples of the above but
     // the centre sums, which are rounded once here)
-    for (int j = 0; j < 3; ++j) {
-        k.c8[j] = (T)(-4.0 * g.inv12h[j]);
-        k.k16[j] = (T)(16.0 * ph.kappa * g.inv12h2[j]);
-    }
-    k.kc = (T)(-30.0 * ph.kappa * (g.inv12h2[0] + g.inv12h2[1] + g.inv12h2[2]));
-    for (int i = 0; i < 3; ++i) {
-        double sum = 0.0;
+    if constexpr (kTapWeighted<T>) {
         for (int j = 0; j < 3; ++j) {
-            const double v = ph.nu * g.inv12h2[j] * (i == j ? 4.0 / 3.0 : 1.0);
-            k.v16[i][j] = (T)(16.0 * v);
-            sum += v;
+            k.c8[j] = -4.0 * g.inv12h[j];
+            k.k16[j] = 16.0 * ph.kappa * g.inv12h2[j];
         }
-        k.vc[i] = (T)(-30.0 * sum);
+        k.kc = -30.0 * ph.kappa * (g.inv12h2[0] + g.inv12h2[1] + g.inv12h2[2]);
+        for (int i = 0; i < 3; ++i) {
+            double sum = 0.0;
+            for (int j = 0; j < 3; ++j) {
+                const double v = ph.nu * g.inv12h2[j] * (i == j ? 4.0 / 3.0 : 1.0);
+                k.v16[i][j] = 16.0 * v;
+                sum += v;
+            }
+            k.vc[i] = -30.0 * sum;
+        }
     }
     k.nu = (T)ph.nu;
     k.c_rho = shifted ? (T)-1.0 : (T)0.0;

@@ -951,6 +951,9 @@ struct TmaItem {
     df64* Qs;
     float* Wnext;
 };
+// Two blocks per SM need 2 x (ring + item, in 128-byte units) + 2 x 1 KB of the
+// SM's 228 KB: the item may take at most 464 bytes beside the 115,248-byte ring.
+static_assert(sizeof(TmaItem) <= 464, "TmaItem too large for two batched TMA blocks per SM");
 
 template <bool RESID>
 __global__ void __launch_bounds__(kMThreads, 2)
