@@ -16,9 +16,11 @@
 // the shifted (perturbation) fields avoid the loss of digits that the large
 // mean pressure and energy (p0 = 1/(gamma M^2)) would cause in the
 // differences.  One thread evaluates one grid point (RS: one thread per point
-// and equation); periodic boundaries (Section 3) are the wrapped neighbour
-// offsets of fd::Nbr, or a ghost-padded field layout for the TMA-staged
-// binary32 recompute-all kernel.
+// and equation), except the z-marching recompute-all kernels (binary32 and
+// df64), where a block stages planes of a tile in shared memory; periodic
+// boundaries (Section 3) are the wrapped neighbour offsets of fd::Nbr, modulo
+// halo indices (thread-staged tiles), or a ghost-padded field layout for the
+// TMA-staged binary32 recompute-all kernel.
 //
 // Sections: initial condition; primitives and the RK update; the fused
 // residual (RA, SS) and its accessors; RA (global memory, shared-memory
@@ -27,7 +29,8 @@
 //
 // On GB300 binary64 issues at 1/64 of the binary32 rate, so the binary64
 // kernels are bound by FP64 instructions per point, not by memory traffic;
-// stencil taps are read through the read-only data cache.
+// stencil taps are read through the read-only data cache, and the binary64
+// fused residual weights every tap through one FMA (kTapWeighted).
 #include <cuda.h>
 
 #include <cstdlib>
