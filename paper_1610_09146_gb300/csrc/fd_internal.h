@@ -32,7 +32,7 @@ cudaError_t launch_from_df64(const df64* src, double* dst, long long n, const Sh
 // shifted double-words), out the next state (or R when resid), Qs the saved
 // register, Wnext the working fields of `out` for the next stage (written by
 // the last kernel of a stage unless resid).
-//   RA: launch_ra (binary32: launch_ra_tiled / launch_ra_tma)
+//   RA: launch_ra (binary64), launch_ra_tiled (df64, binary32), launch_ra_tma (binary32)
 //   SS: launch_ss_grad, launch_ss
 //   BL: launch_bl_prod, launch_bl_d1, launch_bl_d2, launch_bl_res
 //   SN: launch_sn;  RS: launch_ss_grad, launch_rs

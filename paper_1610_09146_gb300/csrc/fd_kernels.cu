@@ -2002,9 +2002,12 @@ cudaError_t launch_rs(const Grid& g, const Phys& ph, const RKStage& rk, bool res
     return cudaGetLastError();
 }
 
+// binary64 recompute-all runs the global-memory kernel; binary32 and df64 run
+// the z-marching kernels (launch_ra_tiled, launch_ra_tma)
+template cudaError_t launch_ra<double>(const Grid&, const Coef<double>&, const Phys&, const RKStage&, bool,
+                                       const double*, const double*, const double*, double*, double*, double*,
+                                       cudaStream_t);
 #define FD_INSTANTIATE(T)                                                                                        \
-    template cudaError_t launch_ra<T>(const Grid&, const Coef<T>&, const Phys&, const RKStage&, bool, const T*,  \
-                                      const T*, const state_t<T>*, state_t<T>*, state_t<T>*, T*, cudaStream_t); \
     template cudaError_t launch_ss_grad<T>(const Grid&, const Coef<T>&, const T*, T*, cudaStream_t);            \
     template cudaError_t launch_ss<T>(const Grid&, const Coef<T>&, const Phys&, const RKStage&, bool, const T*,  \
                                       const T*, const T*, const state_t<T>*, state_t<T>*, state_t<T>*, T*,      \
@@ -2023,9 +2026,6 @@ FD_INSTANTIATE(double)
 FD_INSTANTIATE(float)
 FD_INSTANTIATE(df64)
 #undef FD_INSTANTIATE
-template cudaError_t launch_ra_tiled<double>(const Grid&, const Coef<double>&, const Phys&, const RKStage&, bool,
-                                             const double*, const double*, const double*, double*, double*, double*,
-                                             cudaStream_t);
 template cudaError_t launch_ra_tiled<float>(const Grid&, const Coef<float>&, const Phys&, const RKStage&, bool,
                                             const float*, const float*, const df64*, df64*, df64*, float*,
                                             cudaStream_t);
