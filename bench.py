@@ -58,12 +58,13 @@ HBM_FALLBACK_GBS = 6800.0
 # write with the update (so "prims" runs only after a state is set).
 COST = {
     # binary64 SS: the gradient pass also stores the three pair sums of the diagonal
-    # gradients; the fused residual weights every tap through one FMA (ncu at 160^3:
-    # fused 229/229/224 FP64 instructions and 405/405/395 flops by stage, grad 39)
-    ("f64", "store_some", "fused"): (401.7, 309.3, 227.3),
+    # gradients; the fused residual weights every tap through one FMA and starts each
+    # momentum residual as Q hd + v_i (ncu at 160^3: fused 226/226/221 FP64 instructions
+    # and 405/405/395 flops by stage, grad 39)
+    ("f64", "store_some", "fused"): (401.7, 309.3, 224.3),
     ("f64", "store_some", "grad"): (48, 120, 39),
-    # binary64 RA, tap-weighted (ncu at 160^3: 347/347/342 instructions, 562/562/552 flops)
-    ("f64", "recompute_all", "fused"): (558.7, 213.3, 345.3),
+    # binary64 RA, tap-weighted (ncu at 160^3: 344/344/339 instructions, 562/562/552 flops)
+    ("f64", "recompute_all", "fused"): (558.7, 213.3, 342.3),
     ("f64", "store_all", "fused"): (177, 701.3, 140),
     ("f64", "store_all", "deriv1"): (225, 576, 180),
     ("f64", "store_all", "deriv2"): (114, 200, 84),

@@ -437,8 +437,74 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
     }
     const T div = G[0][0] + G[1][1] + G[2][2];
     const T hd = T(-0.5) * div;
+    // viscous stress divergence v_i = nu [ sum_j D2_j u_i + 1/3 sum_k D_ik u_k ]
+    auto viscous = [&](int i) {
+        T vi = 0;
+        if constexpr (kTapWeighted<T>) {
+            vi = k.vc[i] * uc[i];
 #pragma unroll
-    for (int f = 0; f < 5; ++f) R[f] = A.center(f) * hd;
+            for (int j = 0; j < 3; ++j) {
+                T t[4];
+                A.taps(U + i, j, t);
+                vi = fmx(k.v16[i][j], t[1], vi);
+                vi = fmx(k.v16[i][j], t[2], vi);
+                vi = fmx(-k.vs2[i][j], t[0], vi);
+                vi = fmx(-k.vs2[i][j], t[3], vi);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                T t[4];
+                A.taps(U + i, j, t);
+                vi = fmx(k.vs2[i][j], delta2_taps(t, uc[i]), vi);
+            }
+        }
+        const int j1 = i == 0 ? 1 : 0, j2 = i == 2 ? 1 : 2;  // the two axes other than i
+        if constexpr (STORED_G) {
+            T t[4];
+            if constexpr (kStoresPairSums<T>)
+                A.pair_taps(i, t);
+            else
+                A.grad_pair_taps(j1, j2, i, t);
+            vi = fmx(k.vmix1[i], delta1_taps(t), vi);
+        } else {
+            bool queued = false;
+            if constexpr (Acc::kZQueue) {
+                if (i == 2) {  // D_z(D_x u_x + D_y u_y) from the queued planes
+                    const T t[4] = {A.zq[0], A.zq[1], A.zq[3], A.zq[4]};
+                    vi = fmx(k.vmix1[2], delta1_taps(t), vi);
+                    queued = true;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < (queued ? 0 : 2); ++q) {
+                const int kk = q == 0 ? j1 : j2;
+                T t[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    T u4[4];
+                    A.taps_shifted(U + kk, kk, i, a, u4);
+                    t[a] = delta1_taps(u4);
+                }
+                vi = fmx(k.vmix[i][kk], delta1_taps(t), vi);
+            }
+        }
+        return vi;
+    };
+    // binary64: the viscous terms first, so that each momentum residual starts
+    // as Q_f hd + v_i in one FMA
+    [[maybe_unused]] T vis[3];
+    if constexpr (kTapWeighted<T>) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) vis[i] = viscous(i);
+        R[0] = A.center(0) * hd;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) R[1 + i] = fmx(A.center(1 + i), hd, vis[i]);
+        R[4] = A.center(4) * hd;
+    } else {
+#pragma unroll
+        for (int f = 0; f < 5; ++f) R[f] = A.center(f) * hd;
+    }
 
     // convective sums, pressure gradient and pressure work, direction by direction
     if constexpr (kTapWeighted<T>) {
@@ -515,60 +581,16 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
     }
 
     // viscous stress divergence and its work
+    if constexpr (kTapWeighted<T>) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        T vi = 0;
-        if constexpr (kTapWeighted<T>) {
-            vi = k.vc[i] * uc[i];
+        for (int i = 0; i < 3; ++i) R[4] = fmx(uc[i], vis[i], R[4]);
+    } else {
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                T t[4];
-                A.taps(U + i, j, t);
-                vi = fmx(k.v16[i][j], t[1], vi);
-                vi = fmx(k.v16[i][j], t[2], vi);
-                vi = fmx(-k.vs2[i][j], t[0], vi);
-                vi = fmx(-k.vs2[i][j], t[3], vi);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                T t[4];
-                A.taps(U + i, j, t);
-                vi = fmx(k.vs2[i][j], delta2_taps(t, uc[i]), vi);
-            }
+        for (int i = 0; i < 3; ++i) {
+            const T vi = viscous(i);
+            R[1 + i] += vi;
+            R[4] = fmx(uc[i], vi, R[4]);
         }
-        const int j1 = i == 0 ? 1 : 0, j2 = i == 2 ? 1 : 2;  // the two axes other than i
-        if constexpr (STORED_G) {
-            T t[4];
-            if constexpr (kStoresPairSums<T>)
-                A.pair_taps(i, t);
-            else
-                A.grad_pair_taps(j1, j2, i, t);
-            vi = fmx(k.vmix1[i], delta1_taps(t), vi);
-        } else {
-            bool queued = false;
-            if constexpr (Acc::kZQueue) {
-                if (i == 2) {  // D_z(D_x u_x + D_y u_y) from the queued planes
-                    const T t[4] = {A.zq[0], A.zq[1], A.zq[3], A.zq[4]};
-                    vi = fmx(k.vmix1[2], delta1_taps(t), vi);
-                    queued = true;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < (queued ? 0 : 2); ++q) {
-                const int kk = q == 0 ? j1 : j2;
-                T t[4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    T u4[4];
-                    A.taps_shifted(U + kk, kk, i, a, u4);
-                    t[a] = delta1_taps(u4);
-                }
-                vi = fmx(k.vmix[i][kk], delta1_taps(t), vi);
-            }
-        }
-        R[1 + i] += vi;
-        R[4] = fmx(uc[i], vi, R[4]);
     }
 
     // viscous dissipation tau_ij D_j u_i
