@@ -606,9 +606,12 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
         diss = fmx(T(-2.0 / 3.0) * div, div, diss);
         R[4] = fmx(k.nu, diss, R[4]);
     }
-    if (k.c_rho != T(0)) {
-        R[0] = fmx(k.c_rho, div, R[0]);
-        R[4] = fmx(k.c_E, div, R[4]);
+    // the perturbation form's mean-state terms (binary64 fields are not shifted)
+    if constexpr (!std::is_same<T, double>::value) {
+        if (k.c_rho != T(0)) {
+            R[0] = fmx(k.c_rho, div, R[0]);
+            R[4] = fmx(k.c_E, div, R[4]);
+        }
     }
 }
 
