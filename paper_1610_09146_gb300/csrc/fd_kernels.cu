@@ -408,10 +408,12 @@ struct GlobalAcc {
 // to D_j(Q_f u_j) + u_j D_j Q_f by linearity of the stencil.  In binary64
 // (kTapWeighted) the stencil weight of each tap is folded into that product's
 // velocity factor and every tap value enters through one FMA (the same sums,
-// associated per tap instead of per difference).  STORED_G: SS
-// reads G from the nine gradient arrays and differences the stored pair sums
-// P_i = G_jj + G_kk for the mixed derivatives; otherwise (RA) G and
-// D_i(D_k u_k) come from u taps.
+// associated per tap instead of per difference), and the viscous terms come
+// first so that each momentum residual starts as Q_f (-div/2) + v_i in one
+// FMA.  STORED_G: SS reads G from the nine gradient arrays and, for the mixed
+// derivatives, differences P_i = G_jj + G_kk (stored by the gradient pass in
+// binary64, summed at the taps otherwise); without it (RA) G and D_i(D_k u_k)
+// come from u taps.
 template <class T, bool STORED_G, class Acc>
 __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T R[5]) {
     constexpr int U = 5, P = 8, TT = 9;  // field indices of u_0, p, T
