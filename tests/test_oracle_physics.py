@@ -56,6 +56,38 @@ def test_tgv_initial_enstrophy_closed_form(n, mach):
     assert abs(ens - expect) < 1e-15
 
 
+@pytest.mark.parametrize("n", [8, 12, 16])
+def test_kinetic_energy_is_density_weighted(n):
+    # rho = 1 + a cos 2x, u = sin x: <rho u^2 / 2> = (1/2 - a/4) / 2 on any grid of
+    # more than 4 points (the unweighted mean would be 1/4)
+    a = 0.3
+    X, Y, Z = grid(n)
+    rho = 1.0 + a * np.cos(2 * X)
+    Q = np.zeros((5, n, n, n))
+    Q[0] = rho
+    Q[1] = rho * np.sin(X)
+    Q[4] = 200.0
+    ke, _ = O.diagnostics(Q)
+    assert abs(ke - (0.25 - a / 8)) < 1e-15
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_curl_free_field_has_zero_enstrophy(n):
+    # u = v = w = f(x + y + z) on a cubic grid: every D_j u_i differences the same
+    # stencil values (up to the rounding of x + y + z), so each vorticity component
+    # is a difference of two equal numbers; a sign slip would give |omega| ~ 1
+    X, Y, Z = grid(n)
+    f = 0.5 * np.sin(X + Y + Z)
+    rho = 1.0 + 0.1 * np.cos(2 * X)
+    Q = np.zeros((5, n, n, n))
+    Q[0] = rho
+    Q[1] = Q[2] = Q[3] = rho * f
+    Q[4] = 200.0
+    ke, ens = O.diagnostics(Q)
+    assert ens < 1e-24
+    assert abs(ke - 0.1875) < 1e-15  # 3/2 <rho f^2>, the cos 2x weighting averages out here
+
+
 def test_tgv_initial_state_fields():
     n = 16
     Q = O.tgv_ic(n, n, n, GAMMA, 0.1)
