@@ -15,7 +15,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PIN_FILES = ["test_oracle_stencils.py", "test_oracle_rk.py", "test_oracle_physics.py"]
 
-# name: (text in oracle/fd_oracle.c, mistaken text); each original occurs exactly once
+# name: (text in oracle/fd_oracle.c, mistaken text); each original occurs exactly once.
+# (Storing the velocity gradients transposed is not among them: the residual uses
+# only their diagonal and the symmetric sum tau_ij G_ij, so it computes the same.)
 MUTATIONS = {
     # first and second differences (Section 2, fourth-order central stencils)
     "d1_scale": ("(8.0 * (fp1 - fm1) - (fp2 - fm2)) / (12.0 * h)", "(8.0 * (fp1 - fm1) - (fp2 - fm2)) / (12.5 * h)"),
@@ -43,9 +45,28 @@ MUTATIONS = {
     "heat_flux_sign": ("RE[q] += kappa * d2[q];", "RE[q] -= kappa * d2[q];"),
     "stress_index": ("s += tau * G[(3 * i + j) * n + q];", "s += tau * G[(3 * i + i) * n + q];"),
     "viscous_work_dropped": ("RE[q] += u[i][q] * (nu * visc[q]);", "RE[q] += 0.0;"),
+    "pressure_work_sign": ("for (long q = 0; q < n; ++q) RE[q] -= d[q];", "for (long q = 0; q < n; ++q) RE[q] += d[q];"),
+    "viscosity_scale": ("double nu = 1.0 / P->Re;", "double nu = 1.0 / (2.0 * P->Re);"),
+    "conductivity_prandtl_dropped": ("P->Mach * P->Mach * P->Pr * P->Re);", "P->Mach * P->Mach * P->Re);"),
+    "dissipation_two_thirds": ("(i == j ? 2.0 / 3.0 * dk : 0.0)", "(i == j ? 1.0 / 3.0 * dk : 0.0)"),
+    "dissipation_symmetric_part": ("G[(3 * i + j) * n + q] + G[(3 * j + i) * n + q] -",
+                                   "G[(3 * i + j) * n + q] + G[(3 * i + j) * n + q] -"),
+    "divergence_index": ("double dk = G[0 * n + q] + G[4 * n + q] + G[8 * n + q];",
+                         "double dk = G[0 * n + q] + G[4 * n + q] + G[7 * n + q];"),
+    "ic_velocity_sign": ("double v = -cos(x) * sin(y) * cos(z);", "double v = cos(x) * sin(y) * cos(z);"),
+    "d1_wrapped_tap": ("double* out) {\n#pragma omp parallel for schedule(static)\n    for (int z = 0; z < nz; ++z)\n"
+                       "        for (int y = 0; y < ny; ++y)\n            for (int x = 0; x < nx; ++x) {\n"
+                       "                double fm2, fm1, fp1, fp2;\n                if (axis == 0) {\n"
+                       "                    fm2 = f[at(nx, ny, wrap(x - 2, nx), y, z)];",
+                       "double* out) {\n#pragma omp parallel for schedule(static)\n    for (int z = 0; z < nz; ++z)\n"
+                       "        for (int y = 0; y < ny; ++y)\n            for (int x = 0; x < nx; ++x) {\n"
+                       "                double fm2, fm1, fp1, fp2;\n                if (axis == 0) {\n"
+                       "                    fm2 = f[at(nx, ny, wrap(x - 3, nx), y, z)];"),
     # low-storage RK3 (Section 2, Fig. 1)
     "rk_a_coefficient": ("{2.0 / 3.0, 5.0 / 12.0, 3.0 / 5.0}", "{2.0 / 3.0, 5.0 / 12.0, 0.6000001}"),
     "rk_b_coefficient": ("{1.0 / 4.0, 3.0 / 20.0, 0.0}", "{1.0 / 4.0, 3.0 / 19.0, 0.0}"),
+    "rk_register_kept_one_stage_short": ("if (s < 2) Qs[q] = qs + OR_RK_B[s] * dt * R[q];",
+                                         "if (s < 1) Qs[q] = qs + OR_RK_B[s] * dt * R[q];"),
     # diagnostics (Section 3)
     "vorticity_sign": ("double oy = G[(3 * 0 + 2) * n + q] - G[(3 * 2 + 0) * n + q];",
                        "double oy = G[(3 * 0 + 2) * n + q] + G[(3 * 2 + 0) * n + q];"),
