@@ -47,6 +47,18 @@ def test_binding_covers_every_declared_symbol():
     assert set(declared_functions()) <= set(native.exported_symbols()) | {"fd_create"}
 
 
+def test_binding_constants_match_the_header():
+    text = open(os.path.join(ROOT, "include", "fdgb300.h")).read()
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (FD_[A-Z0-9_]+) \(?(-?\d+)\)?", text)}
+    assert len(defines) >= 20
+    for name, value in defines.items():
+        assert getattr(native, name) == value, name
+    # the profile class names follow the FD_KERNEL_* numbering
+    classes = sorted((v, k) for k, v in defines.items() if k.startswith("FD_KERNEL_") and k != "FD_KERNEL_CLASSES")
+    assert [k[len("FD_KERNEL_"):].lower() for _, k in classes] == list(native.KERNEL_CLASS_NAMES)
+    assert len(classes) == defines["FD_KERNEL_CLASSES"]
+
+
 @pytest.mark.parametrize("args,code", [
     ((4, 16, 16, 1600, 0.1, 0.71, 1.4, 1e-3, 0, 0), fd.FD_EINVAL),          # axis < 5
     ((16, 16, 16, 0.0, 0.1, 0.71, 1.4, 1e-3, 0, 0), fd.FD_EINVAL),          # Re <= 0
