@@ -62,7 +62,8 @@ extern "C" {
  * evaluate the derivative set of the paper as written, with identical
  * arithmetic per derivative.  In all five the primitive variables u_i, p, T
  * are evaluated and stored (Section 2, the paragraph after Fig. 1).  Every
- * family exists for every dtype; the batch and server take SS and RA. */
+ * family exists for the dtypes FD_F64, FD_F32_ACCDW and FD_DF64; FD_F64_DW is
+ * store-some only; the batch and server take SS and RA. */
 #define FD_STORE_ALL 0
 #define FD_STORE_SOME 1
 #define FD_RECOMPUTE_ALL 2
@@ -93,6 +94,18 @@ extern "C" {
 #define FD_F64 0
 #define FD_F32_ACCDW 1
 #define FD_DF64 2
+/* FD_F64_DW     binary64 results (the binary64 parity bound of FD_F64) from
+ *               mixed arithmetic, store-some family only: the state, the saved
+ *               register, the RK update and the pressure p of Eq. 6 (whose
+ *               mean is ~70 times its variation at Mach 0.1, so its binary64
+ *               rounding is what the smallest momentum component resolves)
+ *               are binary64, and the pressure gradient differences the
+ *               binary64 pressures exactly; every other term of the residual
+ *               and the nine stored velocity gradients use the double-word
+ *               arithmetic of FD_DF64 on shifted fields.  About 27 binary64
+ *               instructions per point and stage instead of ~260.  No
+ *               counterpart in the paper. */
+#define FD_F64_DW 3
 
 /* Device allocator callbacks (for example PyTorch's caching allocator).
  * alloc returns a device pointer aligned to at least 256 bytes, or NULL;
@@ -117,7 +130,7 @@ typedef struct fd_handle fd_handle;
  *               gamma > 1; dt > 0 is the time step of every fd_step;
  *   algorithm   FD_STORE_ALL, FD_STORE_SOME, FD_RECOMPUTE_ALL,
  *               FD_RECOMPUTE_SOME or FD_STORE_NONE;
- *   dtype       FD_F64, FD_F32_ACCDW or FD_DF64;
+ *   dtype       FD_F64, FD_F32_ACCDW, FD_DF64, or FD_F64_DW (FD_STORE_SOME only);
  *   alloc       NULL for cudaMalloc/cudaFree, else allocator callbacks;
  *   cuda_stream cudaStream_t for all work of this handle (NULL = default).
  * On success *out receives the handle.  Errors: FD_EINVAL, FD_ENOMEM,

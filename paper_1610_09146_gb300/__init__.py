@@ -20,8 +20,8 @@ import math
 import numpy as np
 
 from . import native
-from .native import (FD_DF64, FD_EBUSY, FD_ECUDA, FD_EINVAL, FD_ENOMEM, FD_EUNSTABLE, FD_F32_ACCDW, FD_F64, FD_OK,
-                     FD_RECOMPUTE_ALL, FD_RECOMPUTE_SOME, FD_STORE_ALL, FD_STORE_NONE, FD_STORE_SOME, FdAlloc, FdError, fd_check_finite, fd_create,
+from .native import (FD_DF64, FD_EBUSY, FD_ECUDA, FD_EINVAL, FD_ENOMEM, FD_EUNSTABLE, FD_F32_ACCDW, FD_F64, FD_F64_DW,
+                     FD_OK, FD_RECOMPUTE_ALL, FD_RECOMPUTE_SOME, FD_STORE_ALL, FD_STORE_NONE, FD_STORE_SOME, FdAlloc, FdError, fd_check_finite, fd_create,
                      fd_destroy, fd_device_bytes, fd_diagnostics, fd_get_state, fd_last_error, fd_residual,
                      fd_set_state, fd_step)
 
@@ -29,7 +29,7 @@ ALGORITHMS = {"store_all": FD_STORE_ALL, "store_some": FD_STORE_SOME, "recompute
               "recompute_some": FD_RECOMPUTE_SOME, "store_none": FD_STORE_NONE,
               "BL": FD_STORE_ALL, "SS": FD_STORE_SOME, "RA": FD_RECOMPUTE_ALL, "RS": FD_RECOMPUTE_SOME,
               "SN": FD_STORE_NONE}
-DTYPES = {"f64": FD_F64, "f32": FD_F32_ACCDW, "f32_accdw": FD_F32_ACCDW, "df64": FD_DF64}
+DTYPES = {"f64": FD_F64, "f32": FD_F32_ACCDW, "f32_accdw": FD_F32_ACCDW, "df64": FD_DF64, "f64dw": FD_F64_DW}
 
 from .workloads import dt_for_grid  # noqa: E402  (Section 3 time-step rule)
 
@@ -208,7 +208,8 @@ class Solver:
     algorithm: "store_all" | "store_some" | "recompute_all" | "recompute_some" | "store_none"
                (or "BL" | "SS" | "RA" | "RS" | "SN")
     dtype: "f64" | "f32" (binary32 stencils, compensated double-word state, binary64
-           reductions) | "df64" (double-word arithmetic on the binary32 pipe, binary64-accurate)
+           reductions) | "df64" (double-word arithmetic on the binary32 pipe) | "f64dw"
+           (store-some only: binary64 state, pressure and RK update, double-word stencils)
     stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (current torch stream)
     """
 

@@ -15,7 +15,8 @@
 //   Wf[2] binary32 mode: the ten perturbation fields, ping-pong likewise
 //         (ghost-padded for the TMA-staged recompute-all kernel; W[0] then
 //         only serves as scratch of the diagnostics and the residual);
-//   Wd[2] df64 mode: the ten perturbation fields as double-words;
+//   Wd[2] df64 and mixed (FD_F64_DW) modes: the ten perturbation fields as
+//         double-words (the mixed mode keeps binary64 u, v, w, p in W[2]);
 //   and the reduction scratch.  In the binary32 and df64 modes Q[2] and Qs
 //   hold shifted double-words, converted to and from binary64 at the API.
 #include <cuda_runtime.h>
@@ -132,8 +133,11 @@ int check_args(int nx, int ny, int nz, double Re, double Mach, double Pr, double
     if (algorithm != FD_STORE_ALL && algorithm != FD_STORE_SOME && algorithm != FD_RECOMPUTE_ALL &&
         algorithm != FD_RECOMPUTE_SOME && algorithm != FD_STORE_NONE)
         return fail_global(FD_EINVAL, "unknown algorithm %d", algorithm);
-    if (dtype != FD_F64 && dtype != FD_F32_ACCDW && dtype != FD_DF64)
+    if (dtype != FD_F64 && dtype != FD_F32_ACCDW && dtype != FD_DF64 && dtype != FD_F64_DW)
         return fail_global(FD_EINVAL, "unknown dtype %d", dtype);
+    if (dtype == FD_F64_DW && algorithm != FD_STORE_SOME)
+        return fail_global(FD_EINVAL, "dtype FD_F64_DW exists for the store-some family only (algorithm %d)",
+                           algorithm);
     return FD_OK;
 }
 
@@ -160,8 +164,14 @@ Layout plan(long long n, int algorithm, int dtype, size_t wf_points) {
     L.q1 = take(f5);
     L.qs = take(f5);
     L.w1 = L.g = L.p = L.d1 = L.d2 = L.wf0 = L.wf1 = L.gf = L.wd0 = L.wd1 = L.gd = (size_t)-1;
-    L.w0 = dtype == FD_DF64 ? (size_t)-1 : take(f5);
-    if (dtype == FD_DF64) {
+    L.w0 = dtype == FD_DF64 ? (size_t)-1 : take(dtype == FD_F64_DW ? 4 * n * sizeof(double) : f5);
+    if (dtype == FD_F64_DW) {
+        // binary64 state; W[2] the binary64 u, v, w, p; Wd[2] the double-word working fields
+        L.w1 = take(4 * n * sizeof(double));
+        L.wd0 = take(10 * n * sizeof(fd::df64));
+        L.wd1 = take(10 * n * sizeof(fd::df64));
+        L.gd = take(fd::kGradArrays<fd::df64> * n * sizeof(fd::df64));
+    } else if (dtype == FD_DF64) {
         // state Q[2], Qs hold double-words (8 bytes per value, like binary64)
         L.wd0 = take(10 * n * sizeof(fd::df64));
         L.wd1 = take(10 * n * sizeof(fd::df64));
@@ -299,6 +309,22 @@ cudaError_t run_stage(fd_handle* h, int s, bool resid, double* out) {
         return stage_kernels<double>(h, rk, resid, Qin, h->W[wc], h->G, h->P, h->D1, h->D2, Qin, Qout,
                                      resid ? nullptr : h->W[1 - wc]);
     }
+    if (h->dtype == FD_F64_DW) {  // store-some only (fd_create checks)
+        using fd::df64;
+        if (!h->wvalid) {
+            e = timed(h, FD_KERNEL_PRIMS,
+                      [&] { return fd::launch_prims_hyb(g, ph, Qin, h->Wd[wc], h->W[wc], h->stream); });
+            if (e != cudaSuccess) return e;
+            h->wvalid = true;
+        }
+        e = timed(h, FD_KERNEL_GRAD,
+                  [&] { return fd::launch_ss_grad<df64>(g, h->kw, h->Wd[wc] + 5 * n, h->Gd, h->stream); });
+        if (e != cudaSuccess) return e;
+        return timed(h, FD_KERNEL_FUSED, [&] {
+            return fd::launch_ss_hyb(g, h->kw, ph, rk, resid, h->Wd[wc], h->Gd, h->W[wc], Qin, Qout, h->Qs,
+                                     resid ? nullptr : h->Wd[1 - wc], resid ? nullptr : h->W[1 - wc], h->stream);
+        });
+    }
     if (h->dtype == FD_DF64) {
         using fd::df64;
         const df64* Qd = reinterpret_cast<const df64*>(Qin);
@@ -329,7 +355,7 @@ cudaError_t run_stage(fd_handle* h, int s, bool resid, double* out) {
 // binary32 and df64 modes: the state buffers hold shifted double-words; these
 // move a binary64 copy of the current state through the saved register Qs,
 // which is dead between steps (stage 0 rewrites it).
-bool dw_state(int dtype) { return dtype != FD_F64; }
+bool dw_state(int dtype) { return dtype == FD_F32_ACCDW || dtype == FD_DF64; }
 
 fd::Shift5 state_shift(const fd_handle* h) { return fd::Shift5{{1.0, 0.0, 0.0, 0.0, h->phys.rhoE0}}; }
 
@@ -554,9 +580,9 @@ int fd_diagnostics(fd_handle* h, double* ke, double* enstrophy) {
     // overwrite (binary64, df64), or W[0], unused by the binary32 stages.  The
     // double-word modes first convert the state to binary64 in Qs (dead
     // between steps).
-    double* Wv = h->dtype == FD_F64    ? h->W[1 - h->wcur]
-                 : h->dtype == FD_DF64 ? reinterpret_cast<double*>(h->Wd[1 - h->wcur])
-                                       : h->W[0];
+    double* Wv = h->dtype == FD_F64                               ? h->W[1 - h->wcur]
+                 : h->dtype == FD_DF64 || h->dtype == FD_F64_DW ? reinterpret_cast<double*>(h->Wd[1 - h->wcur])
+                                                                : h->W[0];
     const double* Q = h->Q[h->cur];
     cudaError_t e = cudaSuccess;
     if (dw_state(h->dtype)) {

@@ -87,6 +87,115 @@ __device__ __forceinline__ bool operator!=(df64 x, df64 y) { return x.hi != y.hi
 // a * b + c (a product then a sum; not a fused operation).
 __device__ __forceinline__ df64 fmx(df64 a, df64 b, df64 c) { return a * b + c; }
 
+// ---- binary64 <-> double-word by integer operations ----------------------
+// On GB300 every conversion instruction between binary32 and binary64 issues on
+// the FP64 pipe at the rate of a DFMA (2 per SM per clock, measured), so the
+// kernels that mix binary64 with double-word arithmetic move values between
+// the two formats by rearranging the IEEE 754 fields with integer operations.
+//
+// Bit images of the two formats (binary64: sign, 11-bit exponent E biased by
+// 1023, 52-bit fraction M; binary32: sign, 8-bit exponent biased by 127, 23-bit
+// fraction).
+__host__ __device__ __forceinline__ unsigned f32_bits(float x) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(x);
+#else
+    unsigned u;
+    __builtin_memcpy(&u, &x, 4);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ float f32_of(unsigned u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float x;
+    __builtin_memcpy(&x, &u, 4);
+    return x;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned f64_hi(double x) {
+#ifdef __CUDA_ARCH__
+    return (unsigned)__double2hiint(x);
+#else
+    unsigned long long u;
+    __builtin_memcpy(&u, &x, 8);
+    return (unsigned)(u >> 32);
+#endif
+}
+__host__ __device__ __forceinline__ unsigned f64_lo(double x) {
+#ifdef __CUDA_ARCH__
+    return (unsigned)__double2loint(x);
+#else
+    unsigned long long u;
+    __builtin_memcpy(&u, &x, 8);
+    return (unsigned)u;
+#endif
+}
+__host__ __device__ __forceinline__ double f64_of(unsigned hi, unsigned lo) {
+#ifdef __CUDA_ARCH__
+    return __hiloint2double((int)hi, (int)lo);
+#else
+    const unsigned long long u = ((unsigned long long)hi << 32) | lo;
+    double x;
+    __builtin_memcpy(&x, &u, 8);
+    return x;
+#endif
+}
+__host__ __device__ __forceinline__ float i32_to_f32(int i) {
+#ifdef __CUDA_ARCH__
+    return __int2float_rn(i);  // I2F: integer pipe, not FP64
+#else
+    return (float)i;
+#endif
+}
+
+// Double-word of a binary64 value x (about 48 of its 53 significand bits):
+//   hi = x rounded to 24 significand bits (half away from zero): the binary64
+//        fraction's top 23 bits, incremented when the next bit is set (a carry
+//        into the exponent field is the correct rounding), with the exponent
+//        re-biased by 1023 - 127 = 896;
+//   lo = x - hi, exactly the remaining 29 fraction bits as a signed integer
+//        (negative when hi was rounded up), converted to binary32 (rounded to
+//        24 bits) and scaled by 2^(E - 1075).
+// |x - (hi + lo)| <= 2^-48 |x| for 2^-74 <= |x| < 2^128; below 2^-74 the trailing
+// word is dropped and below 2^-126 the result is 0 (absolute error below 2^-74
+// resp. 2^-126); |x| >= 2^128, infinities and NaN map to a binary32 infinity or NaN.
+__host__ __device__ __forceinline__ df64 dw_of_f64(double x) {
+    const unsigned hw = f64_hi(x), lw = f64_lo(x);
+    const unsigned sign = hw & 0x80000000u;
+    const int E = (int)((hw >> 20) & 0x7ffu);
+    // (hw << 3) | (lw >> 29): exponent bits 8..0 over the top 23 fraction bits;
+    // adding 128 << 23 maps E mod 512 to E - 896 for 897 <= E <= 1150
+    const unsigned top = (hw << 3) | (lw >> 29);
+    unsigned hb = (top + 0x40000000u + ((lw >> 28) & 1u)) | sign;
+    const int rem = (int)(lw << 3) >> 3;  // the 29 trailing fraction bits, sign-extended from bit 28
+    const int se = E - 948 > 0 ? E - 948 : 0;  // binary32 exponent field of 2^(E - 1075), 0 below range
+    float lo = i32_to_f32(rem) * f32_of(((unsigned)se << 23) | sign);
+    if (E < 897) hb = sign;
+    if (E > 1150) {
+        const bool nan = E == 2047 && (((hw & 0xfffffu) | lw) != 0u);
+        hb = sign | (nan ? 0x7fc00000u : 0x7f800000u);
+        lo = 0.0f;
+    }
+    return df64(f32_of(hb), lo);
+}
+
+// Exact binary64 value of a binary32 number (normal numbers, zero, infinities
+// and NaN; binary32 subnormals, below 2^-126, become zero): the fraction moves
+// to the top of the binary64 fraction and the exponent is re-biased by 896.
+__host__ __device__ __forceinline__ double f64_of_f32(float f) {
+    const unsigned b = f32_bits(f);
+    const unsigned sign = b & 0x80000000u, mag = b & 0x7fffffffu;
+    if (mag < 0x00800000u) return f64_of(sign, 0u);
+    if (mag >= 0x7f800000u)
+        return f64_of(sign | 0x7ff00000u | (mag & 0x007fffffu ? 0x00080000u : 0u), 0u);
+    return f64_of(sign | ((mag >> 3) + 0x38000000u), b << 29);
+}
+
+// hi + lo of a double-word rounded to binary64 (one DADD).
+__host__ __device__ __forceinline__ double f64_of_dw(df64 x) { return f64_of_f32(x.hi) + f64_of_f32(x.lo); }
+
 // 1 / x: the binary32 reciprocal of the leading word refined by one Newton
 // step r' = r + r (1 - x r) evaluated in double-word arithmetic.
 __device__ __forceinline__ df64 recip(df64 x) {

@@ -68,6 +68,16 @@ template <class T>
 cudaError_t launch_ss(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid, const T* Qf,
                       const T* Wf, const T* Gw, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext,
                       cudaStream_t st);
+// Store-some in mixed binary64 / double-word arithmetic (FD_F64_DW): binary64
+// state Q / Qs / out, binary64 velocities and pressure W64 = (u, v, w, p) (4
+// arrays), the ten shifted double-word working fields F (as in the df64 mode)
+// and the nine double-word gradients of launch_ss_grad<df64> (given the df64
+// coefficients k).  launch_prims_hyb writes F and W64 of a state.
+cudaError_t launch_prims_hyb(const Grid& g, const Phys& ph, const double* Q, df64* F, double* W64,
+                             cudaStream_t st);
+cudaError_t launch_ss_hyb(const Grid& g, const Coef<df64>& k, const Phys& ph, const RKStage& rk, bool resid,
+                          const df64* F, const df64* Gw, const double* W64, const double* Q64, double* out,
+                          double* Qs, df64* Fnext, double* W64next, cudaStream_t st);
 template <class T>
 cudaError_t launch_bl_prod(const Grid& g, const T* Qf, const T* Wf, T* P, cudaStream_t st);
 template <class T>

@@ -414,7 +414,10 @@ struct GlobalAcc {
 // derivatives, differences P_i = G_jj + G_kk (stored by the gradient pass in
 // binary64, summed at the taps otherwise); without it (RA) G and D_i(D_k u_k)
 // come from u taps.
-template <class T, bool STORED_G, class Acc>
+//
+// PGRAD = false leaves the pressure gradient -D_i p out of the momentum
+// residuals (the mixed binary64 / double-word kernel adds it in binary64).
+template <class T, bool STORED_G, class Acc, bool PGRAD = true>
 __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T R[5]) {
     constexpr int U = 5, P = 8, TT = 9;  // field indices of u_0, p, T
     T uc[3];
@@ -533,7 +536,7 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
 #pragma unroll
                 for (int a = 0; a < 4; ++a) R[f] = fmx(qt[a], ws[a], R[f]);
             }
-            R[1 + j] = fmx(k.cp[j], delta1_taps(pt), R[1 + j]);
+            if constexpr (PGRAD) R[1 + j] = fmx(k.cp[j], delta1_taps(pt), R[1 + j]);
 #pragma unroll
             for (int a = 0; a < 4; ++a) pw = fmx(pt[a], wu[a], pw);
         }
@@ -552,7 +555,7 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
                 A.taps(f, j, qt);
                 R[f] = fmx(k.c1[j], delta1_prod(qt, st), R[f]);
             }
-            R[1 + j] = fmx(k.cp[j], delta1_taps(pt), R[1 + j]);
+            if constexpr (PGRAD) R[1 + j] = fmx(k.cp[j], delta1_taps(pt), R[1 + j]);
             R[4] = fmx(k.cp[j], delta1_prod(pt, ut), R[4]);
         }
     }
@@ -1090,6 +1093,142 @@ __global__ void __launch_bounds__(128) k_ss_f32(Grid g, Coef<float> k, Phys ph, 
                                                 df64* __restrict__ out, df64* __restrict__ Qs,
                                                 float* __restrict__ Wnext) {
     ss_point<float, RESID>(g, k, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
+}
+
+// ------------------------------------- SS, binary64 with double-word stencils
+// Store-some in mixed arithmetic (FD_F64_DW).  On GB300 a binary64 instruction
+// occupies its pipe as long as 64 binary32 ones do, and the binary64 fused
+// kernel is bound by that pipe.  This form keeps in binary64 what decides the
+// binary64 result, and evaluates the rest in double-word arithmetic:
+//   binary64:
+//   - the state Q, the saved register Qs and the RK update (Fig. 1), two FMAs
+//     per variable and register, so the state rounds as in the binary64 path;
+//   - the primitives u_i and p of Eq. 6, formed as in the binary64 path and
+//     stored.  The mean of p, 1/(gamma M^2), is ~70 times its variation at
+//     M = 0.1, and its binary64 rounding (one unit is 1.4e-14) is what the
+//     smallest variable, rho w, resolves through -D_z p; the pressure
+//     gradient differences the binary64 values (neighbouring pressures
+//     differ by far less than a factor 2, so each difference is exact), and
+//     only the exact differences move to double-word arithmetic;
+//   - div u = sum_i D_i u_i from the binary64 velocities, for the two terms
+//     that carry a mean: -div in the mass residual and -(rhoE0 + p0) div in the
+//     energy residual (the mean energy and the mean pressure work; ~250 div at
+//     M = 0.1, which would magnify a double-word div 250-fold);
+//   double-word, on shifted fields (rho-1, rho u_i, rho E - rhoE0, u_i,
+//   p - p0, T - 1) on the binary32 pipe, as in the df64 mode: convection,
+//   pressure work, the viscous stress divergence and its work, the
+//   dissipation, the heat flux and the nine velocity gradients.  Each is a
+//   stencil sum of operands no larger than the residual's own scale times the
+//   stencil weights, so its rounding (~2^-48 of the operands) stays near 1e-14
+//   of the residual.
+// Values move between the formats by integer operations on the IEEE fields
+// (dw_of_f64, f64_of_dw): a conversion instruction would cost a DFMA.
+//
+// Binary64 instructions per point and stage: 6 pressure differences, 14 for
+// div u (three first differences, their sum) and 2 FMAs adding its terms, 5
+// sums hi + lo of the residual, 10 RK FMAs (5 in stage 2), and ~17 for the
+// next stage's primitives (1 / rho, u_i, p, and rho - 1, rho E - rhoE0, p - p0).
+
+// Working fields of a binary64 state: the ten shifted double-word fields F and
+// the binary64 velocities and pressure W64 = (u, v, w, p).  u_i and p are the
+// binary64 path's own formulas; rho - 1, rho E - rhoE0 and p - p0 are exact in
+// binary64 (operands within a factor 2) and then split, and
+// T - 1 = (gamma M^2 (p - p0) - (rho - 1)) / rho is double-word arithmetic
+// (gamma M^2 p0 = 1).
+__device__ __forceinline__ void hyb_prims_point(const Phys& ph, const double q[5], df64* __restrict__ F,
+                                                double* __restrict__ W64, int n, int c) {
+    const double inv = 1.0 / q[0];
+    const double u = q[1] * inv, v = q[2] * inv, w = q[3] * inv;
+    const double p = ph.gm1 * fmx(-0.5, fmx(q[1], u, fmx(q[2], v, q[3] * w)), q[4]);
+    const df64 rp = dw_of_f64(q[0] - 1.0);
+    const df64 pp = dw_of_f64(p - ph.p0);
+    F[c] = rp;
+    F[n + c] = dw_of_f64(q[1]);
+    F[2 * n + c] = dw_of_f64(q[2]);
+    F[3 * n + c] = dw_of_f64(q[3]);
+    F[4 * n + c] = dw_of_f64(q[4] - ph.rhoE0);
+    F[5 * n + c] = dw_of_f64(u);
+    F[6 * n + c] = dw_of_f64(v);
+    F[7 * n + c] = dw_of_f64(w);
+    F[8 * n + c] = pp;
+    F[9 * n + c] = fmx(ph.gM2_w, pp, -rp) * dw_of_f64(inv);
+    W64[c] = u;
+    W64[n + c] = v;
+    W64[2 * n + c] = w;
+    W64[3 * n + c] = p;
+}
+
+__global__ void __launch_bounds__(256) k_prims_hyb(Grid g, Phys ph, const double* __restrict__ Q,
+                                                   df64* __restrict__ F, double* __restrict__ W64) {
+    const int idx = grid_index();
+    if (idx >= g.n) return;
+    const int n = g.n;
+    double q[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) q[f] = Q[f * n + idx];
+    hyb_prims_point(ph, q, F, W64, n, idx);
+}
+
+// Fused residual + RK update + next-stage working fields.  F / W64: the
+// working fields of the stage's state, Gw: its nine velocity gradients
+// (double-word, from k_ss_grad<df64>), Q64 the binary64 state the stage starts
+// from (read as Qs in stage 0), out the next state (or R when RESID), Fnext /
+// W64next the next stage's working fields.  k is the df64 mode's coefficient
+// record with its two mean-state terms (c_rho, c_E) set to zero: those enter
+// here in binary64, with c_E = -(rhoE0 + p0).
+template <bool RESID>
+__global__ void __launch_bounds__(128, 4) k_ss_hyb(Grid g, Coef<df64> k, Phys ph, RKStage rk, double c_E,
+                                                   const df64* __restrict__ F, const df64* __restrict__ Gw,
+                                                   const double* __restrict__ W64, const double* __restrict__ Q64,
+                                                   double* __restrict__ out, double* __restrict__ Qs,
+                                                   df64* __restrict__ Fnext, double* __restrict__ W64next) {
+    const int idx = grid_index();
+    if (idx >= g.n) return;
+    const int n = g.n;
+    df64 Rw[5];
+    {
+        const Nbr s = make_nbr(g, idx);
+        fused_residual<df64, true, GlobalAcc<df64>, false>(GlobalAcc<df64>{s, n, F, F + 5 * (size_t)n, Gw}, k, Rw);
+    }
+    // the neighbour offsets again (cheaper than keeping them live through the residual)
+    const Nbr s = make_nbr(g, idx);
+    // -D_j p: 8 (p_{+1} - p_{-1}) + (p_{-2} - p_{+2}), differences exact in binary64
+    const double* Pd = W64 + 3 * (size_t)n;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        double t[4];
+        taps(Pd, s.c, s.o[j], t);
+        const df64 d = scale2(dw_of_f64(t[2] - t[1]), 8.0f) + dw_of_f64(t[0] - t[3]);
+        Rw[1 + j] = fmx(k.cp[j], d, Rw[1 + j]);
+    }
+    // div u in binary64, as the binary64 gradient pass forms D_i u_i
+    double div = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        double t[4];
+        taps(W64 + j * (size_t)n, s.c, s.o[j], t);
+        const double gjj = g.inv12h[j] * delta1_taps(t);
+        div = j == 0 ? gjj : div + gjj;
+    }
+    double R[5];
+    R[0] = fmx(-1.0, div, f64_of_f32(Rw[0].hi)) + f64_of_f32(Rw[0].lo);
+#pragma unroll
+    for (int f = 1; f < 4; ++f) R[f] = f64_of_dw(Rw[f]);
+    R[4] = fmx(c_E, div, f64_of_f32(Rw[4].hi)) + f64_of_f32(Rw[4].lo);
+    if constexpr (RESID) {
+#pragma unroll
+        for (int f = 0; f < 5; ++f) out[f * n + s.c] = R[f];
+    } else {
+        double qn[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+            const double qs = rk.stage == 0 ? Q64[f * n + s.c] : Qs[f * n + s.c];
+            qn[f] = fmx(rk.adt, R[f], qs);
+            out[f * n + s.c] = qn[f];
+            if (rk.stage < 2) Qs[f * n + s.c] = fmx(rk.bdt, R[f], qs);
+        }
+        hyb_prims_point(ph, qn, Fnext, W64next, n, s.c);
+    }
 }
 
 // ------------------------------------------------------------------ BL
@@ -1975,6 +2114,28 @@ cudaError_t launch_ss(const Grid& g, const Coef<T>& k, const Phys& ph, const RKS
         else
             k_ss<T, false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prims_hyb(const Grid& g, const Phys& ph, const double* Q, df64* F, double* W64,
+                             cudaStream_t st) {
+    k_prims_hyb<<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, Q, F, W64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ss_hyb(const Grid& g, const Coef<df64>& k, const Phys& ph, const RKStage& rk, bool resid,
+                          const df64* F, const df64* Gw, const double* W64, const double* Q64, double* out,
+                          double* Qs, df64* Fnext, double* W64next, cudaStream_t st) {
+    Coef<df64> kh = k;  // the mean-state terms enter in binary64 (see k_ss_hyb)
+    kh.c_rho = df64(0.0f, 0.0f);
+    kh.c_E = df64(0.0f, 0.0f);
+    const double c_E = -(ph.rhoE0 + ph.p0);
+    if (resid)
+        k_ss_hyb<true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, kh, ph, rk, c_E, F, Gw, W64, Q64, out, Qs, Fnext,
+                                                             W64next);
+    else
+        k_ss_hyb<false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, kh, ph, rk, c_E, F, Gw, W64, Q64, out, Qs, Fnext,
+                                                              W64next);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ FD_STORE_NONE = 4
 FD_F64 = 0
 FD_F32_ACCDW = 1
 FD_DF64 = 2
+FD_F64_DW = 3
 
 FD_KERNEL_PRIMS = 0
 FD_KERNEL_GRAD = 1
