@@ -174,16 +174,35 @@ __device__ __forceinline__ T delta2_taps(const T t[4], T f0) {
 }
 
 // Double-word forms of the three stencil helpers: the weights 8 and 16 scale
-// exactly (powers of two), 30 through a double-word x binary32 product.
+// exactly (powers of two), 30 through an exact binary32 product.  They use the unnormalised
+// products and sums of fd_df64.cuh (mul_nn, add_nn): the result carries an
+// absolute error of ~2^-47 of the taps' magnitude (times the weights), which is
+// what a stencil difference of double-word taps resolves in any case.
 __device__ __forceinline__ df64 delta1_prod(const df64 a[4], const df64 b[4]) {
-    df64 x = a[2] * b[2] - a[1] * b[1];
-    df64 y = a[3] * b[3] - a[0] * b[0];
-    return scale2(x, 8.0f) - y;
+    const df64 x = sub_nn(mul_nn(a[2], b[2]), mul_nn(a[1], b[1]));
+    const df64 y = sub_nn(mul_nn(a[3], b[3]), mul_nn(a[0], b[0]));
+    return sub_nn(scale2(x, 8.0f), y);
 }
-__device__ __forceinline__ df64 delta1_taps(const df64 t[4]) { return scale2(t[2] - t[1], 8.0f) + (t[0] - t[3]); }
+__device__ __forceinline__ df64 delta1_taps(const df64 t[4]) {
+    return add_nn(scale2(sub_nn(t[2], t[1]), 8.0f), sub_nn(t[0], t[3]));
+}
 __device__ __forceinline__ df64 delta2_taps(const df64 t[4], df64 f0) {
-    return (scale2(t[2] + t[1], 16.0f) - (t[3] + t[0])) - times_fp(f0, 30.0f);
+    const df64 s = sub_nn(scale2(add_nn(t[2], t[1]), 16.0f), add_nn(t[3], t[0]));
+    return sub_nn(s, mul_nn(f0, 30.0f));
 }
+
+// Multiply-accumulate a b + c of the fused residual's long sums: fmx in
+// binary64 and binary32, the unnormalised double-word forms in df64.
+__device__ __forceinline__ double acc(double a, double b, double c) { return fmx(a, b, c); }
+__device__ __forceinline__ float acc(float a, float b, float c) { return fmx(a, b, c); }
+__device__ __forceinline__ df64 acc(df64 a, df64 b, df64 c) { return add_nn(mul_nn(a, b), c); }
+// The same for a sum a + b, and the final renormalisation of a residual.
+__device__ __forceinline__ double sum(double a, double b) { return a + b; }
+__device__ __forceinline__ float sum(float a, float b) { return a + b; }
+__device__ __forceinline__ df64 sum(df64 a, df64 b) { return add_nn(a, b); }
+__device__ __forceinline__ double settle(double a) { return a; }
+__device__ __forceinline__ float settle(float a) { return a; }
+__device__ __forceinline__ df64 settle(df64 a) { return renorm(a); }
 
 // Per-tap weights of the binary64 fused residual (kTapWeighted), where every
 // tap value enters the residual through one fused multiply-add:

@@ -196,6 +196,37 @@ __host__ __device__ __forceinline__ double f64_of_f32(float f) {
 // hi + lo of a double-word rounded to binary64 (one DADD).
 __host__ __device__ __forceinline__ double f64_of_dw(df64 x) { return f64_of_f32(x.hi) + f64_of_f32(x.lo); }
 
+// ---- unnormalised forms for long stencil sums -----------------------------
+// The fused residual sums many products of stencil taps.  There the pair
+// (hi, lo) need not be renormalised after every operation: what the result
+// needs is an absolute error of ~2^-47 of the operands' scale, and that holds
+// for unevaluated sums whose trailing word stays within a few units of the
+// leading word's last place (or, after a cancellation in the leading words,
+// within that of the operands).  These forms drop the renormalisation:
+//   mul_nn(x, y): hi = fl(x.hi y.hi), lo = its exact error (FMA) + x.hi y.lo
+//                 + x.lo y.hi; the term x.lo y.lo (below 2^-46 |x y|) is dropped
+//                 (4 operations, against 10 for DWTimesDW);
+//   add_nn(x, y): TwoSum of the leading words, the trailing words added to its
+//                 error (8 operations, against 11 for SloppyDWPlusDW);
+//   renorm(x):    the pair as a normalised double-word (TwoSum: exact for any
+//                 two binary32 numbers).
+__device__ __forceinline__ df64 mul_nn(df64 x, df64 y) {
+    const float ph = __fmul_rn(x.hi, y.hi);
+    const float e = __fmaf_rn(x.hi, y.hi, -ph);
+    return df64(ph, __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e)));
+}
+__device__ __forceinline__ df64 add_nn(df64 x, df64 y) {
+    const df64 s = two_sum(x.hi, y.hi);
+    return df64(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ df64 sub_nn(df64 x, df64 y) { return add_nn(x, -y); }
+// x times a binary32 y, unnormalised (DWTimesFP without its final FastTwoSum).
+__device__ __forceinline__ df64 mul_nn(df64 x, float y) {
+    const float ph = __fmul_rn(x.hi, y);
+    return df64(ph, __fmaf_rn(x.lo, y, __fmaf_rn(x.hi, y, -ph)));
+}
+__device__ __forceinline__ df64 renorm(df64 x) { return two_sum(x.hi, x.lo); }
+
 // 1 / x: the binary32 reciprocal of the leading word refined by one Newton
 // step r' = r + r (1 - x r) evaluated in double-word arithmetic.
 __device__ __forceinline__ df64 recip(df64 x) {

@@ -461,7 +461,7 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
             for (int j = 0; j < 3; ++j) {
                 T t[4];
                 A.taps(U + i, j, t);
-                vi = fmx(k.vs2[i][j], delta2_taps(t, uc[i]), vi);
+                vi = acc(k.vs2[i][j], delta2_taps(t, uc[i]), vi);
             }
         }
         const int j1 = i == 0 ? 1 : 0, j2 = i == 2 ? 1 : 2;  // the two axes other than i
@@ -471,13 +471,13 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
                 A.pair_taps(i, t);
             else
                 A.grad_pair_taps(j1, j2, i, t);
-            vi = fmx(k.vmix1[i], delta1_taps(t), vi);
+            vi = acc(k.vmix1[i], delta1_taps(t), vi);
         } else {
             bool queued = false;
             if constexpr (Acc::kZQueue) {
                 if (i == 2) {  // D_z(D_x u_x + D_y u_y) from the queued planes
                     const T t[4] = {A.zq[0], A.zq[1], A.zq[3], A.zq[4]};
-                    vi = fmx(k.vmix1[2], delta1_taps(t), vi);
+                    vi = acc(k.vmix1[2], delta1_taps(t), vi);
                     queued = true;
                 }
             }
@@ -491,7 +491,7 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
                     A.taps_shifted(U + kk, kk, i, a, u4);
                     t[a] = delta1_taps(u4);
                 }
-                vi = fmx(k.vmix[i][kk], delta1_taps(t), vi);
+                vi = acc(k.vmix[i][kk], delta1_taps(t), vi);
             }
         }
         return vi;
@@ -553,10 +553,10 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
             for (int f = 0; f < 5; ++f) {
                 T qt[4];
                 A.taps(f, j, qt);
-                R[f] = fmx(k.c1[j], delta1_prod(qt, st), R[f]);
+                R[f] = acc(k.c1[j], delta1_prod(qt, st), R[f]);
             }
-            if constexpr (PGRAD) R[1 + j] = fmx(k.cp[j], delta1_taps(pt), R[1 + j]);
-            R[4] = fmx(k.cp[j], delta1_prod(pt, ut), R[4]);
+            if constexpr (PGRAD) R[1 + j] = acc(k.cp[j], delta1_taps(pt), R[1 + j]);
+            R[4] = acc(k.cp[j], delta1_prod(pt, ut), R[4]);
         }
     }
 
@@ -580,7 +580,7 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
             for (int j = 0; j < 3; ++j) {
                 T t[4];
                 A.taps(TT, j, t);
-                R[4] = fmx(k.ks2[j], delta2_taps(t, T0), R[4]);
+                R[4] = acc(k.ks2[j], delta2_taps(t, T0), R[4]);
             }
         }
     }
@@ -593,31 +593,33 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const T vi = viscous(i);
-            R[1 + i] += vi;
-            R[4] = fmx(uc[i], vi, R[4]);
+            R[1 + i] = sum(R[1 + i], vi);
+            R[4] = acc(uc[i], vi, R[4]);
         }
     }
 
     // viscous dissipation tau_ij D_j u_i
     {
         T d = G[0][0] * G[0][0];
-        d = fmx(G[1][1], G[1][1], d);
-        d = fmx(G[2][2], G[2][2], d);
+        d = acc(G[1][1], G[1][1], d);
+        d = acc(G[2][2], G[2][2], d);
         T s01 = G[0][1] + G[1][0], s02 = G[0][2] + G[2][0], s12 = G[1][2] + G[2][1];
         T o = s01 * s01;
-        o = fmx(s02, s02, o);
-        o = fmx(s12, s12, o);
-        T diss = fmx(T(2), d, o);
-        diss = fmx(T(-2.0 / 3.0) * div, div, diss);
-        R[4] = fmx(k.nu, diss, R[4]);
+        o = acc(s02, s02, o);
+        o = acc(s12, s12, o);
+        T diss = acc(T(2), d, o);
+        diss = acc(T(-2.0 / 3.0) * div, div, diss);
+        R[4] = acc(k.nu, diss, R[4]);
     }
     // the perturbation form's mean-state terms (binary64 fields are not shifted)
     if constexpr (!std::is_same<T, double>::value) {
         if (k.c_rho != T(0)) {
-            R[0] = fmx(k.c_rho, div, R[0]);
-            R[4] = fmx(k.c_E, div, R[4]);
+            R[0] = acc(k.c_rho, div, R[0]);
+            R[4] = acc(k.c_E, div, R[4]);
         }
     }
+#pragma unroll
+    for (int f = 0; f < 5; ++f) R[f] = settle(R[f]);
 }
 
 // ------------------------------------------------------------------ RA
