@@ -282,7 +282,9 @@ const char* fd_batch_last_error(const fd_batch* b);
  * solves, advances every active solve (all of them in the same launches,
  * grouped by dtype and family), and retires the solves that reached their
  * step count: their kinetic energy and enstrophy become results for
- * fd_server_poll and their memory returns to the arena.  Ticks are
+ * fd_server_poll, and their final state stays readable through
+ * fd_server_get_state until the first tick after their result was polled,
+ * which returns their memory to the arena.  Ticks are
  * time-sliced: a solve advances by an odd number of RK3 steps per tick, one
  * for the solve with the dearest step of the active set and, for a cheaper
  * solve, as many as fit in that step's time (at most 31, never past its
@@ -336,8 +338,18 @@ int fd_server_cancel(fd_server* s, long long tag);
  * tick.  Errors: FD_ECUDA. */
 int fd_server_tick(fd_server* s, int* active_out);
 
-/* Move up to max finished results into out[]; *n_out receives the count. */
+/* Move up to max finished results into out[]; *n_out receives the count.
+ * The next fd_server_tick releases the polled solves' device memory (and
+ * states). */
 int fd_server_poll(fd_server* s, fd_result* out, int max, int* n_out);
+
+/* Copy the final state of a finished solve (layout and rules of fd_get_state:
+ * 5*nx*ny*nz doubles, host or device dst, binary64 also for FD_F32_ACCDW
+ * requests); valid from the tick that finished it until the first tick after
+ * its result was polled.  If several kept solves share the tag, the one that
+ * finished first.  Synchronises the server's stream.  Errors: FD_EINVAL (no
+ * such solve, wrong n_elems, NULL), FD_ECUDA. */
+int fd_server_get_state(fd_server* s, long long tag, double* dst, size_t n_elems, int dst_is_device);
 
 int fd_server_get_stats(const fd_server* s, fd_server_stats* out);
 
@@ -368,8 +380,9 @@ const char* fd_server_last_error(const fd_server* s);
  * the library until the process exits).  All calls share it and it keeps the last call's contents, which
  * no call reads before overwriting; two calls whose work overlaps on the GPU
  * (different streams, or host threads racing on one device) race on it and
- * must be ordered by the caller.  The first call on each device looks up the
- * scratch address with cudaGetSymbolAddress; make that first call before any
+ * must be ordered by the caller.  The first call on each device (and the first
+ * after that device's context was replaced, e.g. by cudaDeviceReset) looks up
+ * the scratch address with cudaGetSymbolAddress; make that call before any
  * stream capture begins.
  *
  * Errors: FD_EINVAL for a NULL pointer, an axis below 5 points, more than
@@ -392,6 +405,16 @@ int fd_residual_noalloc(const double* Q, double* R, int nx, int ny, int nz, doub
  * paper has no counterpart.  Errors: FD_EINVAL (err_word NULL, or TMA staging
  * turned off by FDGB300_NO_TMA=1), FD_ENOMEM, FD_ECUDA. */
 int fd_selftest_wait_timeout(int* err_word);
+
+/* ---- measured binary64 rate -----------------------------------------------
+ * The denominator of the binary64 kernels' roofline: runs a loop of
+ * independent binary64 FMA chains over 8 blocks of 256 threads per SM of the
+ * current device (one untimed launch, then three timed ones on a private
+ * stream) and stores the rate in *flops_per_s (two flops per FMA).  scratch is
+ * caller-owned device memory of at least SMs * 2048 doubles (16 KB per SM)
+ * that the kernel overwrites.  The paper has no counterpart.  Synchronises the
+ * private stream.  Errors: FD_EINVAL (NULL, scratch too small), FD_ECUDA. */
+int fd_fp64_peak(double* flops_per_s, void* scratch, size_t scratch_bytes);
 
 /* Free every device buffer of the handle and the handle itself.  NULL is a
  * no-op.  Synchronises the handle's stream first. */

@@ -177,8 +177,17 @@ class Server:
         return native.fd_server_tick(self.s)
 
     def poll(self):
+        """Finished results (the next tick releases each polled solve's memory and state)."""
         return [dict(tag=r.tag, status=r.status, steps=r.steps_done, ke=r.ke, enstrophy=r.enstrophy)
                 for r in native.fd_server_poll(self.s)]
+
+    def state(self, tag, shape):
+        """Final state [5][nz][ny][nx] of a finished solve, until the first tick after its
+        result was polled (shape = its grid as given in the request: n or (nx, ny, nz))."""
+        nx, ny, nz = (shape, shape, shape) if isinstance(shape, int) else tuple(shape)
+        out = np.empty((5, nz, ny, nx), dtype=np.float64)
+        native.fd_server_get_state(self.s, int(tag), out)
+        return out
 
     def stats(self):
         st = native.fd_server_get_stats(self.s)
@@ -266,6 +275,22 @@ class Solver:
     def diagnostics(self):
         """(kinetic energy, enstrophy) of the current state."""
         return fd_diagnostics(self.h)
+
+    def history(self, steps_per_sample: int, samples: int):
+        """Kinetic energy and enstrophy every steps_per_sample RK3 steps (Section 3,
+        Fig. 3): arrays t, ke, enstrophy of samples + 1 entries, starting with the
+        current state at t = 0 (t in units of this solver's time step dt)."""
+        t, ke, en = [0.0], [], []
+        k, e = self.diagnostics()
+        ke.append(k)
+        en.append(e)
+        for i in range(samples):
+            self.step(steps_per_sample)
+            k, e = self.diagnostics()
+            t.append((i + 1) * steps_per_sample * self.dt)
+            ke.append(k)
+            en.append(e)
+        return np.array(t), np.array(ke), np.array(en)
 
     def check_finite(self) -> bool:
         return fd_check_finite(self.h) == FD_OK

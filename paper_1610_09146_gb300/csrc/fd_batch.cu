@@ -223,10 +223,9 @@ cudaError_t build_graphs(fd_batch* b) {
         cudaError_t le = b->dtype == FD_F64 ? enqueue_step<double>(b, p, b->cap[0], b->cap[1])
                                             : enqueue_step<float>(b, p, b->cap[0], b->cap[1]);
         e = cudaStreamEndCapture(b->cap[0], &g);
+        if (le == cudaSuccess && e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[p], g, 0);
+        if (g) cudaGraphDestroy(g);
         if (le != cudaSuccess) return le;
-        if (e != cudaSuccess) return e;
-        e = cudaGraphInstantiate(&b->exec[p], g, 0);
-        cudaGraphDestroy(g);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

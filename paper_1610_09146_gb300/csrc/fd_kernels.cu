@@ -1617,16 +1617,42 @@ __global__ void __launch_bounds__(kRsPoints * 5) k_rs(Grid g, Phys ph, RKStage r
 // runs the same per-point code as the single-instance kernels, so a batched
 // instance evolves bitwise as it would alone.  `parity` selects Q[parity] /
 // W[parity] as the stage's input (all instances of a batch flip together).
+// Launch shape of the batched global-memory fused kernel: binary64 store-some
+// 128 threads with registers capped for three blocks (12 warps per SM; the
+// FP64 pipe needs the warps: 8 warps of 256-thread blocks gave 7.1 solves/s
+// on the 64-instance ensemble, 16 warps with 100 bytes of spills 11.9, 12
+// warps 12.0), binary64 recompute-all 128 threads without a cap (its residual
+// needs ~170 registers), binary32 256 threads, two blocks per SM.
+template <class T>
+constexpr int kBatchFusedThreads = sizeof(T) == sizeof(double) ? 128 : 256;
 template <class T, bool STORED_G>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_batch_fused(const BatchInst<T>* __restrict__ insts,
-                                                     const BatchTile* __restrict__ tiles, int ntiles, int stage,
-                                                     int parity) {
+constexpr int kBatchFusedMinBlocks = sizeof(T) == sizeof(double) ? (STORED_G ? 3 : 1) : 2;
+
+// The instance record of a work item, copied to shared memory by the whole
+// block in 16-byte pieces, and only when the item belongs to another instance
+// than the block's previous one (a block's items are mostly of one instance).
+template <class T>
+__device__ __forceinline__ void stage_inst(BatchInst<T>& I, const BatchInst<T>* __restrict__ insts, int inst,
+                                           int& cur) {
+    static_assert(sizeof(BatchInst<T>) % 16 == 0, "the record is copied in 16-byte pieces");
+    if (inst == cur) return;
+    __syncthreads();  // every thread is done with the previous record
+    const int4* src = reinterpret_cast<const int4*>(insts + inst);
+    int4* dst = reinterpret_cast<int4*>(&I);
+    for (int i = threadIdx.x; i < (int)(sizeof(BatchInst<T>) / 16); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    cur = inst;
+}
+
+template <class T, bool STORED_G>
+__global__ void __launch_bounds__(kBatchFusedThreads<T>, kBatchFusedMinBlocks<T, STORED_G>)
+    k_batch_fused(const BatchInst<T>* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles, int stage,
+                  int parity) {
     __shared__ BatchInst<T> I;
+    int cur = -1;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const BatchTile tl = tiles[t];
-        __syncthreads();
-        if (threadIdx.x == 0) I = insts[tl.inst];
-        __syncthreads();
+        stage_inst(I, insts, tl.inst, cur);
         const int n = I.g.n;
         const state_t<T>* Qin = I.Q[parity];
         state_t<T>* Qout = I.Q[1 - parity];
@@ -1652,11 +1678,10 @@ __global__ void __launch_bounds__(kTX* kTY, sizeof(T) == 4 ? 2 : 1)
                      int stage, int parity) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BatchInst<T> I;
+    int cur = -1;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const BatchTile tl = tiles[t];
-        __syncthreads();
-        if (threadIdx.x == 0) I = insts[tl.inst];
-        __syncthreads();
+        stage_inst(I, insts, tl.inst, cur);
         const int ntx = (I.g.nx + kTX - 1) / kTX, nty = (I.g.ny + kTY - 1) / kTY;
         const int zt = tl.start / (ntx * nty), r = tl.start % (ntx * nty);
         const int n = I.g.n;
@@ -1674,11 +1699,10 @@ template <class T>
 __global__ void __launch_bounds__(256) k_batch_grad(const BatchInst<T>* __restrict__ insts,
                                                     const BatchTile* __restrict__ tiles, int ntiles, int parity) {
     __shared__ BatchInst<T> I;
+    int cur = -1;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const BatchTile tl = tiles[t];
-        __syncthreads();
-        if (threadIdx.x == 0) I = insts[tl.inst];
-        __syncthreads();
+        stage_inst(I, insts, tl.inst, cur);
         const int n = I.g.n;
         const T* Wc = I.W[parity];
         const T* Wf = sizeof(T) == sizeof(double) ? Wc : Wc + 5 * (size_t)n;
@@ -1703,11 +1727,10 @@ template <class T>
 __global__ void __launch_bounds__(256) k_batch_prims(const BatchInst<T>* __restrict__ insts,
                                                      const BatchTile* __restrict__ tiles, int ntiles, int parity) {
     __shared__ BatchInst<T> I;
+    int cur = -1;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const BatchTile tl = tiles[t];
-        __syncthreads();
-        if (threadIdx.x == 0) I = insts[tl.inst];
-        __syncthreads();
+        stage_inst(I, insts, tl.inst, cur);
         const int n = I.g.n;
         for (int p = threadIdx.x; p < tl.count; p += blockDim.x) {
             const int c = tl.start + p;
@@ -1765,9 +1788,9 @@ int batch_blocks_per_sm(bool fused, bool stored_g) {
     if (!fused)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_grad<T>, 256, 0);
     else if (stored_g)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_fused<T, true>, 256, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_fused<T, true>, kBatchFusedThreads<T>, 0);
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_fused<T, false>, 256, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_fused<T, false>, kBatchFusedThreads<T>, 0);
     return e == cudaSuccess && b > 0 ? b : 1;
 }
 
@@ -1792,9 +1815,9 @@ cudaError_t launch_batch_fused(const BatchInst<T>* insts, const BatchTile* tiles
                                int stage, int parity, int grid, cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
     if (stored_g)
-        k_batch_fused<T, true><<<grid, 256, 0, st>>>(insts, tiles, ntiles, stage, parity);
+        k_batch_fused<T, true><<<grid, kBatchFusedThreads<T>, 0, st>>>(insts, tiles, ntiles, stage, parity);
     else
-        k_batch_fused<T, false><<<grid, 256, 0, st>>>(insts, tiles, ntiles, stage, parity);
+        k_batch_fused<T, false><<<grid, kBatchFusedThreads<T>, 0, st>>>(insts, tiles, ntiles, stage, parity);
     return cudaGetLastError();
 }
 

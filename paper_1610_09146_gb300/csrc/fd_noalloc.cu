@@ -14,6 +14,7 @@
 // of at most FD_NOALLOC_MAX_POINTS points.  It is a file-scope __device__
 // array, so every GPU that loads the library keeps it (17 x 262144 x 8 bytes
 // = 35.7 MB) until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -29,23 +30,47 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchArrays * (size_t)FD_NOALLOC_MAX_POINTS];
 
-// Device address of g_noalloc_scratch per device, looked up once per device
-// (with that device current).  In host code the symbol's name is only a
-// host-side stand-in, never a device address.
+// Device address of g_noalloc_scratch per device, looked up with that device
+// current.  In host code the symbol's name is only a host-side stand-in, never
+// a device address.  The address belongs to the context the module was loaded
+// into: each cached address is kept beside that context (cuCtxGetCurrent,
+// through the runtime's driver entry point) and looked up again when the
+// device's current context is a different one, e.g. after cudaDeviceReset.
 std::mutex g_setup_mutex;
 double* g_scratch_ptr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+cudaError_t current_context(CUcontext* ctx) {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    static GetCurrent get = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<GetCurrent>(p);
+    }();
+    if (!get) return cudaErrorNotSupported;
+    return get(ctx) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
 
 cudaError_t scratch_for_current_device(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    CUcontext ctx = nullptr;
+    if ((e = current_context(&ctx)) != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (!ctx || !g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
+        // the lookup also makes the device's primary context current when no
+        // context is yet, so the context is read again after it
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
+        if ((e = current_context(&ctx)) != cudaSuccess) return e;
         g_scratch_ptr[dev] = static_cast<double*>(p);
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;

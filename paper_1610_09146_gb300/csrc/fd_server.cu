@@ -12,7 +12,9 @@
 // admitted solve writes its initial state into Q[parity], so every tick runs
 // one RK3 step of every active solve with the batched kernels, one group per
 // (dtype, family).  A tick ends synchronised; finished solves are retired
-// with their diagnostics and their memory returns to the arena.
+// with their diagnostics; their state stays readable (fd_server_get_state)
+// until the first tick after their result was polled, which returns their
+// memory to the arena.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -147,6 +149,18 @@ struct Active {
     int k = 1;          // steps per tick (odd; see plan_steps)
 };
 
+// A finished solve: its arena block (and so its final state, in Q[parity])
+// is kept for fd_server_get_state until the first tick after its result was
+// polled.
+struct Finished {
+    fd_request r;
+    Layout L;
+    size_t off;
+    int n;
+    int parity;
+    bool polled = false;
+};
+
 // Time slicing.  A tick advances every active solve by an odd number of steps
 // k: the dearest step of the active set gets one, and a cheaper solve gets as
 // many as fit in that step's time (at most kMaxSteps, never past its request),
@@ -185,6 +199,7 @@ struct fd_server {
     std::deque<fd_request> queue;
     std::vector<Active> active;
     std::vector<fd_result> done;
+    std::vector<Finished> finished;  // retired solves whose state is still kept
     bool dirty = true;
     int parity = 0;
     long long submitted = 0, completed = 0, ticks = 0;
@@ -483,6 +498,15 @@ int fd_server_tick(fd_server* s, int* active_out) {
     if (!s) return fail_global(FD_EINVAL, "fd_server_tick: NULL server");
     s->ticks++;
     cudaError_t e = cudaSuccess;
+    // 0. finished solves whose results were polled since the last tick free their blocks
+    for (size_t i = 0; i < s->finished.size();) {
+        if (s->finished[i].polled) {
+            s->arena.release(s->finished[i].off, s->finished[i].L.total);
+            s->finished.erase(s->finished.begin() + i);
+        } else {
+            ++i;
+        }
+    }
     // 1. cancelled active solves leave without diagnostics
     for (size_t i = 0; i < s->active.size();) {
         Active& a = s->active[i];
@@ -602,7 +626,7 @@ int fd_server_tick(fd_server* s, int* active_out) {
         double ke = res[2 * k], en = res[2 * k + 1];
         int st = std::isfinite(ke) && std::isfinite(en) ? FD_OK : FD_EUNSTABLE;
         s->done.push_back({a.r.tag, st, a.done, ke, en});
-        s->arena.release(a.off, a.L.total);
+        s->finished.push_back({a.r, a.L, a.off, a.n, s->parity, false});
         s->active.erase(s->active.begin() + fin[k]);
         s->completed++;
         s->dirty = true;
@@ -614,9 +638,47 @@ int fd_server_poll(fd_server* s, fd_result* out, int max, int* n_out) {
     if (!s) return fail_global(FD_EINVAL, "fd_server_poll: NULL server");
     if (max < 0 || (max > 0 && !out)) return s->fail(FD_EINVAL, "fd_server_poll: bad output buffer");
     int n = std::min<int>(max, (int)s->done.size());
-    for (int i = 0; i < n; ++i) out[i] = s->done[i];
+    for (int i = 0; i < n; ++i) {
+        out[i] = s->done[i];
+        // the solve's block returns to the arena at the next tick
+        for (auto& f : s->finished)
+            if (f.r.tag == out[i].tag && !f.polled) {
+                f.polled = true;
+                break;
+            }
+    }
     s->done.erase(s->done.begin(), s->done.begin() + n);
     if (n_out) *n_out = n;
+    return FD_OK;
+}
+
+int fd_server_get_state(fd_server* s, long long tag, double* dst, size_t n_elems, int dst_is_device) {
+    if (!s) return fail_global(FD_EINVAL, "fd_server_get_state: NULL server");
+    if (!dst) return s->fail(FD_EINVAL, "fd_server_get_state: dst is NULL");
+    const Finished* f = nullptr;
+    for (const auto& x : s->finished)
+        if (x.r.tag == tag) {
+            f = &x;
+            break;
+        }
+    if (!f) return s->fail(FD_EINVAL, "fd_server_get_state: no kept state of a finished solve with tag %lld", tag);
+    if (n_elems != 5 * (size_t)f->n)
+        return s->fail(FD_EINVAL, "fd_server_get_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)f->n);
+    char* b = s->base() + f->off;
+    const double* src = reinterpret_cast<const double*>(b + (f->parity ? f->L.q1 : f->L.q0));
+    cudaError_t e = cudaSuccess;
+    if (f->r.dtype != FD_F64) {  // shifted double-word state to binary64 through the solve's dead Qs
+        double* tmp = reinterpret_cast<double*>(b + f->L.qs);
+        const fd::Phys ph = fd::make_phys(f->r.Re, f->r.Mach, f->r.Pr, f->r.gamma);
+        e = fd::launch_from_df64(reinterpret_cast<const fd::df64*>(src), tmp, f->n,
+                                 fd::Shift5{{1.0, 0.0, 0.0, 0.0, ph.rhoE0}}, s->stream);
+        src = tmp;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dst, src, n_elems * sizeof(double),
+                            dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "fd_server_get_state");
     return FD_OK;
 }
 

@@ -133,6 +133,8 @@ _SIGS = {
     "fd_server_cancel": (ctypes.c_int, [_vp, ctypes.c_longlong]),
     "fd_server_tick": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "fd_server_poll": (ctypes.c_int, [_vp, ctypes.POINTER(FdResult), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "fd_fp64_peak": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), _vp, ctypes.c_size_t]),
+    "fd_server_get_state": (ctypes.c_int, [_vp, ctypes.c_longlong, _vp, ctypes.c_size_t, ctypes.c_int]),
     "fd_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(FdServerStats)]),
     "fd_server_destroy": (ctypes.c_int, [_vp]),
     "fd_server_last_error": (ctypes.c_char_p, [_vp]),
@@ -384,6 +386,15 @@ def fd_server_poll(srv, max_results=1024):
     return [buf[i] for i in range(n.value)]
 
 
+def fd_server_get_state(srv, tag, dst, n_elems=None, dst_is_device=None):
+    """Final state of a finished, unpolled solve into dst (numpy float64 array, or a device
+    pointer with n_elems and dst_is_device=1)."""
+    if isinstance(dst, np.ndarray):
+        return _scheck(load().fd_server_get_state(srv, tag, _hostptr(dst), dst.size, 0), srv)
+    return _scheck(load().fd_server_get_state(srv, tag, dst, n_elems, 1 if dst_is_device is None else
+                                              int(dst_is_device)), srv)
+
+
 def fd_server_get_stats(srv):
     st = FdServerStats()
     _scheck(load().fd_server_get_stats(srv, ctypes.byref(st)), srv)
@@ -396,3 +407,15 @@ def fd_server_destroy(srv):
 
 def fd_server_last_error(srv=None):
     return load().fd_server_last_error(srv).decode()
+
+
+def fd_fp64_peak():
+    """Measured binary64 FMA rate of the current device in flop/s (fd_fp64_peak)."""
+    import torch
+    scratch = torch.empty(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+                          * 2048, dtype=torch.float64, device="cuda")
+    out = ctypes.c_double()
+    rc = load().fd_fp64_peak(ctypes.byref(out), scratch.data_ptr(), scratch.numel() * 8)
+    if rc != FD_OK:
+        raise FdError(rc, "fd_fp64_peak failed")
+    return out.value

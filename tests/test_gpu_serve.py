@@ -3,9 +3,14 @@
 Requests that arrive while others are active join the running batch (same
 launches), so a solve's result must not depend on its neighbours: the server's
 kinetic energy and enstrophy of every solve equal, bit for bit, those of the same
-solve run alone through fd_create / fd_step / fd_diagnostics.
+solve run alone through fd_create / fd_step / fd_diagnostics; the final states of
+binary64 solves served in a mix match the FP64 oracle (relative L-inf 1e-12), and
+those of binary32 solves equal the same solve alone over the whole state.
 """
+import numpy as np
 import pytest
+
+import oracle as O
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -76,6 +81,8 @@ def test_admission_respects_the_arena():
         assert srv.tick() == 1          # tag 11 admitted now
         srv.tick()
         assert [r["tag"] for r in srv.poll()] == [11]
+        assert srv.stats()["arena_used"] > 0   # 11's state is kept until the next tick
+        srv.tick()
         assert srv.stats()["arena_used"] == 0
 
 
@@ -126,3 +133,49 @@ def test_tma_and_thread_staged_binary32_solves_share_a_tick():
         ke, en = alone(r)
         assert got[r["tag"]]["status"] == fd.FD_OK
         assert got[r["tag"]]["ke"] == ke and got[r["tag"]]["enstrophy"] == en, r["tag"]
+
+
+def test_served_states_match_the_oracle_and_alone():
+    """Solves join and leave a running mix; each final state is read through
+    fd_server_get_state after its result is polled (before the next tick)."""
+    reqs = [
+        dict(tag=31, n=(12, 10, 14), steps=4, Re=800.0, Mach=0.2, dtype="f64", algorithm="store_some", dt=1e-3),
+        dict(tag=32, n=16, steps=6, Re=1600.0, Mach=0.1, dtype="f64", algorithm="recompute_all", dt=1e-3),
+        dict(tag=33, n=(16, 12, 20), steps=5, Re=2000.0, Mach=0.3, dtype="f32", algorithm="recompute_all", dt=1e-3),
+        dict(tag=34, n=(10, 14, 12), steps=3, Re=1200.0, Mach=0.25, dtype="f32", algorithm="store_some", dt=2e-3),
+        dict(tag=35, n=(20, 8, 16), steps=7, Re=3000.0, Mach=0.15, dtype="f64", algorithm="store_some", dt=1e-3),
+    ]
+    by_tag = {r["tag"]: r for r in reqs}
+    states, results = {}, {}
+    with fd.Server(1 << 30, max_active=8) as srv:
+        srv.submit(reqs[0])
+        srv.submit(reqs[2])
+        srv.tick()
+        srv.submit(reqs[1])
+        srv.tick()
+        srv.submit(reqs[3])
+        srv.submit(reqs[4])
+        for _ in range(40):
+            srv.tick()
+            for r in srv.poll():
+                results[r["tag"]] = r
+                states[r["tag"]] = srv.state(r["tag"], by_tag[r["tag"]]["n"])
+            if len(results) == len(reqs):
+                break
+        with pytest.raises(fd.FdError) as e:
+            srv.state(999, 8)
+        assert e.value.code == fd.FD_EINVAL
+    assert set(states) == set(by_tag)
+    for tag, r in by_tag.items():
+        assert results[tag]["status"] == fd.FD_OK and results[tag]["steps"] == r["steps"]
+        Q = states[tag]
+        if r["dtype"] == "f64":
+            n = r["n"]
+            nx, ny, nz = (n, n, n) if isinstance(n, int) else n
+            ref = O.run(O.tgv_ic(nx, ny, nz, 1.4, r["Mach"]), r["steps"], dt=r["dt"], Re=r["Re"], Mach=r["Mach"])
+            err = max(np.abs(Q[v] - ref[v]).max() / np.abs(ref[v]).max() for v in range(5))
+            assert err <= 1e-12, tag
+        with fd.Solver(r["n"], Re=r["Re"], Mach=r["Mach"], dt=r["dt"], algorithm=r["algorithm"],
+                       dtype=r["dtype"]) as s:
+            s.step(r["steps"])
+            assert np.array_equal(s.state(), Q), tag

@@ -1,5 +1,6 @@
 """fd_residual_noalloc: the store-some residual without any allocation, checked
-against fd_residual (which works through a handle) on the same states.
+against fd_residual (which works through a handle) and against the oracle's
+residual on the same states.
 
 The entry point is for callers that cannot allocate device memory when they need
 R(Q) (an external integrator inside a stream capture or a fixed memory budget);
@@ -10,6 +11,7 @@ the shared scratch by one call can leak into the next.
 import numpy as np
 import pytest
 
+import oracle as O
 from tests.inputs import rough_state, smooth_state
 
 torch = pytest.importorskip("torch")
@@ -60,6 +62,8 @@ def test_two_calls_in_a_row_match_fd_residual():
     Rb = noalloc_residual(Qb, stream)
     assert rel_linf(Ra, Ra_ref) <= 1e-12
     assert rel_linf(Rb, Rb_ref) <= 1e-12
+    assert rel_linf(Ra, O.residual(Qa, Re=RE, Mach=MACH, Pr=PR, gamma=GAMMA)) <= 1e-12
+    assert rel_linf(Rb, O.residual(Qb, Re=RE, Mach=MACH, Pr=PR, gamma=GAMMA)) <= 1e-12
 
 
 def test_largest_allowed_grid_then_a_small_one():
@@ -71,6 +75,8 @@ def test_largest_allowed_grid_then_a_small_one():
     Rb = noalloc_residual(Qb, stream)
     assert rel_linf(Ra, reference_residual(Qa)) <= 1e-12
     assert rel_linf(Rb, reference_residual(Qb)) <= 1e-12
+    assert rel_linf(Ra, O.residual(Qa, Re=RE, Mach=MACH, Pr=PR, gamma=GAMMA)) <= 1e-12
+    assert rel_linf(Rb, O.residual(Qb, Re=RE, Mach=MACH, Pr=PR, gamma=GAMMA)) <= 1e-12
 
 
 def test_sizes_beyond_the_scratch_are_rejected():
