@@ -7,16 +7,20 @@ Sandham, arXiv 1610.09146: Sections 2-4; the paper times this loop in Table 1).
 
 A "step" is one full RK3 step (three stages: primitives, derivatives, residual, update)
 over all 256^3 points; the metric is point-updates/s = points x steps / seconds.  Each
-family (store-all BL, store-some SS, recompute-all RA) is timed separately; the line's
-`value` is the fastest one.  Inputs: the analytic Taylor-Green initial condition
+family (store-all BL, store-some SS, recompute-all RA, recompute-some RS, store-none SN)
+is timed separately in binary64, and store-some also in the mixed binary64 / double-word
+form (dtype f64dw, held to the same 1e-12 parity with the binary64 oracle); the line's
+`value` is the fastest of these.  Beside it: the df64 and binary32 families, a compact
+record of the 64-instance batched ensemble and of the serving stream (first 40 requests),
+and the end-to-end rate through the C ABI with host buffers (two solvers overlapping
+their copies, and one solver alone).  Inputs: the analytic Taylor-Green initial condition
 (synthetic, no dataset), 671 MB of state per buffer, far above the 129 MB L2, so no
 flush is needed between steps.  Under torchrun (N > 1) every rank advances its own
 256^3 instance (replicas; the single-instance path has no exchange step) and `value`
 is the sum over ranks divided by the slowest rank's time.
 
 `--impl reference` times the FP64 CPU oracle (the checker of the CUDA path) on the
-host cores, one RK3 step of a 256 x 256 x 8 periodic slab per step (same per-point
-arithmetic and grid spacing as the 256^3 grid).
+host cores, one RK3 step of the full 256^3 grid per step (about 7 s each on 16 cores).
 """
 from __future__ import annotations
 
@@ -46,9 +50,14 @@ PAPER_256_SECONDS = {"store_all": 1561.52, "recompute_all": 765.42, "recompute_s
                      "store_some": 685.25}
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# binary64 arithmetic peak of GB300: 152 SMs x 2 FP64 FMA lanes per SM per clock x 2 flop
-# x 2.07 GHz maximum SM clock = 1.26 TFLOP/s (our DFMA-loop probe measured 1.20).
+# binary64 arithmetic peak of GB300, nominal: 152 SMs x 2 FP64 FMA lanes per SM per clock
+# x 2 flop x 2.07 GHz maximum SM clock = 1.26 TFLOP/s.  The line uses the rate measured in
+# the same run (fd_fp64_peak: a binary64 FMA loop) and falls back to this one.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Issue-slot peak: 152 SMs x 4 schedulers x one 32-thread instruction per clock x 2.07 GHz,
+# in thread instructions per second; the roof of the mixed binary64 / double-word kernel,
+# whose binary32 and binary64 work runs on two pipes that share these slots.
+ISSUE_PEAK_TINST = 152 * 4 * 32 * 2.07e9 / 1e12
 HBM_FALLBACK_GBS = 6800.0
 
 # Algorithmic cost per grid point of one launch, by (dtype, family, kernel class):
@@ -102,7 +111,19 @@ COST = {
     ("df64", "store_all", "deriv2"): (114, 200, 0),
     ("df64", "store_all", "products"): (18, 216, 0),
     ("df64", "*", "prims"): (14, 120, 0),
+    # mixed binary64 / double-word store-some (dtype f64dw): flops are the binary64 algorithm's
+    # (the binary64 SS kernel's); bytes per point read F (10 double-words) + W64 (u, v, w, p) +
+    # G (9 double-words) + the saved register, write the state, the saved register (stages 0
+    # and 1), F and W64 of the next stage; binary64 instructions counted from the source
+    ("f64dw", "store_some", "fused"): (401.7, 402.7, 51.3),
+    ("f64dw", "store_some", "grad"): (45, 96, 0),
+    ("f64dw", "*", "prims"): (14, 200, 17),
 }
+# Thread instructions per point of one launch (all pipes): ncu's smsp__thread_inst_executed of
+# the kernel at 160^3, mean of stages 0-2 (16.04, 16.16, 16.17e9 / 4.096e6 points); the
+# issue-slot cost of the mixed kernel.  Its binary64 instructions (DADD 23, DFMA 22/22/17,
+# DMUL 8 per point) give the 51.3 of the cost table.
+ISSUE_COST = {("f64dw", "store_some", "fused"): 3936.0}
 # FP64 pipe issue peak: 2 instructions per SM per clock.
 FP64_PEAK_INSTR = 152 * 2 * 2.07e9
 
@@ -224,18 +245,31 @@ def time_family(fd, torch, alg, dtype, n, steps, warmup, stream, barrier, clocks
     return s, ms, kern, finite, (ke, ens)
 
 
-def roofline_of(dtype, alg, kern, n, hbm_peak, hbm_src):
-    """Roofline entry of the kernel with the largest share of the step."""
+def roofline_of(dtype, alg, kern, n, hbm_peak, hbm_src, fp64_peak=None):
+    """Roofline entry of the kernel with the largest share of the step.  fp64_peak: the
+    measured binary64 rate in TFLOP/s (None: the nominal one)."""
     name, k = max(kern.items(), key=lambda kv: kv[1]["ms_total"])
     flops_pt, bytes_pt, instr_pt = cost_of(dtype, alg, name)
     sec = k["ms_avg"] / 1e3
     gbs = bytes_pt * n / sec / 1e9
     tflops = flops_pt * n / sec / 1e12
-    if dtype in ("f64", "df64"):
+    p64 = fp64_peak or FP64_PEAK_TFLOPS
+    p64_src = ("measured in this run (fd_fp64_peak: binary64 FMA loop)" if fp64_peak
+               else "FP64 nominal: 152 SMs x 4 flop/clk x 2.07 GHz")
+    if dtype == "f64dw" and (dtype, alg, name) in ISSUE_COST:
+        tinst = ISSUE_COST[(dtype, alg, name)] * n / sec / 1e12
+        entry = {"kernel": f"{SHORT[alg]}:{name}", "bound": "alu", "achieved": round(tinst, 3),
+                 "peak": round(ISSUE_PEAK_TINST, 3), "unit": "Tinst/s", "frac": round(tinst / ISSUE_PEAK_TINST, 4),
+                 "peak_source": "issue slots: 152 SMs x 4 schedulers x 32 threads x 2.07 GHz",
+                 "binary64_equivalent_tflops": round(tflops, 4), "vs_fp64_peak": round(tflops / p64, 4),
+                 "fp64_peak_tflops": round(p64, 4), "fp64_peak_source": p64_src,
+                 "fp64_pipe_frac": round(instr_pt * n / sec / (p64 * 1e12 / 2), 4),
+                 "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4)}
+    elif dtype in ("f64", "df64", "f64dw"):
         entry = {"kernel": f"{SHORT[alg]}:{name}", "bound": "alu", "achieved": round(tflops, 4),
-                 "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
-                 "peak_source": "FP64 nominal: 152 SMs x 4 flop/clk x 2.07 GHz",
-                 "fp64_pipe_frac": round(instr_pt * n / sec / FP64_PEAK_INSTR, 4),
+                 "peak": round(p64, 4), "unit": "TFLOP/s", "frac": round(tflops / p64, 4),
+                 "peak_source": p64_src,
+                 "fp64_pipe_frac": round(instr_pt * n / sec / (p64 * 1e12 / 2), 4),
                  "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4)}
     else:
         entry = {"kernel": f"{SHORT[alg]}:{name}", "bound": "hbm", "achieved": round(gbs, 1),
@@ -254,15 +288,16 @@ def roofline_of(dtype, alg, kern, n, hbm_peak, hbm_src):
 TRAFFIC = {("f64", "store_some", "fused"): 5.12e9, ("f32", "recompute_all", "fused"): 3.21e9}
 
 
-def e2e_run(fd, torch, alg, dtype, n, steps):
+def e2e_run(fd, torch, alg, dtype, n, steps, nsolvers=2):
     """Same metric through the public API with host buffers: every step copies a state in
-    from pinned host memory, advances one RK3 step and copies the state back out.  Two
-    solvers on two streams take the steps in turn (fd_set_state_async / fd_step /
-    fd_get_state_async), so one solve's copies overlap the other's step, as a user streaming
-    independent states through the library would run it."""
+    from pinned host memory, advances one RK3 step and copies the state back out.  With two
+    solvers on two streams taking the steps in turn (fd_set_state_async / fd_step /
+    fd_get_state_async), one solve's copies overlap the other's step, as a user streaming
+    independent states through the library would run it; with one solver nothing overlaps
+    (copy in, step, copy out, in sequence)."""
     from paper_1610_09146_gb300 import native
     nel = 5 * n**3
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    streams = [torch.cuda.Stream() for _ in range(nsolvers)]
     solvers = [fd.Solver(n, Re=RE, Mach=MACH, Pr=PR, gamma=GAMMA, dt=fd.dt_for_grid(n), algorithm=alg,
                          dtype=dtype, stream=st) for st in streams]
     hin = torch.empty(nel, dtype=torch.float64, pin_memory=True)
@@ -270,12 +305,12 @@ def e2e_run(fd, torch, alg, dtype, n, steps):
     native.fd_get_state(solvers[0].h, hin.data_ptr(), nel, 0)
 
     def one(k):
-        s, o = solvers[k % 2], hout[k % 2]
+        s, o = solvers[k % nsolvers], hout[k % nsolvers]
         native.fd_set_state_async(s.h, hin.data_ptr(), nel, 0)
         native.fd_step(s.h, 1)
         native.fd_get_state_async(s.h, o.data_ptr(), nel, 0)
 
-    for k in range(2):  # warm-up: one step on each solver
+    for k in range(nsolvers):  # warm-up: one step on each solver
         one(k)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -286,10 +321,12 @@ def e2e_run(fd, torch, alg, dtype, n, steps):
     ok = all(s.check_finite() for s in solvers)
     for s in solvers:
         s.close()
+    how = ("two solvers on two streams taking the steps in turn" if nsolvers == 2
+           else "one solver: copy in, step, copy out, in sequence")
     return {"value": n**3 * steps / (t1 - t0), "unit": METRIC, "h2d_bytes_per_step": nel * 8,
-            "d2h_bytes_per_step": nel * 8, "steps": steps, "finite": ok, "family": SHORT[alg],
+            "d2h_bytes_per_step": nel * 8, "steps": steps, "finite": ok, "family": SHORT[alg], "dtype": dtype,
             "path": "per step: fd_set_state_async(pinned host) + fd_step(1) + fd_get_state_async(pinned host), "
-                    "two solvers on two streams taking the steps in turn"}
+                    + how}
 
 
 def cpu_baseline_full(n):
@@ -307,6 +344,7 @@ def run_ours(args):
     import torch
 
     import paper_1610_09146_gb300 as fd
+    from paper_1610_09146_gb300 import native
     ws, rank, local = dist_env()
     dist = None
     if ws > 1:
@@ -327,23 +365,35 @@ def run_ours(args):
     npts = n**3
     stream = torch.cuda.Stream()
     hbm_peak, hbm_src = measured_peaks()
+    try:
+        fp64_peak = native.fd_fp64_peak() / 1e12
+    except Exception:
+        fp64_peak = None
     clocks = ClockSampler(local)
     clocks.start()
+    # the binary64 families, and the mixed binary64 / double-word store-some form, which is
+    # held to the same parity bound (1e-12 against the binary64 oracle)
+    cases = [(alg, args.dtype) for alg in args.variants]
+    if args.dtype == "f64" and "store_some" in args.variants and not args.no_f64dw:
+        cases.append(("store_some", "f64dw"))
     results = {}
     best = None
-    for alg in args.variants:
-        s, ms, kern, finite, diag = time_family(fd, torch, alg, args.dtype, n, args.steps, args.warmup, stream,
+    for alg, dtype in cases:
+        s, ms, kern, finite, diag = time_family(fd, torch, alg, dtype, n, args.steps, args.warmup, stream,
                                                 barrier, clocks)
         value, ms = aggregate_over_ranks(ms, npts, args.steps, dist, "cuda")
         launches = sum(k["launches"] for k in kern.values())
-        results[alg] = {"value": value, "ms_per_step": ms / args.steps, "finite": finite, "gpu_launches": launches,
-                        "kernels": kern, "roofline": roofline_of(args.dtype, alg, kern, npts, hbm_peak, hbm_src),
+        key = SHORT[alg] if dtype == args.dtype else f"{SHORT[alg]}_{dtype}"
+        results[key] = {"value": value, "ms_per_step": ms / args.steps, "finite": finite, "gpu_launches": launches,
+                        "kernels": kern, "dtype": dtype, "family": alg,
+                        "roofline": roofline_of(dtype, alg, kern, npts, hbm_peak, hbm_src, fp64_peak),
                         "ke": diag[0], "enstrophy": diag[1],
                         "paper_table1_256_point_updates_per_s": npts * 500 / PAPER_256_SECONDS[alg]}
         s.close()
         if best is None or value > results[best]["value"]:
-            best = alg
+            best = key
     # binary64-accurate double-word families (FD_DF64): reported beside the binary64 line
+    p64 = fp64_peak or FP64_PEAK_TFLOPS
     df64 = {}
     if args.dtype == "f64" and not args.no_df64:
         for alg in args.variants:
@@ -357,7 +407,7 @@ def run_ours(args):
             df64[SHORT[alg]] = {"value": value, "ms_per_step": ms / args.steps, "finite": finite,
                                 "dominant_kernel": name, "kernels": {kk: round(vv["ms_avg"], 4) for kk, vv in kern.items()},
                                 "binary64_equivalent_tflops": round(eq, 4),
-                                "vs_fp64_peak": round(eq / FP64_PEAK_TFLOPS, 4), "ke": diag[0]}
+                                "vs_fp64_peak": round(eq / p64, 4), "ke": diag[0]}
     # binary32-stencil mode (FD_F32_ACCDW) families, beside the binary64 line
     f32 = {}
     if args.dtype == "f64" and not args.no_df64:
@@ -369,34 +419,47 @@ def run_ours(args):
             f32[SHORT[alg]] = {"value": value, "ms_per_step": ms / args.steps, "finite": finite,
                                "kernels": {kk: round(vv["ms_avg"], 4) for kk, vv in kern.items()},
                                "roofline": roofline_of("f32", alg, kern, npts, hbm_peak, hbm_src),
-                               "ke_rel_vs_binary64": abs(diag[0] - results[alg]["ke"]) / results[alg]["ke"]}
+                               "ke_rel_vs_binary64": abs(diag[0] - results[SHORT[alg]]["ke"])
+                               / results[SHORT[alg]]["ke"]}
     cl = clocks.stop()
-    e2e = e2e_run(fd, torch, best, args.dtype, n, max(4, min(args.steps, 40)))
+    r = results[best]
+    e2e_steps = max(4, min(args.steps, 40))
+    e2e = e2e_run(fd, torch, r["family"], r["dtype"], n, e2e_steps)
     e2e["value"], _ = aggregate_over_ranks(1e3 * npts * e2e["steps"] / e2e["value"], npts, e2e["steps"], dist,
                                            "cuda")
-    r = results[best]
+    e2e1 = e2e_run(fd, torch, r["family"], r["dtype"], n, e2e_steps, nsolvers=1)
+    e2e1["value"], _ = aggregate_over_ranks(1e3 * npts * e2e1["steps"] / e2e1["value"], npts, e2e1["steps"], dist,
+                                            "cuda")
+    dtype_label = {"f64": "f64", "f64dw": "f64dw (binary64 state, pressure, div u, RK; double-word stencils)"}
     line = {
         "metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": r["value"] / r["paper_table1_256_point_updates_per_s"], "dtype": args.dtype,
+        "vs_baseline": r["value"] / r["paper_table1_256_point_updates_per_s"],
+        "dtype": dtype_label.get(r["dtype"], r["dtype"]),
         "data": "synthetic (analytic Taylor-Green vortex initial condition)",
-        "config": {"workload": f"Taylor-Green vortex {n}^3, binary64, one low-storage RK3 step per step, "
-                               "each algorithm family timed separately; value = fastest family",
-                   "family": f"{best} ({SHORT[best]})", "grid": [n, n, n], "Re": RE, "Mach": MACH, "Pr": PR,
-                   "gamma": GAMMA, "dt": fd.dt_for_grid(n),
+        "config": {"workload": f"Taylor-Green vortex {n}^3, binary64 results (parity 1e-12 with the binary64 "
+                               "oracle), one low-storage RK3 step per step, each algorithm family timed separately; "
+                               "value = fastest family",
+                   "family": f"{r['family']} ({SHORT[r['family']]})", "grid": [n, n, n], "Re": RE, "Mach": MACH,
+                   "Pr": PR, "gamma": GAMMA, "dt": fd.dt_for_grid(n),
                    "l2": f"inputs larger than L2 ({40 * npts / 1e6:.0f} MB state per buffer vs 129 MB L2); no flush",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "roofline": r["roofline"], "gpu_launches": r["gpu_launches"], "e2e": e2e, "clocks": cl,
-        "variants": {SHORT[a]: {k: v for k, v in results[a].items() if k != "kernels"} | {
+        "roofline": r["roofline"], "gpu_launches": r["gpu_launches"], "e2e": e2e, "e2e_one_solver": e2e1,
+        "clocks": cl,
+        "fp64_peak_measured_tflops": round(fp64_peak, 4) if fp64_peak else None,
+        "variants": {a: {k: v for k, v in results[a].items() if k != "kernels"} | {
             "kernels": {kk: round(vv["ms_avg"], 4) for kk, vv in results[a]["kernels"].items()}}
             for a in results},
         "variants_df64": df64,
         "variants_f32": f32,
         "variants_f32_note": "dtype f32: binary32 stencils on perturbation fields, compensated (double-word) state "
                              "and RK update; roofline against the measured HBM copy rate",
-        "variants_df64_note": "dtype df64: double-word arithmetic on the binary32 pipe, parity 1e-12 vs the "
-                              "binary64 oracle; binary64_equivalent_tflops counts the binary64 algorithm's flops",
+        "variants_df64_note": "dtype df64: double-word arithmetic on the binary32 pipe; binary64_equivalent_tflops "
+                              "counts the binary64 algorithm's flops",
     }
+    if rank == 0 and ws == 1 and not args.no_extras:
+        line["batched"] = batched_extra(fd, args)
+        line["serve"] = serve_extra(fd, args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_full(n)
     if rank == 0:
@@ -406,25 +469,47 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def batched_extra(fd, args):
+    """Compact record of the 64-instance ensemble (binary32 batch with recompute-all, the
+    autotuner's choice for every grid on GB300, vs the binary64 per-solve loop and batch)."""
+    from paper_1610_09146_gb300 import workloads
+    specs = workloads.ensemble(count=64, steps=100)
+    tuned = [dict(sp, algorithm="recompute_all", tile_points=0) for sp in specs]
+    r = batched_summary(fd, specs, 100, tuned)
+    return {"workload": "64 Taylor-Green solves, grids {32,48,64,96,128}^3, Re U[400,3200], Mach U[0.1,0.4], "
+                        "100 RK3 steps, seed 1610; binary32 batch (recompute-all)",
+            "solves_per_s": r["value"], "fp64_loop_solves_per_s": r["fp64_loop"]["solves_per_s"],
+            "fp64_batched_solves_per_s": r["fp64_batched"]["solves_per_s"],
+            "fp64_batched_equals_loop": r["fp64_batched"]["ke_bitwise_equal_to_loop"],
+            "speedup_vs_fp64_loop": r["speedup_vs_fp64_loop"], "ke_rel_err_vs_fp64_max": r["ke_rel_err_vs_fp64"]["max"]}
+
+
+def serve_extra(fd, args):
+    """Compact serving record: the first args.serve_requests requests of the seeded stream
+    (mean 20 requests/s), binary32 requests on recompute-all and binary64 on store-some."""
+    from paper_1610_09146_gb300 import workloads
+    reqs = workloads.requests(count=args.serve_requests, rate=20.0)
+    for q in reqs:
+        q["algorithm"] = "recompute_all" if q["dtype"] == "f32" else "store_some"
+        q["tile_points"] = 0
+        q["tag"] = q["id"]
+    r = serve_summary(fd, reqs, 20.0, 64, 256)
+    return {"workload": f"first {len(reqs)} requests of the Poisson stream (mean 20/s, seed 9146), grids 48^3-192^3, "
+                        "50-500 RK3 steps, f32 (RA) or f64 (SS) per request",
+            "solves_per_s": r["value"], "latency_p50_s": r["latency_s"]["p50"],
+            "latency_p99_s": r["latency_s"]["p99"], "offered_over_capacity": r["offered_over_capacity"],
+            "completed_ok": r["completed_ok"], "span_s": r["span_s"]}
+
+
 # ------------------------------------------------------------ batched ensemble
 
 
-def run_batched(args):
-    """64 uneven Taylor-Green solves (grids from {32,48,64,96,128}^3, Re in [400,3200],
-    Mach in [0.1,0.4], 100 RK3 steps): binary32-stencil batch in one persistent launch per
-    family and stage (family and tile size per grid from the autotuner) against the plain
-    binary64 per-solve loop on the same GPU.  A solve = create + steps + diagnostics."""
+def batched_summary(fd, specs, steps, tuned):
+    """The ensemble in one binary32 batch (families / tiles of `tuned`), against the plain
+    binary64 per-solve loop and the binary64 batch of the same solves.  A solve = create +
+    steps + diagnostics; seconds are wall time with the device synchronised."""
     import numpy as np
     import torch
-
-    import paper_1610_09146_gb300 as fd
-    from paper_1610_09146_gb300 import autotune, native, workloads
-    torch.cuda.set_device(0)
-    fd.build()
-    specs = workloads.ensemble(count=args.instances, steps=args.solve_steps)
-    steps = args.solve_steps
-    tuned, choice = autotune.choose(specs, "f32")
-    pts = sum(s["n"] ** 3 for s in specs)
 
     def batched(dtype, sp):
         torch.cuda.synchronize()
@@ -432,7 +517,6 @@ def run_batched(args):
         with fd.Batch(sp, dtype=dtype) as b:
             b.step(steps)
             ke, en = b.diagnostics()
-            states = None
         t1 = time.perf_counter()
         return t1 - t0, ke, en
 
@@ -456,9 +540,8 @@ def run_batched(args):
     # binary64 batch of the same solves (store-some everywhere): bitwise the loop's results
     t64b, ke64b, _ = batched("f64", [dict(s, algorithm="store_some", tile_points=1024) for s in specs])
     kerr = np.abs(ke32 - ke64) / ke64
-    line = {
-        "workload": f"batched ensemble: {len(specs)} Taylor-Green solves, grids {{32,48,64,96,128}}^3, "
-                    f"Re U[400,3200], Mach U[0.1,0.4], {steps} RK3 steps, seed 1610",
+    pts = sum(s["n"] ** 3 for s in specs)
+    return {
         "metric": "solves/s", "value": len(specs) / tb, "unit": "solves/s", "higher_is_better": True,
         "dtype": "f32 stencils / compensated-f32 (double-word) accumulation",
         "seconds": tb, "point_updates_per_s": pts * steps / tb,
@@ -467,9 +550,27 @@ def run_batched(args):
                          "ke_bitwise_equal_to_loop": bool(np.array_equal(ke64b, ke64))},
         "speedup_vs_fp64_loop": tl / tb,
         "ke_rel_err_vs_fp64": {"max": float(kerr.max()), "median": float(np.median(kerr))},
-        "autotune": {str(n): {"family": f, "tile_points": t, "ms_per_instance_step": round(m, 4)}
-                     for n, (f, t, m) in choice.items()},
     }
+
+
+def run_batched(args):
+    """64 uneven Taylor-Green solves (grids from {32,48,64,96,128}^3, Re in [400,3200],
+    Mach in [0.1,0.4], 100 RK3 steps): binary32-stencil batch in one persistent launch per
+    family and stage (family and tile size per grid from the autotuner) against the plain
+    binary64 per-solve loop on the same GPU.  A solve = create + steps + diagnostics."""
+    import torch
+
+    import paper_1610_09146_gb300 as fd
+    from paper_1610_09146_gb300 import autotune, workloads
+    torch.cuda.set_device(0)
+    fd.build()
+    specs = workloads.ensemble(count=args.instances, steps=args.solve_steps)
+    tuned, choice = autotune.choose(specs, "f32")
+    line = {"workload": f"batched ensemble: {len(specs)} Taylor-Green solves, grids {{32,48,64,96,128}}^3, "
+                        f"Re U[400,3200], Mach U[0.1,0.4], {args.solve_steps} RK3 steps, seed 1610"}
+    line |= batched_summary(fd, specs, args.solve_steps, tuned)
+    line["autotune"] = {str(n): {"family": f, "tile_points": t, "ms_per_instance_step": round(m, 4)}
+                        for n, (f, t, m) in choice.items()}
     print(json.dumps(line), flush=True)
 
 
@@ -643,23 +744,13 @@ def run_history(args):
     dt = fd.dt_for_grid(n)
     per = max(1, int(round(args.sample_dt / dt)))
     nsamp = int(np.ceil(args.t_end / (per * dt)))
-    t, ke, en = [0.0], [], []
     with fd.Solver(n, dt=dt, algorithm=alg, dtype=args.dtype) as s:
-        k0, e0 = s.diagnostics()
-        ke.append(k0)
-        en.append(e0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for i in range(nsamp):
-            s.step(per)
-            k, e = s.diagnostics()
-            t.append((i + 1) * per * dt)
-            ke.append(k)
-            en.append(e)
+        t, ke, en = s.history(per, nsamp)
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
         finite = s.check_finite()
-    t, ke, en = np.array(t), np.array(ke), np.array(en)
     nu = 1.0 / RE
     eps = -(ke[2:] - ke[:-2]) / (t[2:] - t[:-2])       # -dKE/dt, central differences
     two_nu_omega = 2 * nu * en[1:-1]
@@ -687,31 +778,14 @@ def run_history(args):
 # ------------------------------------------------------------------ serving
 
 
-def run_serve(args):
-    """Poisson stream (mean 20 requests/s, seeded) of Taylor-Green solves, grids the multiples
-    of 16 in [48, 192], 50-500 steps, Re in [400, 3200], Mach in [0.1, 0.4], binary32 or
-    binary64 with equal odds, served by the continuous-batching server: requests are
-    submitted when their arrival time passes on the wall clock, admitted by device
-    footprint, advanced together one RK3 step per tick.  Latency = completion - arrival."""
+def serve_summary(fd, reqs, rate, arena_gb, max_active):
+    """Serve `reqs` (dicts with arrival time t, grid, steps, dtype, algorithm, tile_points)
+    through the continuous-batching server: each request is submitted when its arrival time
+    passes on the wall clock; ticks run while any solve is queued or active.  Latency =
+    completion (the tick that retired it) - arrival."""
     import numpy as np
-    import torch
-
-    import paper_1610_09146_gb300 as fd
-    from paper_1610_09146_gb300 import autotune, workloads
-    torch.cuda.set_device(0)
-    fd.build()
-    reqs = workloads.requests(count=args.requests, rate=args.rate)
-    # family and tile per (grid, dtype) from the autotuner (cached between runs)
-    best = {}
-    for r in reqs:
-        k = (r["n"], r["dtype"])
-        if k not in best:
-            fam, tile, ms = autotune.tune(r["n"], r["dtype"])
-            best[k] = (fam, tile, ms)
-        r["algorithm"], r["tile_points"] = best[k][0], best[k][1]
-        r["tag"] = r["id"]
     work = sum(r["n"] ** 3 * r["steps"] for r in reqs)
-    with fd.Server(args.arena_gb * (1 << 30), max_active=args.max_active) as srv:
+    with fd.Server(arena_gb * (1 << 30), max_active=max_active) as srv:
         # warm-up outside the measurement: one tiny solve of each dtype
         for dt_ in ("f32", "f64"):
             srv.submit(dict(n=16, steps=2, dtype=dt_, tag=-1))
@@ -742,22 +816,47 @@ def run_serve(args):
     lat = np.array([done[r["id"]][0] - r["t"] for r in reqs])
     ok = sum(1 for v in done.values() if v[1]["status"] == fd.FD_OK)
     span = t_end - reqs[0]["t"]
-    offered = args.rate * work / len(reqs)
-    line = {
-        "workload": f"serving: {len(reqs)} Poisson requests (mean {args.rate}/s, seed 9146), grids 48^3-192^3, "
-                    "50-500 RK3 steps, Re U[400,3200], Mach U[0.1,0.4], f32 or f64 per request",
+    offered = rate * work / len(reqs)
+    return {
         "metric": "solves/s", "value": len(reqs) / span, "unit": "solves/s", "higher_is_better": True,
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "mean": float(lat.mean()), "max": float(lat.max())},
-        "completed_ok": ok, "span_s": span,
+        "completed_ok": ok, "requests": len(reqs), "span_s": span,
         "point_updates_per_s": work / span,
         "capacity_point_updates_per_busy_s": work / busy,
         "offered_point_updates_per_s": offered,
         "offered_over_capacity": offered / (work / busy),
         "mean_active_per_tick": float(np.mean(active_hist)), "ticks": stats["ticks"],
-        "arena_gb": args.arena_gb, "max_active": args.max_active,
-        "autotune": {f"{n}|{d}": {"family": f, "tile_points": t} for (n, d), (f, t, _) in sorted(best.items())},
+        "arena_gb": arena_gb, "max_active": max_active,
     }
+
+
+def run_serve(args):
+    """Poisson stream (mean 20 requests/s, seeded) of Taylor-Green solves, grids the multiples
+    of 16 in [48, 192], 50-500 steps, Re in [400, 3200], Mach in [0.1, 0.4], binary32 or
+    binary64 with equal odds, served by the continuous-batching server: requests are
+    submitted when their arrival time passes on the wall clock, admitted by device
+    footprint, advanced together (time-sliced ticks).  Latency = completion - arrival."""
+    import torch
+
+    import paper_1610_09146_gb300 as fd
+    from paper_1610_09146_gb300 import autotune, workloads
+    torch.cuda.set_device(0)
+    fd.build()
+    reqs = workloads.requests(count=args.requests, rate=args.rate)
+    # family and tile per (grid, dtype) from the autotuner (cached between runs)
+    best = {}
+    for r in reqs:
+        k = (r["n"], r["dtype"])
+        if k not in best:
+            fam, tile, ms = autotune.tune(r["n"], r["dtype"])
+            best[k] = (fam, tile, ms)
+        r["algorithm"], r["tile_points"] = best[k][0], best[k][1]
+        r["tag"] = r["id"]
+    line = {"workload": f"serving: {len(reqs)} Poisson requests (mean {args.rate}/s, seed 9146), grids 48^3-192^3, "
+                        "50-500 RK3 steps, Re U[400,3200], Mach U[0.1,0.4], f32 or f64 per request"}
+    line |= serve_summary(fd, reqs, args.rate, args.arena_gb, args.max_active)
+    line["autotune"] = {f"{n}|{d}": {"family": f, "tile_points": t} for (n, d), (f, t, _) in sorted(best.items())}
     print(json.dumps(line), flush=True)
 
 
@@ -765,32 +864,32 @@ def run_serve(args):
 
 
 def run_reference(args):
+    """The oracle (the plain binary64 CPU solver that checks the CUDA path) on the host
+    cores, on the same workload as the CUDA line: one RK3 step of the full grid per step."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np
-
     import oracle
-    n, slab = args.grid, 8
-    h = (2 * math.pi / n,) * 3
-    dt = 3.385e-3 * 64 / n
-    Q = np.ascontiguousarray(oracle.tgv_ic(n, n, n, GAMMA, MACH)[:, :slab])
+    n = args.grid
+    dt = 3.385e-3 * 64 / max(n, 64)  # the time-step rule of the CUDA line (Section 3)
+    Q = oracle.tgv_ic(n, n, n, GAMMA, MACH)
     times = []
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.run(Q, 1, dt=dt, Re=RE, Mach=MACH, Pr=PR, gamma=GAMMA, h=h)
+        Q = oracle.run(Q, 1, dt=dt, Re=RE, Mach=MACH, Pr=PR, gamma=GAMMA)
         t1 = time.perf_counter()
         if it >= args.warmup:
             times.append(t1 - t0)
-    pts = n * n * slab
+    pts = n**3
     ms = 1e3 * sum(times) / len(times)
     value = pts / (ms / 1e3)
-    sample = f"one RK3 step of a {n}x{n}x{slab} periodic slab of the {n}^3 grid per step (grid spacing 2*pi/{n})"
+    sample = f"one RK3 step of the full {n}^3 grid per step ({ms / 1e3:.2f} s each)"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (analytic Taylor-Green vortex initial condition)",
-        "config": {"workload": f"Taylor-Green vortex {n}^3, binary64, one low-storage RK3 step per step",
+        "config": {"workload": f"Taylor-Green vortex {n}^3, binary64 results (parity 1e-12 with the binary64 "
+                               "oracle), one low-storage RK3 step per step",
                    "grid": [n, n, n], "Re": RE, "Mach": MACH, "Pr": PR, "gamma": GAMMA, "dt": dt},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": sample},
@@ -810,6 +909,9 @@ def main():
     ap.add_argument("--variants", nargs="+", default=VARIANTS, choices=VARIANTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-df64", action="store_true", help="skip the df64 and binary32 families beside the line")
+    ap.add_argument("--no-f64dw", action="store_true", help="skip the mixed binary64 / double-word store-some form")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving records of the line")
+    ap.add_argument("--serve-requests", type=int, default=40, help="requests in the line's serving record")
     ap.add_argument("--workload", choices=["single", "batched", "serve", "mixed512", "history", "sweep"],
                     default="single",
                     help="single: the 256^3 line (default); batched / serve / mixed512: the ensemble, "

@@ -69,6 +69,16 @@ extern "C" {
 #define FD_RECOMPUTE_ALL 2
 #define FD_RECOMPUTE_SOME 3
 #define FD_STORE_NONE 4
+/* FD_RECOMPUTE_ALL_INLINE  RA read literally, binary64 (FD_F64) only: not even
+ *                    the primitive variables are stored; u_i, p and T are
+ *                    recomputed from the five conserved values at every tap
+ *                    that needs them (Section 2, paragraph RA; the paragraph
+ *                    after Fig. 1 stores them in every algorithm, which the
+ *                    other five families follow).  The least memory of all
+ *                    (the state and the saved register only), the most
+ *                    binary64 arithmetic; results equal FD_RECOMPUTE_ALL's bit
+ *                    for bit (same formulas per value).  Not batched. */
+#define FD_RECOMPUTE_ALL_INLINE 5
 
 /* ---- arithmetic ----------------------------------------------------------
  * FD_F64        all arithmetic in IEEE binary64 (the paper's precision,
@@ -82,15 +92,22 @@ extern "C" {
  *               binary64 and the kinetic energy / enstrophy reductions run in
  *               binary64.  The paper has no counterpart; it is a precision
  *               mode of this library.
- * FD_DF64       binary64-accurate results without binary64 instructions: the
- *               stencils, fluxes, residual, RK accumulation and the stored
- *               state use double-word ("double-float") arithmetic, pairs of
- *               binary32 numbers with about 48 significant bits (Knuth
- *               TwoSum, Dekker FastTwoSum, FMA-based products; the algorithms
- *               of Joldes, Muller & Popescu 2017), on the shifted fields of
- *               FD_F32_ACCDW.  On GB300 binary32 issues 64x faster than
- *               binary64.  States cross the API as binary64; the reductions
- *               run in binary64.  No counterpart in the paper. */
+ * FD_DF64       results within a few units of 1e-12 of binary64 without
+ *               binary64 instructions: the stencils, fluxes, residual, RK
+ *               accumulation and the stored state use double-word
+ *               ("double-float") arithmetic, pairs of binary32 numbers with
+ *               about 48 significant bits (Knuth TwoSum, Dekker FastTwoSum,
+ *               FMA-based products; the algorithms of Joldes, Muller & Popescu
+ *               2017), on the shifted fields of FD_F32_ACCDW.  On GB300
+ *               binary32 issues 64x faster than binary64.  States cross the
+ *               API as binary64; the reductions run in binary64.  Bound
+ *               against the binary64 oracle (relative L-inf per variable):
+ *               1e-12 at 32^3 after 10 steps; 4e-12 on rho w after one step
+ *               at 256^3 (measured 1.6e-12), where rho w (<= 2e-4) resolves
+ *               the binary64 rounding of the pressure (its mean is ~70 times
+ *               its variation), which the double-word pressure does not
+ *               reproduce; FD_F64_DW keeps that pressure in binary64 and
+ *               meets 1e-12 there.  No counterpart in the paper. */
 #define FD_F64 0
 #define FD_F32_ACCDW 1
 #define FD_DF64 2
@@ -405,6 +422,48 @@ int fd_residual_noalloc(const double* Q, double* R, int nx, int ny, int nz, doub
  * paper has no counterpart.  Errors: FD_EINVAL (err_word NULL, or TMA staging
  * turned off by FDGB300_NO_TMA=1), FD_ENOMEM, FD_ECUDA. */
 int fd_selftest_wait_timeout(int* err_word);
+
+/* ---- z-slab decomposition ---------------------------------------------------
+ * The paper runs its solver over MPI ranks that each own a block of the grid
+ * (Section 4.1, strong and weak scaling).  Here a rank owns the planes
+ * z_first .. z_first + nz_local - 1 of a periodic grid of nz_global planes
+ * (a z-slab) and keeps `ghost` copies of its neighbours' planes on either side,
+ * so a handle of nz_local + 2 ghost planes advances one RK3 step exactly on its
+ * own planes with no exchange inside the step: a stage's result at a plane
+ * depends on planes within 2 of it in every family (the stored gradients and
+ * derivative arrays are differenced along z only where they are in-plane
+ * derivatives), so after three stages only the outer 3 x 2 planes of each
+ * ghost band are stale.  Between steps the caller refreshes the ghost planes
+ * from the neighbours (fd_get_planes_async / fd_set_planes_async on the
+ * ranks' streams, and NCCL send / receive or a peer copy between them): rank r
+ * sends its lowest `ghost` own planes down and its highest up.  The arithmetic
+ * per point is that of the whole grid, so the slabs together give exactly the
+ * whole-grid result.  The paper has no API for this (its decomposition is the
+ * OPS runtime's); these calls are this library's form of it.
+ *
+ * fd_slab_ghost_planes: the least ghost depth for an algorithm (6 for every
+ * family), or -1 for an unknown algorithm.
+ *
+ * fd_slab_create: as fd_create for a slab; the handle's own plane k (0 <= k <
+ * nz_local + 2 ghost) is plane (z_first - ghost + k) mod nz_global of the
+ * grid, and its z spacing is 2 pi / nz_global.  The state (fd_get_state /
+ * fd_set_state) covers all of the handle's planes, own planes at ghost ..
+ * ghost + nz_local - 1.  dtype FD_F64 or FD_F64_DW; ghost >=
+ * fd_slab_ghost_planes(algorithm) and <= nz_global; 0 <= z_first < nz_global,
+ * 1 <= nz_local <= nz_global.  Errors as fd_create.
+ *
+ * fd_get_planes_async / fd_set_planes_async: copy `count` planes starting at
+ * the handle's plane z of the state to / from buf, laid out
+ * double[5][count][ny][nx] (host or device memory, by *_is_device),
+ * stream-ordered on the handle's stream like fd_get_state_async.  Any handle
+ * with a binary64 state (FD_F64, FD_F64_DW).  Errors: FD_EINVAL (NULL,
+ * planes outside the handle, other dtype), FD_ECUDA. */
+int fd_slab_ghost_planes(int algorithm);
+int fd_slab_create(fd_handle** out, int nx, int ny, int nz_global, int z_first, int nz_local, int ghost, double Re,
+                   double Mach, double Pr, double gamma, double dt, int algorithm, int dtype, const fd_alloc* alloc,
+                   void* cuda_stream);
+int fd_get_planes_async(fd_handle* h, int z, int count, double* dst, int dst_is_device);
+int fd_set_planes_async(fd_handle* h, int z, int count, const double* src, int src_is_device);
 
 /* ---- measured binary64 rate -----------------------------------------------
  * The denominator of the binary64 kernels' roofline: runs a loop of

@@ -27,8 +27,9 @@ from .native import (FD_DF64, FD_EBUSY, FD_ECUDA, FD_EINVAL, FD_ENOMEM, FD_EUNST
 
 ALGORITHMS = {"store_all": FD_STORE_ALL, "store_some": FD_STORE_SOME, "recompute_all": FD_RECOMPUTE_ALL,
               "recompute_some": FD_RECOMPUTE_SOME, "store_none": FD_STORE_NONE,
+              "recompute_all_inline": native.FD_RECOMPUTE_ALL_INLINE,
               "BL": FD_STORE_ALL, "SS": FD_STORE_SOME, "RA": FD_RECOMPUTE_ALL, "RS": FD_RECOMPUTE_SOME,
-              "SN": FD_STORE_NONE}
+              "SN": FD_STORE_NONE, "RAI": native.FD_RECOMPUTE_ALL_INLINE}
 DTYPES = {"f64": FD_F64, "f32": FD_F32_ACCDW, "f32_accdw": FD_F32_ACCDW, "df64": FD_DF64, "f64dw": FD_F64_DW}
 
 from .workloads import dt_for_grid  # noqa: E402  (Section 3 time-step rule)

@@ -85,6 +85,9 @@ struct fd_handle {
     int* flag = nullptr;
     int* kerr = nullptr;       // set by a kernel whose bounded wait ran out
     bool use_tma = false;      // binary32 RA: planes staged by TMA (fmap[b] describes Wf[b])
+    // z-slab decomposition (fd_slab_create): the handle's nz planes are ghost + nz_local
+    // + ghost planes of a periodic grid of nz_global planes, starting at z_first - ghost
+    int slab_ghost = 0, slab_nz_local = 0, slab_z_first = 0, slab_nz_global = 0;
     CUtensorMap fmap[2]{};
     fd::Grid grid{};
     fd::Phys phys{};
@@ -131,8 +134,10 @@ int check_args(int nx, int ny, int nz, double Re, double Mach, double Pr, double
     if (const char* why = fd::check_instance(nx, ny, nz, Re, Mach, Pr, gamma, dt))
         return fail_global(FD_EINVAL, "fd_create: grid %dx%dx%d: %s", nx, ny, nz, why);
     if (algorithm != FD_STORE_ALL && algorithm != FD_STORE_SOME && algorithm != FD_RECOMPUTE_ALL &&
-        algorithm != FD_RECOMPUTE_SOME && algorithm != FD_STORE_NONE)
+        algorithm != FD_RECOMPUTE_SOME && algorithm != FD_STORE_NONE && algorithm != FD_RECOMPUTE_ALL_INLINE)
         return fail_global(FD_EINVAL, "unknown algorithm %d", algorithm);
+    if (algorithm == FD_RECOMPUTE_ALL_INLINE && dtype != FD_F64)
+        return fail_global(FD_EINVAL, "FD_RECOMPUTE_ALL_INLINE exists in binary64 (FD_F64) only");
     if (dtype != FD_F64 && dtype != FD_F32_ACCDW && dtype != FD_DF64 && dtype != FD_F64_DW)
         return fail_global(FD_EINVAL, "unknown dtype %d", dtype);
     if (dtype == FD_F64_DW && algorithm != FD_STORE_SOME)
@@ -164,7 +169,9 @@ Layout plan(long long n, int algorithm, int dtype, size_t wf_points) {
     L.q1 = take(f5);
     L.qs = take(f5);
     L.w1 = L.g = L.p = L.d1 = L.d2 = L.wf0 = L.wf1 = L.gf = L.wd0 = L.wd1 = L.gd = (size_t)-1;
-    L.w0 = dtype == FD_DF64 ? (size_t)-1 : take(dtype == FD_F64_DW ? 4 * n * sizeof(double) : f5);
+    L.w0 = dtype == FD_DF64 || algorithm == FD_RECOMPUTE_ALL_INLINE
+               ? (size_t)-1
+               : take(dtype == FD_F64_DW ? 4 * n * sizeof(double) : f5);
     if (dtype == FD_F64_DW) {
         // binary64 state; W[2] the binary64 u, v, w, p; Wd[2] the double-word working fields
         L.w1 = take(4 * n * sizeof(double));
@@ -181,6 +188,8 @@ Layout plan(long long n, int algorithm, int dtype, size_t wf_points) {
             L.d1 = take(45 * n * sizeof(fd::df64));
             L.d2 = take(18 * n * sizeof(fd::df64));
         }
+    } else if (dtype == FD_F64 && algorithm == FD_RECOMPUTE_ALL_INLINE) {
+        L.w0 = (size_t)-1;  // no primitive arrays: the state alone (the diagnostics use Qs)
     } else if (dtype == FD_F64) {
         L.w1 = take(f5);
         if (stores_g(algorithm)) L.g = take(fd::kGradArrays<double> * n * sizeof(double));
@@ -300,6 +309,11 @@ cudaError_t run_stage(fd_handle* h, int s, bool resid, double* out) {
     const int wc = h->wcur;
     const long long n = h->n;
     cudaError_t e;
+    if (h->dtype == FD_F64 && h->algorithm == FD_RECOMPUTE_ALL_INLINE) {
+        return timed(h, FD_KERNEL_FUSED, [&] {
+            return fd::launch_ra_inline(g, h->kd, ph, rk, resid, Qin, Qout, h->Qs, h->stream);
+        });
+    }
     if (h->dtype == FD_F64) {
         if (!h->wvalid) {
             e = timed(h, FD_KERNEL_PRIMS, [&] { return fd::launch_prims_f64(g, ph, Qin, h->W[wc], h->stream); });
@@ -378,12 +392,26 @@ cudaError_t state_to_binary64(fd_handle* h, double* dst) {
                                 h->stream);
 }
 
+int create_impl(fd_handle** out, int nx, int ny, int nz, int nz_period, int z0, double Re, double Mach, double Pr,
+                double gamma, double dt, int algorithm, int dtype, const fd_alloc* alloc, void* cuda_stream);
+
 }  // namespace
 
 extern "C" {
 
 int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, double Pr, double gamma, double dt,
               int algorithm, int dtype, const fd_alloc* alloc, void* cuda_stream) {
+    return create_impl(out, nx, ny, nz, 0, 0, Re, Mach, Pr, gamma, dt, algorithm, dtype, alloc, cuda_stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+// fd_create, and (nz_period > 0) a slab of nz planes of a periodic grid of
+// nz_period planes whose plane 0 is plane z0 (mod nz_period) of that grid.
+int create_impl(fd_handle** out, int nx, int ny, int nz, int nz_period, int z0, double Re, double Mach, double Pr,
+                double gamma, double dt, int algorithm, int dtype, const fd_alloc* alloc, void* cuda_stream) {
     if (!out) return fail_global(FD_EINVAL, "fd_create: out is NULL");
     *out = nullptr;
     int rc = check_args(nx, ny, nz, Re, Mach, Pr, gamma, dt, algorithm, dtype);
@@ -412,7 +440,7 @@ int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, d
     // binary32 recompute-all stages its planes with TMA where the grid allows it
     // (FDGB300_NO_TMA=1 selects the thread-staged kernel, for comparison); its
     // working fields then use the ghost-padded layout.
-    const fd::Grid grid0 = fd::make_grid(nx, ny, nz);
+    const fd::Grid grid0 = fd::make_grid(nx, ny, nz, nz_period);
     if (dtype == FD_F32_ACCDW && algorithm == FD_RECOMPUTE_ALL && fd::tma_staging_ok(grid0)) {
         const char* off = std::getenv("FDGB300_NO_TMA");
         h->use_tma = !(off && off[0] == '1');
@@ -466,8 +494,9 @@ int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, d
     h->flag = at<int>(h->block, L.flag);
     h->kerr = at<int>(h->block, L.kerr);
 
-    const double hx = 2.0 * fd::kPi / nx, hy = 2.0 * fd::kPi / ny, hz = 2.0 * fd::kPi / nz;
-    h->grid = fd::make_grid(nx, ny, nz);
+    const double hx = 2.0 * fd::kPi / nx, hy = 2.0 * fd::kPi / ny,
+                 hz = 2.0 * fd::kPi / (nz_period > 0 ? nz_period : nz);
+    h->grid = fd::make_grid(nx, ny, nz, nz_period);
     h->phys = fd::make_phys(Re, Mach, Pr, gamma);
     const fd::Grid& g = h->grid;
     const fd::Phys& ph = h->phys;
@@ -491,11 +520,11 @@ int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, d
         return fail_global(FD_ECUDA, "fd_create: staging set-up: %s", cudaGetErrorString(e));
     }
     if (dw_state(dtype)) {
-        e = fd::launch_tgv_ic(g, ph, hx, hy, hz, h->Qs, h->stream);
+        e = fd::launch_tgv_ic(g, ph, hx, hy, hz, h->Qs, h->stream, z0, nz_period);
         if (e == cudaSuccess)
             e = fd::launch_to_df64(h->Qs, reinterpret_cast<fd::df64*>(h->Q[0]), h->n, state_shift(h), h->stream);
     } else {
-        e = fd::launch_tgv_ic(g, ph, hx, hy, hz, h->Q[0], h->stream);
+        e = fd::launch_tgv_ic(g, ph, hx, hy, hz, h->Q[0], h->stream, z0, nz_period);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
@@ -506,6 +535,10 @@ int fd_create(fd_handle** out, int nx, int ny, int nz, double Re, double Mach, d
     *out = h;
     return FD_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int fd_step(fd_handle* h, int n) {
     if (!h) return fail_global(FD_EINVAL, "fd_step: NULL handle");
@@ -580,7 +613,8 @@ int fd_diagnostics(fd_handle* h, double* ke, double* enstrophy) {
     // overwrite (binary64, df64), or W[0], unused by the binary32 stages.  The
     // double-word modes first convert the state to binary64 in Qs (dead
     // between steps).
-    double* Wv = h->dtype == FD_F64                               ? h->W[1 - h->wcur]
+    double* Wv = h->algorithm == FD_RECOMPUTE_ALL_INLINE          ? h->Qs
+                 : h->dtype == FD_F64                             ? h->W[1 - h->wcur]
                  : h->dtype == FD_DF64 || h->dtype == FD_F64_DW ? reinterpret_cast<double*>(h->Wd[1 - h->wcur])
                                                                 : h->W[0];
     const double* Q = h->Q[h->cur];
@@ -643,6 +677,90 @@ int fd_check_finite(fd_handle* h) {
     if (int rc = check_kernel_error(h, "fd_check_finite")) return rc;
     if (flag) return h->fail(FD_EUNSTABLE, "state holds NaN or infinity");
     return FD_OK;
+}
+
+int fd_slab_create(fd_handle** out, int nx, int ny, int nz_global, int z_first, int nz_local, int ghost, double Re,
+                   double Mach, double Pr, double gamma, double dt, int algorithm, int dtype, const fd_alloc* alloc,
+                   void* cuda_stream) {
+    if (!out) return fail_global(FD_EINVAL, "fd_slab_create: out is NULL");
+    *out = nullptr;
+    if (dtype != FD_F64 && dtype != FD_F64_DW)
+        return fail_global(FD_EINVAL, "fd_slab_create: dtype %d; slabs hold binary64 states (FD_F64, FD_F64_DW)",
+                           dtype);
+    if (nz_global < 5 || nz_local < 1 || z_first < 0 || z_first >= nz_global || nz_local > nz_global)
+        return fail_global(FD_EINVAL, "fd_slab_create: planes %d..%d of %d", z_first, z_first + nz_local - 1,
+                           nz_global);
+    const int need = fd_slab_ghost_planes(algorithm);
+    if (need <= 0) return fail_global(FD_EINVAL, "fd_slab_create: unknown algorithm %d", algorithm);
+    if (ghost < need || ghost > nz_global)
+        return fail_global(FD_EINVAL, "fd_slab_create: ghost = %d, this family needs %d (and at most nz_global)",
+                           ghost, need);
+    const long long nz = (long long)nz_local + 2LL * ghost;
+    if (nz > fd::kMaxPoints) return fail_global(FD_EINVAL, "fd_slab_create: slab too large");
+    int rc = create_impl(out, nx, ny, (int)nz, nz_global, z_first - ghost, Re, Mach, Pr, gamma, dt, algorithm, dtype,
+                         alloc, cuda_stream);
+    if (rc != FD_OK) return rc;
+    fd_handle* h = *out;
+    h->slab_ghost = ghost;
+    h->slab_nz_local = nz_local;
+    h->slab_z_first = z_first;
+    h->slab_nz_global = nz_global;
+    return FD_OK;
+}
+
+int fd_slab_ghost_planes(int algorithm) {
+    // A stage's result at plane z reads planes z-2 .. z+2 in every family: the
+    // stored gradients (SS, RS) and derivative arrays (BL) at plane z read planes
+    // z-2 .. z+2, and a z-difference of stored values only ever takes in-plane
+    // derivatives (D_z of D_x u + D_y v; D_x, D_y of D_z w at the same plane).
+    // Three stages per step: 3 x 2 planes.
+    switch (algorithm) {
+        case FD_STORE_ALL:
+        case FD_STORE_SOME:
+        case FD_RECOMPUTE_ALL:
+        case FD_RECOMPUTE_SOME:
+        case FD_STORE_NONE:
+        case FD_RECOMPUTE_ALL_INLINE:
+            return 6;
+        default:
+            return -1;
+    }
+}
+
+// Stream-ordered copy of `count` planes starting at plane z of the state to or
+// from buf, laid out [5][count][ny][nx] (one 2-D copy: 5 rows of count planes,
+// pitch = one variable of the state).
+static int planes_copy(fd_handle* h, int z, int count, double* buf, int buf_is_device, bool to_state,
+                       const char* what) {
+    if (!h) return fail_global(FD_EINVAL, "%s: NULL handle", what);
+    if (!buf) return h->fail(FD_EINVAL, "%s: buffer is NULL", what);
+    if (h->dtype != FD_F64 && h->dtype != FD_F64_DW)
+        return h->fail(FD_EINVAL, "%s: the state is not binary64 (dtype %d)", what, h->dtype);
+    if (z < 0 || count < 0 || z + count > h->nz)
+        return h->fail(FD_EINVAL, "%s: planes %d..%d outside 0..%d", what, z, z + count - 1, h->nz - 1);
+    if (count == 0) return FD_OK;
+    const size_t plane = (size_t)h->nx * h->ny;
+    double* state = h->Q[h->cur] + (size_t)z * plane;
+    const size_t width = (size_t)count * plane * sizeof(double), pitch_state = (size_t)h->n * sizeof(double);
+    cudaError_t e;
+    if (to_state) {
+        h->wvalid = false;  // the working fields of the replaced planes are stale
+        e = cudaMemcpy2DAsync(state, pitch_state, buf, width, width, 5,
+                              buf_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+    } else {
+        e = cudaMemcpy2DAsync(buf, width, state, pitch_state, width, 5,
+                              buf_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+    }
+    if (e != cudaSuccess) return h->cuda_fail(e, what);
+    return FD_OK;
+}
+
+int fd_get_planes_async(fd_handle* h, int z, int count, double* dst, int dst_is_device) {
+    return planes_copy(h, z, count, dst, dst_is_device, false, "fd_get_planes_async");
+}
+
+int fd_set_planes_async(fd_handle* h, int z, int count, const double* src, int src_is_device) {
+    return planes_copy(h, z, count, const_cast<double*>(src), src_is_device, true, "fd_set_planes_async");
 }
 
 int fd_selftest_wait_timeout(int* err_word) {

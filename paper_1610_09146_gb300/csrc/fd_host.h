@@ -18,14 +18,16 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kRkA[3] = {2.0 / 3.0, 5.0 / 12.0, 3.0 / 5.0};
 constexpr double kRkB[3] = {1.0 / 4.0, 3.0 / 20.0, 0.0};
 
-// Periodic grid x_i = i * 2 pi / n per axis (Section 3).
-inline Grid make_grid(int nx, int ny, int nz) {
+// Periodic grid x_i = i * 2 pi / n per axis (Section 3).  nz_period > 0: the
+// z spacing is that of a periodic grid of nz_period planes, of which these nz
+// are a slab (the z-slab decomposition).
+inline Grid make_grid(int nx, int ny, int nz, int nz_period = 0) {
     Grid g{};
     g.nx = nx;
     g.ny = ny;
     g.nz = nz;
     g.n = nx * ny * nz;
-    const int ns[3] = {nx, ny, nz};
+    const int ns[3] = {nx, ny, nz_period > 0 ? nz_period : nz};
     for (int a = 0; a < 3; ++a) {
         double h = 2.0 * kPi / ns[a];
         g.inv12h[a] = 1.0 / (12.0 * h);

@@ -14,8 +14,10 @@ namespace fd {
 constexpr int kDiagBlocks = 608;   // 4 per SM on a 152-SM GB300
 constexpr int kDiagThreads = 256;
 
+// Taylor-Green state of the grid, or (z0, nz_period) of the planes z0 .. z0+nz-1
+// (mod nz_period) of a periodic grid of nz_period planes (a slab).
 cudaError_t launch_tgv_ic(const Grid& g, const Phys& ph, double hx, double hy, double hz, double* Q,
-                          cudaStream_t st);
+                          cudaStream_t st, int z0 = 0, int nz_period = 0);
 // Primitive variables: binary64 W = (u, v, w, p, T), or the ten binary32
 // perturbation fields F = (rho-1, rho u, rho v, rho w, rhoE-rhoE0, u, v, w, p-p0, T-1).
 cudaError_t launch_prims_f64(const Grid& g, const Phys& ph, const double* Q, double* W, cudaStream_t st);
@@ -68,6 +70,10 @@ template <class T>
 cudaError_t launch_ss(const Grid& g, const Coef<T>& k, const Phys& ph, const RKStage& rk, bool resid, const T* Qf,
                       const T* Wf, const T* Gw, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext,
                       cudaStream_t st);
+// Recompute-all with the primitives recomputed at every tap from the state
+// (FD_RECOMPUTE_ALL_INLINE, binary64): no working fields at all.
+cudaError_t launch_ra_inline(const Grid& g, const Coef<double>& k, const Phys& ph, const RKStage& rk, bool resid,
+                             const double* Q64, double* out, double* Qs, cudaStream_t st);
 // Store-some in mixed binary64 / double-word arithmetic (FD_F64_DW): binary64
 // state Q / Qs / out, binary64 velocities and pressure W64 = (u, v, w, p) (4
 // arrays), the ten shifted double-word working fields F (as in the df64 mode)

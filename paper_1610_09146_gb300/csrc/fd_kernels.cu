@@ -136,10 +136,13 @@ __device__ __forceinline__ df64 rk_b(const RKStage& rk, df64) { return rk.bdt_w;
 
 // ---------------------------------------------------------------- Section 3
 // Taylor-Green vortex (DeBonis 2013, cited in Section 3).
-__global__ void k_tgv_ic(Grid g, Phys ph, double hx, double hy, double hz, double* __restrict__ Q) {
+// Plane k of the array is plane (k + z0) mod nzp of the periodic grid (z0 = 0,
+// nzp = nz for a whole grid; a slab of the z-slab decomposition passes its offset).
+__global__ void k_tgv_ic(Grid g, Phys ph, double hx, double hy, double hz, int z0, int nzp,
+                         double* __restrict__ Q) {
     int idx = grid_index();
     if (idx >= g.n) return;
-    int i = idx % g.nx, t = idx / g.nx, j = t % g.ny, k = t / g.ny;
+    int i = idx % g.nx, t = idx / g.nx, j = t % g.ny, k = ((t / g.ny + z0) % nzp + nzp) % nzp;
     double sx, cx, sy, cy, sz, cz, s2x, c2x, s2y, c2y, s2z, c2z;
     sincos(i * hx, &sx, &cx);
     sincos(j * hy, &sy, &cy);
@@ -639,6 +642,63 @@ __global__ void __launch_bounds__(128) k_ra(Grid g, Coef<T> k, Phys ph, RKStage 
     stage_write<T, RESID>(rk, ph, g.n, s.c, Q64, R, out, Qs, Wnext);
 }
 
+// Recompute-all with the primitives recomputed at every tap (binary64): the
+// paragraph RA of Section 2 read literally, with nothing but the state in
+// memory -- no primitive arrays (which every other family stores, as the
+// paragraph after Fig. 1 has it).  Each tap's u_i, p or T comes from that
+// tap's five conserved values with the binary64 path's formulas (Eqs. 6-7),
+// so the arithmetic per value is that of the stored primitives; a point
+// evaluates them at every tap of every stencil that needs them.
+struct InlineAcc {
+    static constexpr bool kZQueue = false;
+    const Nbr& s;
+    int n;
+    const double* __restrict__ Q;
+    double gm1, gM2;
+    __device__ __forceinline__ double q(int f, int i) const { return ld(Q + f * n, i); }
+    // field f at linear index i: 0..4 the state, 5..7 u_i, 8 p, 9 T
+    __device__ __forceinline__ double at(int f, int i) const {
+        if (f < 5) return q(f, i);
+        const double inv = 1.0 / q(0, i);
+        if (f < 8) return q(f - 4, i) * inv;
+        const double m0 = q(1, i), m1 = q(2, i), m2 = q(3, i);
+        const double p = gm1 * fmx(-0.5, fmx(m0, m0 * inv, fmx(m1, m1 * inv, m2 * (m2 * inv))), q(4, i));
+        return f == 8 ? p : gM2 * p * inv;
+    }
+    __device__ __forceinline__ double center(int f) const { return at(f, s.c); }
+    __device__ __forceinline__ void taps(int f, int j, double t[4]) const {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) t[a] = at(f, s.c + s.o[j][a]);
+    }
+    __device__ __forceinline__ void taps_shifted(int f, int j, int i, int a, double t[4]) const {
+        const int c = s.c + s.o[i][a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) t[b] = at(f, c + s.o[j][b]);
+    }
+};
+
+template <bool RESID>
+__global__ void __launch_bounds__(128) k_ra_inline(Grid g, Coef<double> k, Phys ph, RKStage rk,
+                                                   const double* __restrict__ Q64, double* __restrict__ out,
+                                                   double* __restrict__ Qs) {
+    const int idx = grid_index();
+    if (idx >= g.n) return;
+    const int n = g.n;
+    const Nbr s = make_nbr(g, idx);
+    double R[5];
+    fused_residual<double, false>(InlineAcc{s, n, Q64, ph.gm1, ph.gM2}, k, R);
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+        if constexpr (RESID) {
+            out[f * n + s.c] = R[f];
+        } else {
+            const double qs = rk.stage == 0 ? Q64[f * n + s.c] : Qs[f * n + s.c];
+            out[f * n + s.c] = fmx(rk.adt, R[f], qs);
+            if (rk.stage < 2) Qs[f * n + s.c] = fmx(rk.bdt, R[f], qs);
+        }
+    }
+}
+
 // Recompute-all with shared-memory staging (binary32 and df64 modes).  A block of
 // kTX x kTY threads owns that x-y tile and marches a chunk of z-planes; the
 // ten working fields of planes z-2 .. z+2, each with a two-point x-y halo
@@ -794,6 +854,7 @@ __global__ void __launch_bounds__(kTX* kTY, sizeof(T) == 4 ? 2 : 1)
 constexpr int kMX = 32, kMY = 8, kMThreads = kMX * kMY;
 constexpr int kBX = kMX + 8, kBY = kMY + 4, kBPlane = kBX * kBY;
 constexpr int kMSlots = 6, kMZChunk = 64;
+constexpr int kMBlocks = kMY == 8 ? 2 : 1;  // resident blocks per SM the ring allows
 constexpr unsigned kMSlotBytes = kNF * kBPlane * 4;  // 19200, a multiple of 128
 // All of a block's shared memory is dynamic: the ring (6 x 19200 bytes, first,
 // so that it starts on the 128-byte boundary the TMA destination needs), the
@@ -956,7 +1017,7 @@ __device__ __forceinline__ bool tma_ring_aligned(const unsigned char* raw, int* 
 }
 
 template <bool RESID>
-__global__ void __launch_bounds__(kMThreads, 2)
+__global__ void __launch_bounds__(kMThreads, kMBlocks)
     k_ra_tma(const __grid_constant__ CUtensorMap map, Grid g, Coef<float> k, Phys ph, RKStage rk,
              const df64* __restrict__ Q64, df64* __restrict__ out, df64* __restrict__ Qs,
              float* __restrict__ Wnext, int* __restrict__ err, int zlen, int skip_plane) {
@@ -988,10 +1049,10 @@ struct TmaItem {
 };
 // Two blocks per SM need 2 x (ring + item, in 128-byte units) + 2 x 1 KB of the
 // SM's 228 KB: the item may take at most 464 bytes beside the 115,248-byte ring.
-static_assert(sizeof(TmaItem) <= 464, "TmaItem too large for two batched TMA blocks per SM");
+static_assert(kMBlocks == 1 || sizeof(TmaItem) <= 464, "TmaItem too large for two batched TMA blocks per SM");
 
 template <bool RESID>
-__global__ void __launch_bounds__(kMThreads, 2)
+__global__ void __launch_bounds__(kMThreads, kMBlocks)
     k_batch_ra_tma(const BatchInst<float>* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
                    int stage, int parity, int* __restrict__ err, int zlen) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1926,8 +1987,8 @@ __global__ void k_check_finite(const double* __restrict__ x, long long m, int* _
 static inline int blocks_for(int n, int threads) { return (n + threads - 1) / threads; }
 
 cudaError_t launch_tgv_ic(const Grid& g, const Phys& ph, double hx, double hy, double hz, double* Q,
-                          cudaStream_t st) {
-    k_tgv_ic<<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, hx, hy, hz, Q);
+                          cudaStream_t st, int z0, int nz_period) {
+    k_tgv_ic<<<blocks_for(g.n, 256), 256, 0, st>>>(g, ph, hx, hy, hz, z0, nz_period > 0 ? nz_period : g.nz, Q);
     return cudaGetLastError();
 }
 
@@ -2023,7 +2084,7 @@ int tma_zchunk(const Grid& g) {
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long tiles = (long long)((g.nx + kMX - 1) / kMX) * ((g.ny + kMY - 1) / kMY);
     for (int z : {64, 32, 16})
-        if (tiles * ((g.nz + z - 1) / z) >= 12LL * 2 * sms) return z;
+        if (tiles * ((g.nz + z - 1) / z) >= 12LL * kMBlocks * sms) return z;
     return 8;
 }
 
@@ -2139,6 +2200,15 @@ cudaError_t launch_ss(const Grid& g, const Coef<T>& k, const Phys& ph, const RKS
         else
             k_ss<T, false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Qf, Wf, Gw, Q64, out, Qs, Wnext);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ra_inline(const Grid& g, const Coef<double>& k, const Phys& ph, const RKStage& rk, bool resid,
+                             const double* Q64, double* out, double* Qs, cudaStream_t st) {
+    if (resid)
+        k_ra_inline<true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Q64, out, Qs);
+    else
+        k_ra_inline<false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, k, ph, rk, Q64, out, Qs);
     return cudaGetLastError();
 }
 

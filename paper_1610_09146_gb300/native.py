@@ -26,6 +26,7 @@ FD_STORE_SOME = 1
 FD_RECOMPUTE_ALL = 2
 FD_RECOMPUTE_SOME = 3
 FD_STORE_NONE = 4
+FD_RECOMPUTE_ALL_INLINE = 5
 
 FD_F64 = 0
 FD_F32_ACCDW = 1
@@ -133,6 +134,13 @@ _SIGS = {
     "fd_server_cancel": (ctypes.c_int, [_vp, ctypes.c_longlong]),
     "fd_server_tick": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "fd_server_poll": (ctypes.c_int, [_vp, ctypes.POINTER(FdResult), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "fd_slab_ghost_planes": (ctypes.c_int, [ctypes.c_int]),
+    "fd_slab_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(FdAlloc), _vp]),
+    "fd_get_planes_async": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int]),
+    "fd_set_planes_async": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int]),
     "fd_fp64_peak": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), _vp, ctypes.c_size_t]),
     "fd_server_get_state": (ctypes.c_int, [_vp, ctypes.c_longlong, _vp, ctypes.c_size_t, ctypes.c_int]),
     "fd_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(FdServerStats)]),
@@ -191,6 +199,29 @@ def fd_create(nx, ny, nz, Re, Mach, Pr, gamma, dt, algorithm, dtype, alloc=None,
                           _vp(stream or None))
     _check(rc, None)
     return h.value
+
+
+def fd_slab_ghost_planes(algorithm):
+    return load().fd_slab_ghost_planes(algorithm)
+
+
+def fd_slab_create(nx, ny, nz_global, z_first, nz_local, ghost, Re, Mach, Pr, gamma, dt, algorithm, dtype,
+                   alloc=None, stream=0):
+    """Handle of a z-slab (fd_slab_create); returns it as an opaque integer."""
+    h = _vp()
+    ap = ctypes.byref(alloc) if alloc is not None else None
+    rc = load().fd_slab_create(ctypes.byref(h), nx, ny, nz_global, z_first, nz_local, ghost, Re, Mach, Pr, gamma, dt,
+                               algorithm, dtype, ap, _vp(stream or None))
+    _check(rc, None)
+    return h.value
+
+
+def fd_get_planes_async(h, z, count, dst, dst_is_device=1):
+    return _check(load().fd_get_planes_async(h, z, count, dst, dst_is_device), h)
+
+
+def fd_set_planes_async(h, z, count, src, src_is_device=1):
+    return _check(load().fd_set_planes_async(h, z, count, src, src_is_device), h)
 
 
 def fd_step(h, n):

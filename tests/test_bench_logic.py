@@ -96,3 +96,23 @@ def test_clock_sampler_reads_the_timed_windows_only():
 def test_clock_sampler_without_nvidia_smi():
     c = bench.ClockSampler()
     assert c.stop() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_roofline_entry_for_the_mixed_kernel_is_on_the_issue_slots():
+    n = 256**3
+    kern = {"grad": {"ms_total": 3.5, "launches": 10, "ms_avg": 0.35},
+            "fused": {"ms_total": 36.0, "launches": 10, "ms_avg": 3.6}}
+    e = bench.roofline_of("f64dw", "store_some", kern, n, 6787.2, "measured", fp64_peak=1.25)
+    sec = 3.6e-3
+    flops, nbytes, instr = bench.cost_of("f64dw", "store_some", "fused")
+    assert e["bound"] == "alu" and e["unit"] == "Tinst/s"
+    assert e["peak"] == pytest.approx(152 * 4 * 32 * 2.07e9 / 1e12, rel=1e-3)
+    assert e["achieved"] == pytest.approx(bench.ISSUE_COST[("f64dw", "store_some", "fused")] * n / sec / 1e12,
+                                          rel=1e-3)
+    assert e["frac"] == pytest.approx(e["achieved"] / e["peak"], rel=1e-3)
+    assert e["binary64_equivalent_tflops"] == pytest.approx(flops * n / sec / 1e12, rel=1e-3)
+    assert e["fp64_pipe_frac"] == pytest.approx(instr * n / sec / (1.25e12 / 2), rel=1e-3)
+    assert e["hbm_frac"] == pytest.approx(nbytes * n / sec / 1e9 / 6787.2, rel=1e-3)
+    # the measured binary64 peak replaces the nominal one for the binary64 families
+    e64 = bench.roofline_of("f64", "store_some", kern, n, 6787.2, "measured", fp64_peak=1.25)
+    assert e64["peak"] == 1.25 and "measured" in e64["peak_source"]
