@@ -42,7 +42,8 @@ N_GRID = 256
 RE, MACH, PR, GAMMA = 1600.0, 0.1, 0.71, 1.4
 METRIC = "point-updates/s"
 VARIANTS = ["store_all", "store_some", "recompute_all", "recompute_some", "store_none"]
-SHORT = {"store_all": "BL", "store_some": "SS", "recompute_all": "RA", "recompute_some": "RS", "store_none": "SN"}
+SHORT = {"store_all": "BL", "store_some": "SS", "recompute_all": "RA", "recompute_some": "RS", "store_none": "SN",
+         "recompute_all_inline": "RAI"}
 
 # Table 1 (Section 4): run-time in seconds of 500 iterations at 256^3 on one 24-core
 # ARCHER node (24 MPI ranks, Cray C -O3, binary64).  Context only, another machine.
@@ -115,6 +116,10 @@ COST = {
     # (the binary64 SS kernel's); bytes per point read F (10 double-words) + W64 (u, v, w, p) +
     # G (9 double-words) + the saved register, write the state, the saved register (stages 0
     # and 1), F and W64 of the next stage; binary64 instructions counted from the source
+    # binary64 recompute-all with the primitives recomputed at every tap (no primitive arrays):
+    # bytes per point read the state taps once and the saved register, write the state and
+    # the saved register; flops / instructions from ncu at 160^3 (DADD + DMUL + 2 DFMA)
+    ("f64", "recompute_all_inline", "fused"): (3095.7, 133.3, 1774.3),
     ("f64dw", "store_some", "fused"): (401.7, 402.7, 51.3),
     ("f64dw", "store_some", "grad"): (45, 96, 0),
     ("f64dw", "*", "prims"): (14, 200, 17),
@@ -673,7 +678,8 @@ def run_sweep(args):
     fd.build()
     hbm_peak, hbm_src = measured_peaks()
     stream = torch.cuda.Stream()
-    cases = [("f64", a) for a in VARIANTS] + [("f32", "recompute_all"), ("f32", "store_some"),
+    cases = [("f64", a) for a in VARIANTS] + [("f64", "recompute_all_inline"), ("f64dw", "store_some"),
+                                              ("f32", "recompute_all"), ("f32", "store_some"),
                                               ("df64", "store_some"), ("df64", "store_none")]
     out = {}
     for n in args.sizes:
