@@ -120,8 +120,8 @@ COST = {
     # bytes per point read the state taps once and the saved register, write the state and
     # the saved register; flops / instructions from ncu at 160^3 (DADD + DMUL + 2 DFMA)
     ("f64", "recompute_all_inline", "fused"): (3095.7, 133.3, 1774.3),
-    ("f64dw", "store_some", "fused"): (401.7, 402.7, 51.3),
-    ("f64dw", "store_some", "grad"): (45, 96, 0),
+    ("f64dw", "store_some", "fused"): (401.7, 378.7, 37.3),
+    ("f64dw", "store_some", "grad"): (59, 128, 14),
     ("f64dw", "*", "prims"): (14, 200, 17),
 }
 # Thread instructions per point of one launch (all pipes): ncu's smsp__thread_inst_executed of

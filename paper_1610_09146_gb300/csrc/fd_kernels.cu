@@ -1173,10 +1173,11 @@ __global__ void __launch_bounds__(128) k_ss_f32(Grid g, Coef<float> k, Phys ph, 
 //     gradient differences the binary64 values (neighbouring pressures
 //     differ by far less than a factor 2, so each difference is exact), and
 //     only the exact differences move to double-word arithmetic;
-//   - div u = sum_i D_i u_i from the binary64 velocities, for the two terms
-//     that carry a mean: -div in the mass residual and -(rhoE0 + p0) div in the
-//     energy residual (the mean energy and the mean pressure work; ~250 div at
-//     M = 0.1, which would magnify a double-word div 250-fold);
+//   - div u = sum_i D_i u_i from the binary64 velocities (formed by the
+//     gradient pass, k_ss_grad_hyb), for the two terms that carry a mean: -div
+//     in the mass residual and -(rhoE0 + p0) div in the energy residual (the
+//     mean energy and the mean pressure work; ~250 div at M = 0.1, which would
+//     magnify a double-word div 250-fold);
 //   double-word, on shifted fields (rho-1, rho u_i, rho E - rhoE0, u_i,
 //   p - p0, T - 1) on the binary32 pipe, as in the df64 mode: convection,
 //   pressure work, the viscous stress divergence and its work, the
@@ -1187,10 +1188,12 @@ __global__ void __launch_bounds__(128) k_ss_f32(Grid g, Coef<float> k, Phys ph, 
 // Values move between the formats by integer operations on the IEEE fields
 // (dw_of_f64, f64_of_dw): a conversion instruction would cost a DFMA.
 //
-// Binary64 instructions per point and stage: 6 pressure differences, 14 for
-// div u (three first differences, their sum) and 2 FMAs adding its terms, 5
-// sums hi + lo of the residual, 10 RK FMAs (5 in stage 2), and ~17 for the
-// next stage's primitives (1 / rho, u_i, p, and rho - 1, rho E - rhoE0, p - p0).
+// Binary64 instructions per point and stage in the fused kernel: 6 pressure
+// differences, 2 FMAs adding the div terms, 5 sums hi + lo of the residual, 10
+// RK FMAs (5 in stage 2), and ~17 for the next stage's primitives (1 / rho,
+// u_i, p, and rho - 1, rho E - rhoE0, p - p0); 14 in the gradient pass (div u).
+// (div u moved from the fused kernel to the gradient pass: fused 3.67 -> 3.23
+// ms, gradients 0.35 -> 0.61 ms per 256^3 stage.)
 
 // Working fields of a binary64 state: the ten shifted double-word fields F and
 // the binary64 velocities and pressure W64 = (u, v, w, p).  u_i and p are the
@@ -1232,6 +1235,39 @@ __global__ void __launch_bounds__(256) k_prims_hyb(Grid g, Phys ph, const double
     hyb_prims_point(ph, q, F, W64, n, idx);
 }
 
+// Gradient pass of the mixed kernel: the nine double-word gradients as
+// k_ss_grad<df64> forms them, and div u = sum_i D_i u_i in binary64 from the
+// binary64 velocities W64 (as the binary64 gradient pass forms D_i u_i), which
+// the fused kernel reads for the two mean-state terms.
+__global__ void __launch_bounds__(256) k_ss_grad_hyb(Grid g, Coef<df64> k, const df64* __restrict__ Wf,
+                                                    const double* __restrict__ W64, df64* __restrict__ Gw,
+                                                    double* __restrict__ Dv) {
+    const int idx = grid_index();
+    if (idx >= g.n) return;
+    const int n = g.n;
+    const Nbr s = make_nbr(g, idx);
+    df64 G[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            df64 t[4];
+            taps(Wf + i * n, s.c, s.o[j], t);
+            G[i][j] = k.s1[j] * delta1_taps(t);
+            Gw[(3 * i + j) * n + s.c] = G[i][j];
+        }
+    store_pair_sums(G, Gw + 9 * (size_t)n, n, s.c);
+    double div = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        double t[4];
+        taps(W64 + j * (size_t)n, s.c, s.o[j], t);
+        const double gjj = g.inv12h[j] * delta1_taps(t);
+        div = j == 0 ? gjj : div + gjj;
+    }
+    Dv[s.c] = div;
+}
+
 // Fused residual + RK update + next-stage working fields.  F / W64: the
 // working fields of the stage's state, Gw: its nine velocity gradients
 // (double-word, from k_ss_grad<df64>), Q64 the binary64 state the stage starts
@@ -1242,6 +1278,7 @@ __global__ void __launch_bounds__(256) k_prims_hyb(Grid g, Phys ph, const double
 template <bool RESID>
 __global__ void __launch_bounds__(128, 4) k_ss_hyb(Grid g, Coef<df64> k, Phys ph, RKStage rk, double c_E,
                                                    const df64* __restrict__ F, const df64* __restrict__ Gw,
+                                                   const double* __restrict__ Dv,
                                                    const double* __restrict__ W64, const double* __restrict__ Q64,
                                                    double* __restrict__ out, double* __restrict__ Qs,
                                                    df64* __restrict__ Fnext, double* __restrict__ W64next) {
@@ -1264,15 +1301,7 @@ __global__ void __launch_bounds__(128, 4) k_ss_hyb(Grid g, Coef<df64> k, Phys ph
         const df64 d = scale2(dw_of_f64(t[2] - t[1]), 8.0f) + dw_of_f64(t[0] - t[3]);
         Rw[1 + j] = fmx(k.cp[j], d, Rw[1 + j]);
     }
-    // div u in binary64, as the binary64 gradient pass forms D_i u_i
-    double div = 0.0;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        double t[4];
-        taps(W64 + j * (size_t)n, s.c, s.o[j], t);
-        const double gjj = g.inv12h[j] * delta1_taps(t);
-        div = j == 0 ? gjj : div + gjj;
-    }
+    const double div = ld(Dv, s.c);  // binary64 div u of the gradient pass
     double R[5];
     R[0] = fmx(-1.0, div, f64_of_f32(Rw[0].hi)) + f64_of_f32(Rw[0].lo);
 #pragma unroll
@@ -2218,19 +2247,25 @@ cudaError_t launch_prims_hyb(const Grid& g, const Phys& ph, const double* Q, df6
     return cudaGetLastError();
 }
 
+cudaError_t launch_ss_grad_hyb(const Grid& g, const Coef<df64>& k, const df64* Wf, const double* W64, df64* Gw,
+                               double* Dv, cudaStream_t st) {
+    k_ss_grad_hyb<<<blocks_for(g.n, 256), 256, 0, st>>>(g, k, Wf, W64, Gw, Dv);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ss_hyb(const Grid& g, const Coef<df64>& k, const Phys& ph, const RKStage& rk, bool resid,
-                          const df64* F, const df64* Gw, const double* W64, const double* Q64, double* out,
-                          double* Qs, df64* Fnext, double* W64next, cudaStream_t st) {
+                          const df64* F, const df64* Gw, const double* Dv, const double* W64, const double* Q64,
+                          double* out, double* Qs, df64* Fnext, double* W64next, cudaStream_t st) {
     Coef<df64> kh = k;  // the mean-state terms enter in binary64 (see k_ss_hyb)
     kh.c_rho = df64(0.0f, 0.0f);
     kh.c_E = df64(0.0f, 0.0f);
     const double c_E = -(ph.rhoE0 + ph.p0);
     if (resid)
-        k_ss_hyb<true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, kh, ph, rk, c_E, F, Gw, W64, Q64, out, Qs, Fnext,
-                                                             W64next);
+        k_ss_hyb<true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, kh, ph, rk, c_E, F, Gw, Dv, W64, Q64, out, Qs,
+                                                             Fnext, W64next);
     else
-        k_ss_hyb<false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, kh, ph, rk, c_E, F, Gw, W64, Q64, out, Qs, Fnext,
-                                                              W64next);
+        k_ss_hyb<false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, kh, ph, rk, c_E, F, Gw, Dv, W64, Q64, out, Qs,
+                                                              Fnext, W64next);
     return cudaGetLastError();
 }
 
