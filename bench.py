@@ -113,22 +113,24 @@ COST = {
     ("df64", "store_all", "products"): (18, 216, 0),
     ("df64", "*", "prims"): (14, 120, 0),
     # mixed binary64 / double-word store-some (dtype f64dw): flops are the binary64 algorithm's
-    # (the binary64 SS kernel's); bytes per point read F (10 double-words) + W64 (u, v, w, p) +
-    # G (9 double-words) + the saved register, write the state, the saved register (stages 0
-    # and 1), F and W64 of the next stage; binary64 instructions counted from the source
+    # (the binary64 SS kernel's); the fused kernel's bytes per point read F (10 double-words),
+    # the binary64 p, G (9 double-words), div u and the saved register, and write the state,
+    # the saved register (stages 0 and 1), F and W64 = (u, v, w, p) of the next stage; the
+    # gradient pass reads u_i as double-words and in binary64 and writes G and div u.
+    # Binary64 instructions per point from ncu at 160^3
     # binary64 recompute-all with the primitives recomputed at every tap (no primitive arrays):
     # bytes per point read the state taps once and the saved register, write the state and
     # the saved register; flops / instructions from ncu at 160^3 (DADD + DMUL + 2 DFMA)
     ("f64", "recompute_all_inline", "fused"): (3095.7, 133.3, 1774.3),
-    ("f64dw", "store_some", "fused"): (401.7, 378.7, 37.3),
+    ("f64dw", "store_some", "fused"): (401.7, 386.7, 37.3),
     ("f64dw", "store_some", "grad"): (59, 128, 14),
     ("f64dw", "*", "prims"): (14, 200, 17),
 }
 # Thread instructions per point of one launch (all pipes): ncu's smsp__thread_inst_executed of
-# the kernel at 160^3, mean of stages 0-2 (16.04, 16.16, 16.17e9 / 4.096e6 points); the
-# issue-slot cost of the mixed kernel.  Its binary64 instructions (DADD 23, DFMA 22/22/17,
-# DMUL 8 per point) give the 51.3 of the cost table.
-ISSUE_COST = {("f64dw", "store_some", "fused"): 3936.0}
+# the kernel at 160^3, mean of stages 0-2 (3824, 3819, 3789 per point); the issue-slot cost of
+# the mixed kernel.  Its binary64 instructions (DADD 15, DMUL 5, DFMA 19/19/14 per point) give
+# the 37.3 of the cost table.
+ISSUE_COST = {("f64dw", "store_some", "fused"): 3811.0}
 # FP64 pipe issue peak: 2 instructions per SM per clock.
 FP64_PEAK_INSTR = 152 * 2 * 2.07e9
 
@@ -288,9 +290,11 @@ def roofline_of(dtype, alg, kern, n, hbm_peak, hbm_src, fp64_peak=None):
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch at 256^3, from ncu captures of the
 # current kernels: binary64 SS fused on a 160^3 grid (three launches, 291 / 332 / 294 B per
-# point by stage) scaled by the point count; binary32 RA (TMA-staged) at 256^3 itself (mean
-# of the three stages' launches: 3.44, 3.43, 2.76 GB).  None where no capture exists.
-TRAFFIC = {("f64", "store_some", "fused"): 5.12e9, ("f32", "recompute_all", "fused"): 3.21e9}
+# point by stage) scaled by the point count; the mixed SS fused likewise (401 / 400 / 360 B per
+# point at 160^3); binary32 RA (TMA-staged) at 256^3 itself (mean of the three stages'
+# launches: 3.44, 3.43, 2.76 GB).  None where no capture exists.
+TRAFFIC = {("f64", "store_some", "fused"): 5.12e9, ("f32", "recompute_all", "fused"): 3.21e9,
+           ("f64dw", "store_some", "fused"): 6.49e9}
 
 
 def e2e_run(fd, torch, alg, dtype, n, steps, nsolvers=2):
@@ -485,6 +489,7 @@ def batched_extra(fd, args):
                         "100 RK3 steps, seed 1610; binary32 batch (recompute-all)",
             "solves_per_s": r["value"], "fp64_loop_solves_per_s": r["fp64_loop"]["solves_per_s"],
             "fp64_batched_solves_per_s": r["fp64_batched"]["solves_per_s"],
+            "f64dw_batched_solves_per_s": r["f64dw_batched"]["solves_per_s"],
             "fp64_batched_equals_loop": r["fp64_batched"]["ke_bitwise_equal_to_loop"],
             "speedup_vs_fp64_loop": r["speedup_vs_fp64_loop"], "ke_rel_err_vs_fp64_max": r["ke_rel_err_vs_fp64"]["max"]}
 
@@ -496,11 +501,13 @@ def serve_extra(fd, args):
     reqs = workloads.requests(count=args.serve_requests, rate=20.0)
     for q in reqs:
         q["algorithm"] = "recompute_all" if q["dtype"] == "f32" else "store_some"
+        if q["dtype"] == "f64":  # binary64 requests run the mixed form (binary64 parity, 2x faster)
+            q["dtype"] = "f64dw"
         q["tile_points"] = 0
         q["tag"] = q["id"]
     r = serve_summary(fd, reqs, 20.0, 64, 256)
     return {"workload": f"first {len(reqs)} requests of the Poisson stream (mean 20/s, seed 9146), grids 48^3-192^3, "
-                        "50-500 RK3 steps, f32 (RA) or f64 (SS) per request",
+                        "50-500 RK3 steps, f32 (RA) or f64 (mixed binary64 / double-word SS) per request",
             "solves_per_s": r["value"], "latency_p50_s": r["latency_s"]["p50"],
             "latency_p99_s": r["latency_s"]["p99"], "offered_over_capacity": r["offered_over_capacity"],
             "completed_ok": r["completed_ok"], "span_s": r["span_s"]}
@@ -544,6 +551,8 @@ def batched_summary(fd, specs, steps, tuned):
     tl, ke64 = loop64()
     # binary64 batch of the same solves (store-some everywhere): bitwise the loop's results
     t64b, ke64b, _ = batched("f64", [dict(s, algorithm="store_some", tile_points=1024) for s in specs])
+    # the mixed binary64 / double-word batch (binary64 parity) of the same solves
+    tdw, kedw, _ = batched("f64dw", [dict(s, algorithm="store_some", tile_points=1024) for s in specs])
     kerr = np.abs(ke32 - ke64) / ke64
     pts = sum(s["n"] ** 3 for s in specs)
     return {
@@ -553,6 +562,8 @@ def batched_summary(fd, specs, steps, tuned):
         "fp64_loop": {"solves_per_s": len(specs) / tl, "seconds": tl, "family": "store_some"},
         "fp64_batched": {"solves_per_s": len(specs) / t64b, "seconds": t64b,
                          "ke_bitwise_equal_to_loop": bool(np.array_equal(ke64b, ke64))},
+        "f64dw_batched": {"solves_per_s": len(specs) / tdw, "seconds": tdw,
+                          "ke_rel_err_vs_fp64_max": float(np.max(np.abs(kedw - ke64) / ke64))},
         "speedup_vs_fp64_loop": tl / tb,
         "ke_rel_err_vs_fp64": {"max": float(kerr.max()), "median": float(np.median(kerr))},
     }
@@ -853,14 +864,20 @@ def run_serve(args):
     # family and tile per (grid, dtype) from the autotuner (cached between runs)
     best = {}
     for r in reqs:
+        r["tag"] = r["id"]
+        if r["dtype"] == "f64" and not args.plain_f64:
+            # binary64 requests run the mixed form (binary64 parity, store-some only)
+            r["dtype"], r["algorithm"], r["tile_points"] = "f64dw", "store_some", 0
+            continue
         k = (r["n"], r["dtype"])
         if k not in best:
             fam, tile, ms = autotune.tune(r["n"], r["dtype"])
             best[k] = (fam, tile, ms)
         r["algorithm"], r["tile_points"] = best[k][0], best[k][1]
-        r["tag"] = r["id"]
     line = {"workload": f"serving: {len(reqs)} Poisson requests (mean {args.rate}/s, seed 9146), grids 48^3-192^3, "
-                        "50-500 RK3 steps, Re U[400,3200], Mach U[0.1,0.4], f32 or f64 per request"}
+                        "50-500 RK3 steps, Re U[400,3200], Mach U[0.1,0.4], f32 or f64 per request"
+                        + (" (f64 on the plain binary64 kernels)" if args.plain_f64 else
+                           " (f64 on the mixed binary64 / double-word store-some kernels)")}
     line |= serve_summary(fd, reqs, args.rate, args.arena_gb, args.max_active)
     line["autotune"] = {f"{n}|{d}": {"family": f, "tile_points": t} for (n, d), (f, t, _) in sorted(best.items())}
     print(json.dumps(line), flush=True)
@@ -918,6 +935,8 @@ def main():
     ap.add_argument("--no-f64dw", action="store_true", help="skip the mixed binary64 / double-word store-some form")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving records of the line")
     ap.add_argument("--serve-requests", type=int, default=40, help="requests in the line's serving record")
+    ap.add_argument("--plain-f64", action="store_true",
+                    help="serve binary64 requests with the plain binary64 kernels instead of the mixed form")
     ap.add_argument("--workload", choices=["single", "batched", "serve", "mixed512", "history", "sweep"],
                     default="single",
                     help="single: the 256^3 line (default); batched / serve / mixed512: the ensemble, "

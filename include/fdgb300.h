@@ -256,7 +256,8 @@ typedef struct fd_instance_desc {
 typedef struct fd_batch fd_batch;
 
 /* Create `count` >= 1 instances described by desc[0..count-1], all in one
- * dtype (FD_F64 or FD_F32_ACCDW), each set to its Taylor-Green initial state.
+ * dtype (FD_F64, FD_F32_ACCDW, or FD_F64_DW with every instance store-some),
+ * each set to its Taylor-Green initial state.
  * One device allocation holds every instance (through alloc, else
  * cudaMalloc).  Errors: FD_EINVAL (a bad descriptor; FD_STORE_ALL is not
  * batched), FD_ENOMEM, FD_ECUDA; the message is in fd_batch_last_error(NULL). */
@@ -312,7 +313,7 @@ typedef struct fd_request {
     int nx, ny, nz;                  /* grid, as for fd_create */
     double Re, Mach, Pr, gamma, dt;  /* as for fd_create */
     int steps;                       /* RK3 steps to run, >= 1 */
-    int dtype;                       /* FD_F64 or FD_F32_ACCDW */
+    int dtype;                       /* FD_F64, FD_F32_ACCDW, or FD_F64_DW (store-some only) */
     int algorithm;                   /* FD_STORE_SOME or FD_RECOMPUTE_ALL */
     int tile_points;                 /* as in fd_instance_desc */
     long long tag;                   /* caller's identifier, returned with the result */

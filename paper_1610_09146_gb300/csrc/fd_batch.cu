@@ -53,7 +53,12 @@ struct InstHost {
     int n;
     bool padded;                   // TMA-staged binary32 RA: ghost-padded working fields
     size_t q0, q1, qs, w0, w1, g;  // byte offsets in the allocation
+    // FD_F64_DW: w0 / w1 hold the double-word fields F; binary64 u, v, w, p and div u here
+    size_t w64_0 = (size_t)-1, w64_1 = (size_t)-1, dv = (size_t)-1;
 };
+
+// The binary32 mode keeps a double-word state; binary64 and the mixed mode a binary64 one.
+bool dw_state(int dtype) { return dtype == FD_F32_ACCDW; }
 
 }  // namespace
 
@@ -127,6 +132,32 @@ void fill_inst(const fd_batch* b, std::vector<fd::BatchInst<T>>& out) {
         I.G = h.g == (size_t)-1 ? nullptr : reinterpret_cast<T*>(b->base() + h.g);
         I.padded = h.padded ? 1 : 0;
         for (int s = 0; s < 3; ++s) I.rk[s] = fd::make_stage(s, h.d.dt);
+    }
+}
+
+// Instance records of a mixed (FD_F64_DW) batch.
+void fill_hyb(const fd_batch* b, std::vector<fd::BatchHyb>& out) {
+    out.resize(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        const InstHost& h = b->inst[i];
+        fd::BatchHyb& I = out[i];
+        std::memset(&I, 0, sizeof I);
+        I.g = fd::make_grid(h.d.nx, h.d.ny, h.d.nz);
+        I.ph = fd::make_phys(h.d.Re, h.d.Mach, h.d.Pr, h.d.gamma);
+        I.k = fd::make_coef<fd::df64>(I.g, I.ph, true);
+        I.k.c_rho = fd::df64(0.0f, 0.0f);  // the mean-state terms enter in binary64
+        I.k.c_E = fd::df64(0.0f, 0.0f);
+        I.c_E = -(I.ph.rhoE0 + I.ph.p0);
+        for (int s = 0; s < 3; ++s) I.rk[s] = fd::make_stage(s, h.d.dt);
+        I.Q[0] = reinterpret_cast<double*>(b->base() + h.q0);
+        I.Q[1] = reinterpret_cast<double*>(b->base() + h.q1);
+        I.Qs = reinterpret_cast<double*>(b->base() + h.qs);
+        I.F[0] = reinterpret_cast<fd::df64*>(b->base() + h.w0);
+        I.F[1] = reinterpret_cast<fd::df64*>(b->base() + h.w1);
+        I.W64[0] = reinterpret_cast<double*>(b->base() + h.w64_0);
+        I.W64[1] = reinterpret_cast<double*>(b->base() + h.w64_1);
+        I.G = reinterpret_cast<fd::df64*>(b->base() + h.g);
+        I.Dv = reinterpret_cast<double*>(b->base() + h.dv);
     }
 }
 
@@ -204,7 +235,23 @@ cudaError_t enqueue_step(fd_batch* b, int p, cudaStream_t st0, cudaStream_t st1)
     return cudaSuccess;
 }
 
+// Mixed store-some batch (FD_F64_DW): three stages of gradients then fused.
+cudaError_t enqueue_step_hyb(fd_batch* b, int p, cudaStream_t st) {
+    auto* I = static_cast<const fd::BatchHyb*>(b->d_inst);
+    cudaError_t e;
+    for (int s = 0, q = p; s < 3; ++s, q ^= 1) {
+        e = b->prof.timed(st, FD_KERNEL_GRAD,
+                          [&] { return fd::launch_batch_grad_hyb(I, b->d_ss, b->n_ss, q, b->grid_grad, st); });
+        if (e != cudaSuccess) return e;
+        e = b->prof.timed(st, FD_KERNEL_FUSED,
+                          [&] { return fd::launch_batch_ss_hyb(I, b->d_ss, b->n_ss, s, q, b->grid_ss_fused, st); });
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t step_direct(fd_batch* b, int p) {
+    if (b->dtype == FD_F64_DW) return enqueue_step_hyb(b, p, b->stream);
     return b->dtype == FD_F64 ? enqueue_step<double>(b, p, b->stream, nullptr)
                               : enqueue_step<float>(b, p, b->stream, nullptr);
 }
@@ -220,8 +267,9 @@ cudaError_t build_graphs(fd_batch* b) {
     for (int p = 0; p < 2; ++p) {
         cudaGraph_t g = nullptr;
         if ((e = cudaStreamBeginCapture(b->cap[0], cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
-        cudaError_t le = b->dtype == FD_F64 ? enqueue_step<double>(b, p, b->cap[0], b->cap[1])
-                                            : enqueue_step<float>(b, p, b->cap[0], b->cap[1]);
+        cudaError_t le = b->dtype == FD_F64_DW ? enqueue_step_hyb(b, p, b->cap[0])
+                         : b->dtype == FD_F64  ? enqueue_step<double>(b, p, b->cap[0], b->cap[1])
+                                               : enqueue_step<float>(b, p, b->cap[0], b->cap[1]);
         e = cudaStreamEndCapture(b->cap[0], &g);
         if (le == cudaSuccess && e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[p], g, 0);
         if (g) cudaGraphDestroy(g);
@@ -266,6 +314,9 @@ int check_kernel_error(fd_batch* b, const char* what) {
 int ensure_prims(fd_batch* b) {
     if (b->wvalid) return FD_OK;
     cudaError_t e = b->prof.timed(b->stream, FD_KERNEL_PRIMS, [&] {
+        if (b->dtype == FD_F64_DW)
+            return fd::launch_batch_prims_hyb(static_cast<const fd::BatchHyb*>(b->d_inst), b->d_all, b->n_all,
+                                              b->parity, b->grid_prims, b->stream);
         if (b->dtype == FD_F64)
             return fd::launch_batch_prims<double>(static_cast<const fd::BatchInst<double>*>(b->d_inst), b->d_all,
                                                   b->n_all, b->parity, b->grid_prims, b->stream);
@@ -291,7 +342,8 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
     if (!out) return fail_global(FD_EINVAL, "fd_batch_create: out is NULL");
     *out = nullptr;
     if (!desc || count < 1) return fail_global(FD_EINVAL, "fd_batch_create: need count >= 1 descriptors");
-    if (dtype != FD_F64 && dtype != FD_F32_ACCDW) return fail_global(FD_EINVAL, "fd_batch_create: dtype %d", dtype);
+    if (dtype != FD_F64 && dtype != FD_F32_ACCDW && dtype != FD_F64_DW)
+        return fail_global(FD_EINVAL, "fd_batch_create: dtype %d", dtype);
     if (alloc && (!alloc->alloc || !alloc->free))
         return fail_global(FD_EINVAL, "fd_batch_create: allocator needs both alloc and free");
     for (int i = 0; i < count; ++i) {
@@ -302,6 +354,8 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
             return fail_global(FD_EINVAL, "fd_batch_create: instance %d: algorithm %d is not batched", i, d.algorithm);
         if (d.tile_points != 0 && d.tile_points < 32)
             return fail_global(FD_EINVAL, "fd_batch_create: instance %d: tile_points %d < 32", i, d.tile_points);
+        if (dtype == FD_F64_DW && d.algorithm != FD_STORE_SOME)
+            return fail_global(FD_EINVAL, "fd_batch_create: instance %d: FD_F64_DW batches are store-some only", i);
     }
     fd_batch* b = new (std::nothrow) fd_batch();
     if (!b) return fail_global(FD_ENOMEM, "fd_batch_create: host allocation failed");
@@ -330,7 +384,8 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
         delete b;
         return fail_global(FD_ECUDA, "fd_batch_create: cudaGetDevice: %s", cudaGetErrorString(e));
     }
-    const size_t tsize = dtype == FD_F64 ? sizeof(double) : sizeof(float);
+    const bool hyb = dtype == FD_F64_DW;
+    const size_t tsize = dtype == FD_F64 ? sizeof(double) : (hyb ? sizeof(fd::df64) : sizeof(float));
     const size_t wfields = dtype == FD_F64 ? 5 : 10;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -338,7 +393,9 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
         off += align256(bytes);
         return at;
     };
-    const size_t inst_bytes = dtype == FD_F64 ? sizeof(fd::BatchInst<double>) : sizeof(fd::BatchInst<float>);
+    const size_t inst_bytes = hyb                 ? sizeof(fd::BatchHyb)
+                              : dtype == FD_F64 ? sizeof(fd::BatchInst<double>)
+                                                : sizeof(fd::BatchInst<float>);
     size_t o_inst = take(inst_bytes * count);
     b->inst.resize(count);
     for (int i = 0; i < count; ++i) {
@@ -353,8 +410,15 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
         const size_t wpts = h.padded ? fd::padded_field_points(fd::make_grid(h.d.nx, h.d.ny, h.d.nz)) : (size_t)h.n;
         h.w0 = take(wfields * wpts * tsize);
         h.w1 = take(wfields * wpts * tsize);
-        const size_t garrays = dtype == FD_F64 ? fd::kGradArrays<double> : fd::kGradArrays<float>;
+        const size_t garrays = dtype == FD_F64 ? fd::kGradArrays<double>
+                               : hyb           ? fd::kGradArrays<fd::df64>
+                                               : fd::kGradArrays<float>;
         h.g = desc[i].algorithm == FD_STORE_SOME ? take(garrays * (size_t)h.n * tsize) : (size_t)-1;
+        if (hyb) {
+            h.w64_0 = take(4 * (size_t)h.n * sizeof(double));
+            h.w64_1 = take(4 * (size_t)h.n * sizeof(double));
+            h.dv = take((size_t)h.n * sizeof(double));
+        }
     }
     std::vector<fd::BatchTile> t_ss, t_ra, t_all;
     make_tiles(b, FD_STORE_SOME, false, t_ss);
@@ -395,7 +459,10 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     if (sms <= 0) sms = 152;
-    if (dtype == FD_F64) {
+    if (hyb) {
+        b->grid_ss_fused = sms * fd::batch_hyb_blocks_per_sm(2);
+        b->grid_grad = sms * fd::batch_hyb_blocks_per_sm(1);
+    } else if (dtype == FD_F64) {
         b->grid_ss_fused = grid_for<double>(sms, true, true);
         b->grid_ra_fused = grid_for<double>(sms, true, false);
         b->grid_grad = grid_for<double>(sms, false, false);
@@ -409,11 +476,16 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
         }
         b->grid_grad = grid_for<float>(sms, false, false);
     }
-    b->grid_prims = b->grid_grad;
+    b->grid_prims = hyb ? sms * fd::batch_hyb_blocks_per_sm(0) : b->grid_grad;
 
     // Instance table and tile lists (host staging is pageable; copies complete
     // before the synchronisation below).
-    if (dtype == FD_F64) {
+    if (hyb) {
+        std::vector<fd::BatchHyb> I;
+        fill_hyb(b, I);
+        e = cudaMemcpyAsync(b->d_inst, I.data(), I.size() * sizeof I[0], cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    } else if (dtype == FD_F64) {
         std::vector<fd::BatchInst<double>> I;
         fill_inst<double>(b, I);
         e = cudaMemcpyAsync(b->d_inst, I.data(), I.size() * sizeof I[0], cudaMemcpyHostToDevice, b->stream);
@@ -448,10 +520,10 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
         const InstHost& h = b->inst[i];
         fd::Grid g = fd::make_grid(h.d.nx, h.d.ny, h.d.nz);
         fd::Phys ph = fd::make_phys(h.d.Re, h.d.Mach, h.d.Pr, h.d.gamma);
-        double* ic = reinterpret_cast<double*>(b->base() + (dtype == FD_F64 ? h.q0 : h.qs));
+        double* ic = reinterpret_cast<double*>(b->base() + (dw_state(dtype) ? h.qs : h.q0));
         e = fd::launch_tgv_ic(g, ph, 2.0 * fd::kPi / h.d.nx, 2.0 * fd::kPi / h.d.ny, 2.0 * fd::kPi / h.d.nz, ic,
                               b->stream);
-        if (e == cudaSuccess && dtype != FD_F64)
+        if (e == cudaSuccess && dw_state(dtype))
             e = fd::launch_to_df64(ic, reinterpret_cast<fd::df64*>(b->base() + h.q0), h.n, state_shift(h), b->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -496,7 +568,7 @@ int fd_batch_get_state(fd_batch* b, int i, double* dst, size_t n_elems, int dst_
         return b->fail(FD_EINVAL, "fd_batch_get_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h.n);
     const char* src = b->base() + (b->parity ? h.q1 : h.q0);
     cudaError_t e = cudaSuccess;
-    if (b->dtype != FD_F64) {
+    if (dw_state(b->dtype)) {
         double* tmp = dst_is_device ? dst : reinterpret_cast<double*>(b->base() + h.qs);
         e = to_binary64(b, h, tmp);
         src = reinterpret_cast<const char*>(tmp);
@@ -518,10 +590,10 @@ int fd_batch_set_state(fd_batch* b, int i, const double* src, size_t n_elems, in
         return b->fail(FD_EINVAL, "fd_batch_set_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)h.n);
     b->wvalid = false;
     char* q = b->base() + (b->parity ? h.q1 : h.q0);
-    char* dst = b->dtype == FD_F64 ? q : b->base() + h.qs;
+    char* dst = dw_state(b->dtype) ? b->base() + h.qs : q;
     cudaError_t e = cudaMemcpyAsync(dst, src, n_elems * sizeof(double),
                                     src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess && b->dtype != FD_F64)
+    if (e == cudaSuccess && dw_state(b->dtype))
         e = fd::launch_to_df64(reinterpret_cast<const double*>(dst), reinterpret_cast<fd::df64*>(q), h.n,
                                state_shift(h), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -536,7 +608,7 @@ int fd_batch_diagnostics(fd_batch* b, double* ke, double* enstrophy) {
         const InstHost& h = b->inst[i];
         fd::Grid g = fd::make_grid(h.d.nx, h.d.ny, h.d.nz);
         const double* Q = reinterpret_cast<const double*>(b->base() + (b->parity ? h.q1 : h.q0));
-        if (b->dtype != FD_F64) {
+        if (dw_state(b->dtype)) {
             double* tmp = reinterpret_cast<double*>(b->base() + h.qs);
             e = to_binary64(b, h, tmp);
             Q = tmp;

@@ -127,6 +127,32 @@ struct BatchTile {
     int inst, start, count;
 };
 
+// One instance of a batch in the mixed binary64 / double-word store-some
+// arithmetic (FD_F64_DW): binary64 state, double-word working fields F,
+// binary64 u, v, w, p (W64), double-word gradients G and binary64 div u (Dv).
+// k is the df64 coefficient record with its mean-state terms zeroed (they
+// enter in binary64, c_E = -(rhoE0 + p0)).
+struct alignas(16) BatchHyb {
+    Grid g;
+    Coef<df64> k;
+    Phys ph;
+    RKStage rk[3];
+    double c_E;
+    double* Q[2];
+    double* Qs;
+    df64* F[2];
+    double* W64[2];
+    df64* G;
+    double* Dv;
+};
+int batch_hyb_blocks_per_sm(int kernel);  // 0: primitives, 1: gradients, 2: fused
+cudaError_t launch_batch_prims_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int parity, int grid,
+                                   cudaStream_t st);
+cudaError_t launch_batch_grad_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int parity, int grid,
+                                  cudaStream_t st);
+cudaError_t launch_batch_ss_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int stage, int parity,
+                                int grid, cudaStream_t st);
+
 template <class T>
 int batch_blocks_per_sm(bool fused, bool stored_g);
 

@@ -1239,11 +1239,9 @@ __global__ void __launch_bounds__(256) k_prims_hyb(Grid g, Phys ph, const double
 // k_ss_grad<df64> forms them, and div u = sum_i D_i u_i in binary64 from the
 // binary64 velocities W64 (as the binary64 gradient pass forms D_i u_i), which
 // the fused kernel reads for the two mean-state terms.
-__global__ void __launch_bounds__(256) k_ss_grad_hyb(Grid g, Coef<df64> k, const df64* __restrict__ Wf,
-                                                    const double* __restrict__ W64, df64* __restrict__ Gw,
-                                                    double* __restrict__ Dv) {
-    const int idx = grid_index();
-    if (idx >= g.n) return;
+__device__ __forceinline__ void ss_grad_hyb_point(const Grid& g, const Coef<df64>& k, const df64* __restrict__ Wf,
+                                                  const double* __restrict__ W64, df64* __restrict__ Gw,
+                                                  double* __restrict__ Dv, int idx) {
     const int n = g.n;
     const Nbr s = make_nbr(g, idx);
     df64 G[3][3];
@@ -1267,6 +1265,13 @@ __global__ void __launch_bounds__(256) k_ss_grad_hyb(Grid g, Coef<df64> k, const
     }
     Dv[s.c] = div;
 }
+__global__ void __launch_bounds__(256) k_ss_grad_hyb(Grid g, Coef<df64> k, const df64* __restrict__ Wf,
+                                                    const double* __restrict__ W64, df64* __restrict__ Gw,
+                                                    double* __restrict__ Dv) {
+    const int idx = grid_index();
+    if (idx >= g.n) return;
+    ss_grad_hyb_point(g, k, Wf, W64, Gw, Dv, idx);
+}
 
 // Fused residual + RK update + next-stage working fields.  F / W64: the
 // working fields of the stage's state, Gw: its nine velocity gradients
@@ -1276,14 +1281,12 @@ __global__ void __launch_bounds__(256) k_ss_grad_hyb(Grid g, Coef<df64> k, const
 // record with its two mean-state terms (c_rho, c_E) set to zero: those enter
 // here in binary64, with c_E = -(rhoE0 + p0).
 template <bool RESID>
-__global__ void __launch_bounds__(128, 4) k_ss_hyb(Grid g, Coef<df64> k, Phys ph, RKStage rk, double c_E,
-                                                   const df64* __restrict__ F, const df64* __restrict__ Gw,
-                                                   const double* __restrict__ Dv,
-                                                   const double* __restrict__ W64, const double* __restrict__ Q64,
-                                                   double* __restrict__ out, double* __restrict__ Qs,
-                                                   df64* __restrict__ Fnext, double* __restrict__ W64next) {
-    const int idx = grid_index();
-    if (idx >= g.n) return;
+__device__ __forceinline__ void ss_hyb_point(const Grid& g, const Coef<df64>& k, const Phys& ph, const RKStage& rk,
+                                             double c_E, const df64* __restrict__ F, const df64* __restrict__ Gw,
+                                             const double* __restrict__ Dv, const double* __restrict__ W64,
+                                             const double* __restrict__ Q64, double* __restrict__ out,
+                                             double* __restrict__ Qs, df64* __restrict__ Fnext,
+                                             double* __restrict__ W64next, int idx) {
     const int n = g.n;
     df64 Rw[5];
     {
@@ -1321,6 +1324,17 @@ __global__ void __launch_bounds__(128, 4) k_ss_hyb(Grid g, Coef<df64> k, Phys ph
         }
         hyb_prims_point(ph, qn, Fnext, W64next, n, s.c);
     }
+}
+template <bool RESID>
+__global__ void __launch_bounds__(128, 4) k_ss_hyb(Grid g, Coef<df64> k, Phys ph, RKStage rk, double c_E,
+                                                   const df64* __restrict__ F, const df64* __restrict__ Gw,
+                                                   const double* __restrict__ Dv,
+                                                   const double* __restrict__ W64, const double* __restrict__ Q64,
+                                                   double* __restrict__ out, double* __restrict__ Qs,
+                                                   df64* __restrict__ Fnext, double* __restrict__ W64next) {
+    const int idx = grid_index();
+    if (idx >= g.n) return;
+    ss_hyb_point<RESID>(g, k, ph, rk, c_E, F, Gw, Dv, W64, Q64, out, Qs, Fnext, W64next, idx);
 }
 
 // ------------------------------------------------------------------ BL
@@ -1721,15 +1735,14 @@ constexpr int kBatchFusedMinBlocks = sizeof(T) == sizeof(double) ? (STORED_G ? 3
 // The instance record of a work item, copied to shared memory by the whole
 // block in 16-byte pieces, and only when the item belongs to another instance
 // than the block's previous one (a block's items are mostly of one instance).
-template <class T>
-__device__ __forceinline__ void stage_inst(BatchInst<T>& I, const BatchInst<T>* __restrict__ insts, int inst,
-                                           int& cur) {
-    static_assert(sizeof(BatchInst<T>) % 16 == 0, "the record is copied in 16-byte pieces");
+template <class Rec>
+__device__ __forceinline__ void stage_inst(Rec& I, const Rec* __restrict__ insts, int inst, int& cur) {
+    static_assert(sizeof(Rec) % 16 == 0, "the record is copied in 16-byte pieces");
     if (inst == cur) return;
     __syncthreads();  // every thread is done with the previous record
     const int4* src = reinterpret_cast<const int4*>(insts + inst);
     int4* dst = reinterpret_cast<int4*>(&I);
-    for (int i = threadIdx.x; i < (int)(sizeof(BatchInst<T>) / 16); i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < (int)(sizeof(Rec) / 16); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
     cur = inst;
 }
@@ -1839,6 +1852,85 @@ __global__ void __launch_bounds__(256) k_batch_prims(const BatchInst<T>* __restr
             prims_point(I.ph, q, I.W[parity], n, c);
         }
     }
+}
+
+// Batched mixed store-some: the single-instance per-point code (hyb_prims_point,
+// ss_grad_hyb_point, ss_hyb_point) over the tile work lists, so a batched
+// instance evolves bitwise as it would alone.
+__global__ void __launch_bounds__(256) k_batch_prims_hyb(const BatchHyb* __restrict__ insts,
+                                                         const BatchTile* __restrict__ tiles, int ntiles,
+                                                         int parity) {
+    __shared__ BatchHyb I;
+    int cur = -1;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        stage_inst(I, insts, tl.inst, cur);
+        const int n = I.g.n;
+        for (int p = threadIdx.x; p < tl.count; p += blockDim.x) {
+            const int c = tl.start + p;
+            double q[5];
+#pragma unroll
+            for (int f = 0; f < 5; ++f) q[f] = I.Q[parity][f * n + c];
+            hyb_prims_point(I.ph, q, I.F[parity], I.W64[parity], n, c);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_batch_grad_hyb(const BatchHyb* __restrict__ insts,
+                                                        const BatchTile* __restrict__ tiles, int ntiles,
+                                                        int parity) {
+    __shared__ BatchHyb I;
+    int cur = -1;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        stage_inst(I, insts, tl.inst, cur);
+        for (int p = threadIdx.x; p < tl.count; p += blockDim.x)
+            ss_grad_hyb_point(I.g, I.k, I.F[parity] + 5 * (size_t)I.g.n, I.W64[parity], I.G, I.Dv, tl.start + p);
+    }
+}
+
+__global__ void __launch_bounds__(128, 3) k_batch_ss_hyb(const BatchHyb* __restrict__ insts,
+                                                         const BatchTile* __restrict__ tiles, int ntiles, int stage,
+                                                         int parity) {
+    __shared__ BatchHyb I;
+    int cur = -1;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        stage_inst(I, insts, tl.inst, cur);
+        for (int p = threadIdx.x; p < tl.count; p += blockDim.x)
+            ss_hyb_point<false>(I.g, I.k, I.ph, I.rk[stage], I.c_E, I.F[parity], I.G, I.Dv, I.W64[parity],
+                                I.Q[parity], I.Q[1 - parity], I.Qs, I.F[1 - parity], I.W64[1 - parity],
+                                tl.start + p);
+    }
+}
+
+int batch_hyb_blocks_per_sm(int kernel) {
+    int b = 0;
+    cudaError_t e = kernel == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_prims_hyb, 256, 0)
+                    : kernel == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_grad_hyb, 256, 0)
+                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_ss_hyb, 128, 0);
+    return e == cudaSuccess && b > 0 ? b : 1;
+}
+
+cudaError_t launch_batch_prims_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int parity, int grid,
+                                   cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    k_batch_prims_hyb<<<grid, 256, 0, st>>>(insts, tiles, ntiles, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_grad_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int parity, int grid,
+                                  cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    k_batch_grad_hyb<<<grid, 256, 0, st>>>(insts, tiles, ntiles, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_ss_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int stage, int parity,
+                                int grid, cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    k_batch_ss_hyb<<<grid, 128, 0, st>>>(insts, tiles, ntiles, stage, parity);
+    return cudaGetLastError();
 }
 
 int tiled_work_items(int nx, int ny, int nz) {

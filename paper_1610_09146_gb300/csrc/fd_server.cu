@@ -98,17 +98,23 @@ class Arena {
 struct Layout {
     size_t q0, q1, qs, w0, w1, g, total;
     bool padded;  // binary32 RA staged by TMA: ghost-padded working fields
+    // FD_F64_DW: w0 / w1 hold the double-word fields; binary64 u, v, w, p and div u here
+    size_t w64_0 = (size_t)-1, w64_1 = (size_t)-1, dv = (size_t)-1;
 };
+
+// Instance group of a request: 0 binary64, 1 binary32, 2 mixed binary64 / double-word.
+int group_of(int dtype) { return dtype == FD_F64 ? 0 : (dtype == FD_F32_ACCDW ? 1 : 2); }
 
 // tma: whether TMA staging may be used (a binary32 RA solve on a grid that
 // allows it then gets the ghost-padded working-field layout, a little larger).
 Layout layout_of(const fd_request& r, bool tma) {
     const size_t n = (size_t)r.nx * r.ny * r.nz;
-    const size_t t = r.dtype == FD_F64 ? sizeof(double) : sizeof(float);
+    const bool hyb = r.dtype == FD_F64_DW;
+    const size_t t = r.dtype == FD_F64 ? sizeof(double) : (hyb ? sizeof(fd::df64) : sizeof(float));
     const size_t wf = r.dtype == FD_F64 ? 5 : 10;
     Layout L{};
     const fd::Grid g = fd::make_grid(r.nx, r.ny, r.nz);
-    L.padded = tma && r.dtype != FD_F64 && r.algorithm == FD_RECOMPUTE_ALL && fd::tma_staging_ok(g);
+    L.padded = tma && r.dtype == FD_F32_ACCDW && r.algorithm == FD_RECOMPUTE_ALL && fd::tma_staging_ok(g);
     const size_t wpts = L.padded ? fd::padded_field_points(g) : n;
     size_t off = 0;
     auto take = [&](size_t b) {
@@ -121,8 +127,15 @@ Layout layout_of(const fd_request& r, bool tma) {
     L.qs = take(5 * n * sizeof(double));
     L.w0 = take(wf * wpts * t);
     L.w1 = take(wf * wpts * t);
-    const size_t garrays = r.dtype == FD_F64 ? fd::kGradArrays<double> : fd::kGradArrays<float>;
+    const size_t garrays = r.dtype == FD_F64 ? fd::kGradArrays<double>
+                           : hyb             ? fd::kGradArrays<fd::df64>
+                                             : fd::kGradArrays<float>;
     L.g = r.algorithm == FD_STORE_SOME ? take(garrays * n * t) : (size_t)-1;
+    if (hyb) {
+        L.w64_0 = take(4 * n * sizeof(double));
+        L.w64_1 = take(4 * n * sizeof(double));
+        L.dv = take(n * sizeof(double));
+    }
     L.total = off;
     return L;
 }
@@ -131,8 +144,9 @@ const char* check_request(const fd_request* r) {
     if (!r) return "request is NULL";
     if (const char* why = fd::check_instance(r->nx, r->ny, r->nz, r->Re, r->Mach, r->Pr, r->gamma, r->dt)) return why;
     if (r->steps < 1) return "steps must be >= 1";
-    if (r->dtype != FD_F64 && r->dtype != FD_F32_ACCDW) return "unknown dtype";
+    if (r->dtype != FD_F64 && r->dtype != FD_F32_ACCDW && r->dtype != FD_F64_DW) return "unknown dtype";
     if (r->algorithm != FD_STORE_SOME && r->algorithm != FD_RECOMPUTE_ALL) return "algorithm must be SS or RA";
+    if (r->dtype == FD_F64_DW && r->algorithm != FD_STORE_SOME) return "FD_F64_DW requests are store-some only";
     if (r->tile_points != 0 && r->tile_points < 32) return "tile_points must be 0 or >= 32";
     return nullptr;
 }
@@ -172,7 +186,8 @@ struct Finished {
 constexpr int kMaxSteps = 31;
 
 double step_cost(const fd_request& r) {
-    return (double)r.nx * r.ny * r.nz * (r.dtype == FD_F64 ? 1.7e-9 : 1.6e-10);
+    const double per_point = r.dtype == FD_F64 ? 1.7e-9 : (r.dtype == FD_F64_DW ? 7.0e-10 : 1.6e-10);
+    return (double)r.nx * r.ny * r.nz * per_point;
 }
 
 }  // namespace
@@ -204,14 +219,14 @@ struct fd_server {
     int parity = 0;
     long long submitted = 0, completed = 0, ticks = 0;
     // current device views (valid after a rebuild)
-    void* inst[2] = {nullptr, nullptr};  // [0] double table, [1] float table
-    // [dtype][family: 0 SS, 1 RA, 2 RA staged by TMA (binary32, padded layout)], ordered by k
-    fd::BatchTile* tiles[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    void* inst[3] = {nullptr, nullptr, nullptr};  // tables of the groups: binary64, binary32, mixed
+    // [group][family: 0 SS, 1 RA, 2 RA staged by TMA (binary32, padded layout)], ordered by k
+    fd::BatchTile* tiles[3][3] = {};
     // ntiles[d][f][r]: tiles of the solves with k > r (a prefix of tiles[d][f])
-    int ntiles[2][3][kMaxSteps] = {};
+    int ntiles[3][3][kMaxSteps] = {};
     int rounds = 1;  // max k over the active set
-    fd::BatchTile* fresh_tiles[2] = {nullptr, nullptr};
-    int nfresh[2] = {0, 0};
+    fd::BatchTile* fresh_tiles[3] = {nullptr, nullptr, nullptr};
+    int nfresh[3] = {0, 0, 0};
     std::string err;
 
     int fail(int code, const char* fmt, ...) {
@@ -265,6 +280,29 @@ fd::BatchInst<T> record(const fd_server* s, const Active& a) {
     return I;
 }
 
+fd::BatchHyb record_hyb(const fd_server* s, const Active& a) {
+    fd::BatchHyb I;
+    std::memset(&I, 0, sizeof I);
+    I.g = fd::make_grid(a.r.nx, a.r.ny, a.r.nz);
+    I.ph = fd::make_phys(a.r.Re, a.r.Mach, a.r.Pr, a.r.gamma);
+    I.k = fd::make_coef<fd::df64>(I.g, I.ph, true);
+    I.k.c_rho = fd::df64(0.0f, 0.0f);  // the mean-state terms enter in binary64
+    I.k.c_E = fd::df64(0.0f, 0.0f);
+    I.c_E = -(I.ph.rhoE0 + I.ph.p0);
+    for (int st = 0; st < 3; ++st) I.rk[st] = fd::make_stage(st, a.r.dt);
+    char* b = s->base() + a.off;
+    I.Q[0] = reinterpret_cast<double*>(b + a.L.q0);
+    I.Q[1] = reinterpret_cast<double*>(b + a.L.q1);
+    I.Qs = reinterpret_cast<double*>(b + a.L.qs);
+    I.F[0] = reinterpret_cast<fd::df64*>(b + a.L.w0);
+    I.F[1] = reinterpret_cast<fd::df64*>(b + a.L.w1);
+    I.W64[0] = reinterpret_cast<double*>(b + a.L.w64_0);
+    I.W64[1] = reinterpret_cast<double*>(b + a.L.w64_1);
+    I.G = reinterpret_cast<fd::df64*>(b + a.L.g);
+    I.Dv = reinterpret_cast<double*>(b + a.L.dv);
+    return I;
+}
+
 void append_tiles(const Active& a, std::vector<fd::BatchTile>& v, bool tiled = false, int tma_zlen = 0) {
     if (tiled) {  // x-y tile / z-chunk work items of the shared-memory recompute-all kernel
         const int m = tma_zlen ? fd::tma_work_items(a.r.nx, a.r.ny, a.r.nz, tma_zlen)
@@ -281,7 +319,8 @@ void append_tiles(const Active& a, std::vector<fd::BatchTile>& v, bool tiled = f
 cudaError_t rebuild(fd_server* s) {
     std::vector<fd::BatchInst<double>> I64;
     std::vector<fd::BatchInst<float>> I32;
-    std::vector<fd::BatchTile> t[2][3], f[2];
+    std::vector<fd::BatchHyb> IH;
+    std::vector<fd::BatchTile> t[3][3], f[3];
     cudaError_t e;
     {  // work-item length of the TMA-staged solves for this active set
         std::vector<int> dims;
@@ -293,14 +332,17 @@ cudaError_t rebuild(fd_server* s) {
     std::vector<Active*> order;
     for (auto& a : s->active) order.push_back(&a);
     std::stable_sort(order.begin(), order.end(), [](const Active* x, const Active* y) { return x->k > y->k; });
-    int count[2][3][kMaxSteps] = {};
+    int count[3][3][kMaxSteps] = {};
     s->rounds = 1;
     for (Active* ap : order) {
         Active& a = *ap;
-        const int d = a.r.dtype == FD_F64 ? 0 : 1;
+        const int d = group_of(a.r.dtype);
         if (d == 0) {
             a.slot = (int)I64.size();
             I64.push_back(record<double>(s, a));
+        } else if (d == 2) {
+            a.slot = (int)IH.size();
+            IH.push_back(record_hyb(s, a));
         } else {
             a.slot = (int)I32.size();
             I32.push_back(record<float>(s, a));
@@ -324,8 +366,9 @@ cudaError_t rebuild(fd_server* s) {
     };
     size_t o64 = take(I64.size() * sizeof(fd::BatchInst<double>));
     size_t o32 = take(I32.size() * sizeof(fd::BatchInst<float>));
-    size_t ot[2][3], of[2];
-    for (int d = 0; d < 2; ++d) {
+    size_t oh = take(IH.size() * sizeof(fd::BatchHyb));
+    size_t ot[3][3], of[3];
+    for (int d = 0; d < 3; ++d) {
         for (int k = 0; k < 3; ++k) ot[d][k] = take(t[d][k].size() * sizeof(fd::BatchTile));
         of[d] = take(f[d].size() * sizeof(fd::BatchTile));
     }
@@ -344,9 +387,11 @@ cudaError_t rebuild(fd_server* s) {
     };
     if ((e = up(o64, I64.data(), I64.size() * sizeof I64[0])) != cudaSuccess) return e;
     if ((e = up(o32, I32.data(), I32.size() * sizeof I32[0])) != cudaSuccess) return e;
+    if ((e = up(oh, IH.data(), IH.size() * sizeof(fd::BatchHyb))) != cudaSuccess) return e;
     s->inst[0] = b + o64;
     s->inst[1] = b + o32;
-    for (int d = 0; d < 2; ++d) {
+    s->inst[2] = b + oh;
+    for (int d = 0; d < 3; ++d) {
         for (int k = 0; k < 3; ++k) {
             if ((e = up(ot[d][k], t[d][k].data(), t[d][k].size() * sizeof(fd::BatchTile))) != cudaSuccess) return e;
             s->tiles[d][k] = reinterpret_cast<fd::BatchTile*>(b + ot[d][k]);
@@ -395,6 +440,26 @@ cudaError_t run_group(fd_server* s, int d, int round) {
                 if (e != cudaSuccess) return e;
             }
         }
+    }
+    return cudaSuccess;
+}
+
+// The mixed (FD_F64_DW) group: store-some only, gradients then fused per stage.
+cudaError_t run_group_hyb(fd_server* s, int round) {
+    auto* I = static_cast<const fd::BatchHyb*>(s->inst[2]);
+    cudaError_t e;
+    const int n = s->ntiles[2][0][round];
+    if (round == 0 && s->nfresh[2]) {
+        const int gp = s->sms * fd::batch_hyb_blocks_per_sm(0);
+        if ((e = fd::launch_batch_prims_hyb(I, s->fresh_tiles[2], s->nfresh[2], s->parity, gp, s->stream)) !=
+            cudaSuccess)
+            return e;
+    }
+    if (!n) return cudaSuccess;
+    const int gg = s->sms * fd::batch_hyb_blocks_per_sm(1), gs = s->sms * fd::batch_hyb_blocks_per_sm(2);
+    for (int st = 0, p = s->parity ^ (round & 1); st < 3; ++st, p ^= 1) {
+        if ((e = fd::launch_batch_grad_hyb(I, s->tiles[2][0], n, p, gg, s->stream)) != cudaSuccess) return e;
+        if ((e = fd::launch_batch_ss_hyb(I, s->tiles[2][0], n, st, p, gs, s->stream)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -537,10 +602,11 @@ int fd_server_tick(fd_server* s, int* active_out) {
         // binary32 solves keep a shifted double-word state (rho - 1, rho u_i,
         // rho E - rhoE0): the binary64 initial condition passes through Qs.
         char* Q = s->base() + off + (s->parity ? L.q1 : L.q0);
-        double* ic = reinterpret_cast<double*>(a.r.dtype == FD_F64 ? Q : s->base() + off + L.qs);
+        const bool dw = a.r.dtype == FD_F32_ACCDW;  // double-word state
+        double* ic = reinterpret_cast<double*>(dw ? s->base() + off + L.qs : Q);
         e = fd::launch_tgv_ic(g, ph, 2.0 * fd::kPi / a.r.nx, 2.0 * fd::kPi / a.r.ny, 2.0 * fd::kPi / a.r.nz, ic,
                               s->stream);
-        if (e == cudaSuccess && a.r.dtype != FD_F64)
+        if (e == cudaSuccess && dw)
             e = fd::launch_to_df64(ic, reinterpret_cast<fd::df64*>(Q), a.n, fd::Shift5{{1.0, 0.0, 0.0, 0.0, ph.rhoE0}},
                                    s->stream);
         if (L.padded) {  // padding columns no point writes are copied but never read: zero them
@@ -580,9 +646,10 @@ int fd_server_tick(fd_server* s, int* active_out) {
     for (int r = 0; r < s->rounds; ++r) {
         if ((e = run_group<double>(s, 0, r)) != cudaSuccess) return s->cuda_fail(e, "fd_server_tick: binary64 group");
         if ((e = run_group<float>(s, 1, r)) != cudaSuccess) return s->cuda_fail(e, "fd_server_tick: binary32 group");
+        if ((e = run_group_hyb(s, r)) != cudaSuccess) return s->cuda_fail(e, "fd_server_tick: mixed group");
     }
     s->parity ^= 1;
-    s->nfresh[0] = s->nfresh[1] = 0;
+    s->nfresh[0] = s->nfresh[1] = s->nfresh[2] = 0;
     for (auto& a : s->active) {
         a.fresh = false;
         a.done += a.k;
@@ -597,7 +664,7 @@ int fd_server_tick(fd_server* s, int* active_out) {
         fd::Grid g = fd::make_grid(a.r.nx, a.r.ny, a.r.nz);
         char* b = s->base() + a.off;
         const double* Q = reinterpret_cast<const double*>(b + (s->parity ? a.L.q1 : a.L.q0));
-        if (a.r.dtype != FD_F64) {  // double-word state to binary64 in the retiring solve's Qs
+        if (a.r.dtype == FD_F32_ACCDW) {  // double-word state to binary64 in the retiring solve's Qs
             double* tmp = reinterpret_cast<double*>(b + a.L.qs);
             fd::Phys ph = fd::make_phys(a.r.Re, a.r.Mach, a.r.Pr, a.r.gamma);
             e = fd::launch_from_df64(reinterpret_cast<const fd::df64*>(Q), tmp, a.n,
@@ -667,7 +734,7 @@ int fd_server_get_state(fd_server* s, long long tag, double* dst, size_t n_elems
     char* b = s->base() + f->off;
     const double* src = reinterpret_cast<const double*>(b + (f->parity ? f->L.q1 : f->L.q0));
     cudaError_t e = cudaSuccess;
-    if (f->r.dtype != FD_F64) {  // shifted double-word state to binary64 through the solve's dead Qs
+    if (f->r.dtype == FD_F32_ACCDW) {  // shifted double-word state to binary64 through the solve's dead Qs
         double* tmp = reinterpret_cast<double*>(b + f->L.qs);
         const fd::Phys ph = fd::make_phys(f->r.Re, f->r.Mach, f->r.Pr, f->r.gamma);
         e = fd::launch_from_df64(reinterpret_cast<const fd::df64*>(src), tmp, f->n,

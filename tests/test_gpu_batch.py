@@ -117,3 +117,27 @@ def test_bad_descriptors_are_rejected():
         fd.Batch([dict(n=16, tile_points=8)], dtype="f32")
     with pytest.raises(fd.FdError):
         fd.Batch([dict(n=4)], dtype="f32")
+
+
+def test_mixed_batch_equals_alone_and_the_oracle():
+    """Mixed binary64 / double-word store-some batch (dtype f64dw): each instance equals
+    itself run alone bit for bit, and the oracle to relative L-inf 1e-12."""
+    steps = 4
+    specs = [dict(s, algorithm="store_some") for s in SPECS]
+    with fd.Batch(specs, dtype="f64dw") as b:
+        b.step(steps)
+        states = [b.state(i) for i in range(len(specs))]
+        ke, en = b.diagnostics()
+        Q0 = smooth_state((10, 9, 8), seed=71)
+        b.set_state(4, Q0)  # set / get of a binary64 state is exact
+        assert np.array_equal(b.state(4), Q0)
+    for i, spec in enumerate(specs):
+        Q, (ke1, en1) = alone(spec, "f64dw", steps)
+        assert np.array_equal(states[i], Q), i
+        assert ke[i] == ke1 and en[i] == en1, i
+        n = spec["n"]
+        nx, ny, nz = (n, n, n) if isinstance(n, int) else n
+        ref = O.run(O.tgv_ic(nx, ny, nz, 1.4, spec["Mach"]), steps, dt=spec["dt"], Re=spec["Re"], Mach=spec["Mach"])
+        assert max(np.abs(Q[v] - ref[v]).max() / np.abs(ref[v]).max() for v in range(5)) <= 1e-12, i
+    with pytest.raises(fd.FdError):
+        fd.Batch([dict(SPECS[0], algorithm="recompute_all")], dtype="f64dw")

@@ -4,8 +4,9 @@ Requests that arrive while others are active join the running batch (same
 launches), so a solve's result must not depend on its neighbours: the server's
 kinetic energy and enstrophy of every solve equal, bit for bit, those of the same
 solve run alone through fd_create / fd_step / fd_diagnostics; the final states of
-binary64 solves served in a mix match the FP64 oracle (relative L-inf 1e-12), and
-those of binary32 solves equal the same solve alone over the whole state.
+binary64 and mixed binary64 / double-word solves served in a mix match the FP64
+oracle (relative L-inf 1e-12), and every solve's final state equals the same solve
+alone over the whole state.
 """
 import numpy as np
 import pytest
@@ -144,6 +145,8 @@ def test_served_states_match_the_oracle_and_alone():
         dict(tag=33, n=(16, 12, 20), steps=5, Re=2000.0, Mach=0.3, dtype="f32", algorithm="recompute_all", dt=1e-3),
         dict(tag=34, n=(10, 14, 12), steps=3, Re=1200.0, Mach=0.25, dtype="f32", algorithm="store_some", dt=2e-3),
         dict(tag=35, n=(20, 8, 16), steps=7, Re=3000.0, Mach=0.15, dtype="f64", algorithm="store_some", dt=1e-3),
+        dict(tag=36, n=(14, 16, 12), steps=5, Re=1600.0, Mach=0.1, dtype="f64dw", algorithm="store_some", dt=1e-3),
+        dict(tag=37, n=18, steps=3, Re=900.0, Mach=0.3, dtype="f64dw", algorithm="store_some", dt=2e-3),
     ]
     by_tag = {r["tag"]: r for r in reqs}
     states, results = {}, {}
@@ -155,6 +158,9 @@ def test_served_states_match_the_oracle_and_alone():
         srv.tick()
         srv.submit(reqs[3])
         srv.submit(reqs[4])
+        srv.submit(reqs[5])
+        srv.tick()
+        srv.submit(reqs[6])
         for _ in range(40):
             srv.tick()
             for r in srv.poll():
@@ -169,7 +175,7 @@ def test_served_states_match_the_oracle_and_alone():
     for tag, r in by_tag.items():
         assert results[tag]["status"] == fd.FD_OK and results[tag]["steps"] == r["steps"]
         Q = states[tag]
-        if r["dtype"] == "f64":
+        if r["dtype"] in ("f64", "f64dw"):
             n = r["n"]
             nx, ny, nz = (n, n, n) if isinstance(n, int) else n
             ref = O.run(O.tgv_ic(nx, ny, nz, 1.4, r["Mach"]), r["steps"], dt=r["dt"], Re=r["Re"], Mach=r["Mach"])
