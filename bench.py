@@ -283,18 +283,37 @@ def roofline_of(dtype, alg, kern, n, hbm_peak, hbm_src, fp64_peak=None):
                  "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
                  "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback"}
     entry["share"] = round(k["ms_total"] / sum(v["ms_total"] for v in kern.values()), 4)
-    entry["traffic"] = TRAFFIC.get((dtype, alg, name))
+    bpp = TRAFFIC_BPP.get((dtype, alg, name))
+    entry["traffic"] = round(bpp * n) if bpp is not None else None
     entry["algorithmic_per_point"] = {"flops": flops_pt, "bytes": bytes_pt, "fp64_instr": instr_pt}
     return entry
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch at 256^3, from ncu captures of the
-# current kernels: binary64 SS fused on a 160^3 grid (three launches, 291 / 332 / 294 B per
-# point by stage) scaled by the point count; the mixed SS fused likewise (401 / 400 / 360 B per
-# point at 160^3); binary32 RA (TMA-staged) at 256^3 itself (mean of the three stages'
-# launches: 3.44, 3.43, 2.76 GB).  None where no capture exists.
-TRAFFIC = {("f64", "store_some", "fused"): 5.12e9, ("f32", "recompute_all", "fused"): 3.21e9,
-           ("f64dw", "store_some", "fused"): 6.49e9}
+# DRAM traffic per point of one launch, dram__bytes_read.sum + dram__bytes_write.sum from one
+# ncu capture of every kernel of the 160^3 bench line (bench.py --grid 160 --steps 2 --warmup 3
+# --no-cpu-baseline --no-extras; mean over the stages' launches), the traffic of a launch being
+# this times the points (the stencil kernels' traffic is proportional to the point count: the
+# binary32 RA kernel gives 185.9 B/point at 160^3 and 191.3 at 256^3).  The roofline entry's
+# `traffic` is this times the points of the run.
+TRAFFIC_BPP = {
+    ("f64", "store_some", "fused"): 304.5, ("f64", "store_some", "grad"): 105.9,
+    ("f64", "recompute_all", "fused"): 205.9, ("f64", "recompute_some", "fused"): 281.0,
+    ("f64", "recompute_some", "grad"): 105.9, ("f64", "store_none", "fused"): 206.2,
+    ("f64", "store_all", "fused"): 696.1, ("f64", "store_all", "deriv1"): 578.2,
+    ("f64", "store_all", "deriv2"): 187.6, ("f64", "store_all", "products"): 200.4,
+    ("f64", "recompute_all_inline", "fused"): 125.3,
+    ("f64dw", "store_some", "fused"): 386.2, ("f64dw", "store_some", "grad"): 115.9,
+    ("f32", "store_some", "fused"): 213.4, ("f32", "store_some", "grad"): 34.5,
+    ("f32", "recompute_all", "fused"): 185.9, ("f32", "recompute_some", "fused"): 214.1,
+    ("f32", "recompute_some", "grad"): 34.5, ("f32", "store_none", "fused"): 175.9,
+    ("f32", "store_all", "fused"): 423.0, ("f32", "store_all", "deriv1"): 277.4,
+    ("f32", "store_all", "deriv2"): 86.7, ("f32", "store_all", "products"): 93.1,
+    ("df64", "store_some", "fused"): 332.1, ("df64", "store_some", "grad"): 81.9,
+    ("df64", "recompute_all", "fused"): 261.1, ("df64", "recompute_some", "fused"): 333.0,
+    ("df64", "recompute_some", "grad"): 81.9, ("df64", "store_none", "fused"): 258.0,
+    ("df64", "store_all", "fused"): 747.6, ("df64", "store_all", "deriv1"): 573.5,
+    ("df64", "store_all", "deriv2"): 187.0, ("df64", "store_all", "products"): 201.5,
+}
 
 
 def e2e_run(fd, torch, alg, dtype, n, steps, nsolvers=2):

@@ -1244,6 +1244,15 @@ __device__ __forceinline__ void ss_grad_hyb_point(const Grid& g, const Coef<df64
                                                   double* __restrict__ Dv, int idx) {
     const int n = g.n;
     const Nbr s = make_nbr(g, idx);
+    double div = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        double t[4];
+        taps(W64 + j * (size_t)n, s.c, s.o[j], t);
+        const double gjj = g.inv12h[j] * delta1_taps(t);
+        div = j == 0 ? gjj : div + gjj;
+    }
+    Dv[s.c] = div;
     df64 G[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -1255,15 +1264,6 @@ __device__ __forceinline__ void ss_grad_hyb_point(const Grid& g, const Coef<df64
             Gw[(3 * i + j) * n + s.c] = G[i][j];
         }
     store_pair_sums(G, Gw + 9 * (size_t)n, n, s.c);
-    double div = 0.0;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        double t[4];
-        taps(W64 + j * (size_t)n, s.c, s.o[j], t);
-        const double gjj = g.inv12h[j] * delta1_taps(t);
-        div = j == 0 ? gjj : div + gjj;
-    }
-    Dv[s.c] = div;
 }
 __global__ void __launch_bounds__(256) k_ss_grad_hyb(Grid g, Coef<df64> k, const df64* __restrict__ Wf,
                                                     const double* __restrict__ W64, df64* __restrict__ Gw,

@@ -42,7 +42,7 @@ def test_roofline_entry_for_binary64():
     assert e["fp64_pipe_frac"] == pytest.approx(instr * n / sec / bench.FP64_PEAK_INSTR, rel=1e-3)
     assert e["hbm_achieved_gbs"] == pytest.approx(nbytes * n / sec / 1e9, rel=1e-3)
     assert e["share"] == pytest.approx(67.0 / 79.5, abs=1e-4)
-    assert e["traffic"] == bench.TRAFFIC[("f64", "store_some", "fused")]
+    assert e["traffic"] == round(bench.TRAFFIC_BPP[("f64", "store_some", "fused")] * n)
     # the nominal FP64 peak: 152 SMs x 2 FMA lanes x 2 flop x 2.07 GHz
     assert bench.FP64_PEAK_TFLOPS == pytest.approx(1.2586, abs=1e-4)
 
@@ -57,7 +57,8 @@ def test_roofline_entry_for_binary32_is_on_the_hbm_rate():
     assert e["frac"] == pytest.approx(e["achieved"] / 6792.7, rel=1e-3)
     assert e["share"] == 1.0
     e = bench.roofline_of("f32", "store_some", {"fused": kern["fused"]}, n, 6800.0, "fallback")
-    assert e["traffic"] is None and e["peak_source"] == "fallback"
+    assert e["traffic"] == round(bench.TRAFFIC_BPP[("f32", "store_some", "fused")] * n)
+    assert e["peak_source"] == "fallback"
 
 
 class _FakeProc:
@@ -116,3 +117,14 @@ def test_roofline_entry_for_the_mixed_kernel_is_on_the_issue_slots():
     # the measured binary64 peak replaces the nominal one for the binary64 families
     e64 = bench.roofline_of("f64", "store_some", kern, n, 6787.2, "measured", fp64_peak=1.25)
     assert e64["peak"] == 1.25 and "measured" in e64["peak_source"]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "df64"])
+@pytest.mark.parametrize("alg", bench.VARIANTS)
+def test_every_reported_kernel_has_measured_traffic(dtype, alg):
+    for kclass in CLASSES[alg]:
+        bpp = bench.TRAFFIC_BPP.get((dtype, alg, kclass))
+        assert bpp is not None and bpp > 0, (dtype, alg, kclass)
+        # measured traffic stays within a factor of the algorithmic bytes
+        _, nbytes, _ = bench.cost_of(dtype, alg, kclass)
+        assert 0.4 * nbytes <= bpp <= 1.5 * nbytes, (dtype, alg, kclass, bpp, nbytes)
