@@ -77,6 +77,7 @@ struct fd_handle {
     double* G = nullptr;   // SS
     double* P = nullptr;   // BL
     double* Dv = nullptr;  // FD_F64_DW: binary64 div u of the current stage
+    fd::df64* Rc = nullptr;  // FD_F64_DW: convective part of the residual
     double* D1 = nullptr;  // BL
     double* D2 = nullptr;  // BL
     float* Gf = nullptr;   // binary32 SS: 9 gradients
@@ -149,7 +150,7 @@ int check_args(int nx, int ny, int nz, double Re, double Mach, double Pr, double
 
 // Byte layout of a handle's single device allocation.
 struct Layout {
-    size_t q0, q1, qs, w0, w1, g, p, d1, d2, wf0, wf1, gf, wd0, wd1, gd, dv, partial, diag, flag, kerr, total;
+    size_t q0, q1, qs, w0, w1, g, p, d1, d2, wf0, wf1, gf, wd0, wd1, gd, dv, rc, partial, diag, flag, kerr, total;
 };
 
 // SS and RS keep the nine velocity gradients in work arrays.
@@ -169,7 +170,7 @@ Layout plan(long long n, int algorithm, int dtype, size_t wf_points) {
     L.q0 = take(f5);
     L.q1 = take(f5);
     L.qs = take(f5);
-    L.w1 = L.g = L.p = L.d1 = L.d2 = L.wf0 = L.wf1 = L.gf = L.wd0 = L.wd1 = L.gd = L.dv = (size_t)-1;
+    L.w1 = L.g = L.p = L.d1 = L.d2 = L.wf0 = L.wf1 = L.gf = L.wd0 = L.wd1 = L.gd = L.dv = L.rc = (size_t)-1;
     L.w0 = dtype == FD_DF64 || algorithm == FD_RECOMPUTE_ALL_INLINE
                ? (size_t)-1
                : take(dtype == FD_F64_DW ? 4 * n * sizeof(double) : f5);
@@ -180,6 +181,7 @@ Layout plan(long long n, int algorithm, int dtype, size_t wf_points) {
         L.wd1 = take(10 * n * sizeof(fd::df64));
         L.gd = take(fd::kGradArrays<fd::df64> * n * sizeof(fd::df64));
         L.dv = take(n * sizeof(double));  // binary64 div u of the stage (gradient pass -> fused kernel)
+        L.rc = take(5 * n * sizeof(fd::df64));  // convective part of the residual (first fused kernel)
     } else if (dtype == FD_DF64) {
         // state Q[2], Qs hold double-words (8 bytes per value, like binary64)
         L.wd0 = take(10 * n * sizeof(fd::df64));
@@ -337,7 +339,7 @@ cudaError_t run_stage(fd_handle* h, int s, bool resid, double* out) {
                   [&] { return fd::launch_ss_grad_hyb(g, h->kw, h->Wd[wc] + 5 * n, h->W[wc], h->Gd, h->Dv, h->stream); });
         if (e != cudaSuccess) return e;
         return timed(h, FD_KERNEL_FUSED, [&] {
-            return fd::launch_ss_hyb(g, h->kw, ph, rk, resid, h->Wd[wc], h->Gd, h->Dv, h->W[wc], Qin, Qout, h->Qs,
+            return fd::launch_ss_hyb(g, h->kw, ph, rk, resid, h->Wd[wc], h->Gd, h->Rc, h->Dv, h->W[wc], Qin, Qout, h->Qs,
                                      resid ? nullptr : h->Wd[1 - wc], resid ? nullptr : h->W[1 - wc], h->stream);
         });
     }
@@ -479,6 +481,7 @@ int create_impl(fd_handle** out, int nx, int ny, int nz, int nz_period, int z0, 
     h->Wd[1] = at<fd::df64>(h->block, L.wd1);
     h->Gd = at<fd::df64>(h->block, L.gd);
     h->Dv = at<double>(h->block, L.dv);
+    h->Rc = at<fd::df64>(h->block, L.rc);
     if (dtype == FD_F64) {
         h->G = at<double>(h->block, L.g);
         h->P = at<double>(h->block, L.p);

@@ -85,8 +85,9 @@ cudaError_t launch_prims_hyb(const Grid& g, const Phys& ph, const double* Q, df6
 cudaError_t launch_ss_grad_hyb(const Grid& g, const Coef<df64>& k, const df64* Wf, const double* W64, df64* Gw,
                                double* Dv, cudaStream_t st);
 cudaError_t launch_ss_hyb(const Grid& g, const Coef<df64>& k, const Phys& ph, const RKStage& rk, bool resid,
-                          const df64* F, const df64* Gw, const double* Dv, const double* W64, const double* Q64,
-                          double* out, double* Qs, df64* Fnext, double* W64next, cudaStream_t st);
+                          const df64* F, const df64* Gw, df64* Rc, const double* Dv, const double* W64,
+                          const double* Q64, double* out, double* Qs, df64* Fnext, double* W64next,
+                          cudaStream_t st);
 template <class T>
 cudaError_t launch_bl_prod(const Grid& g, const T* Qf, const T* Wf, T* P, cudaStream_t st);
 template <class T>
