@@ -54,7 +54,7 @@ struct InstHost {
     bool padded;                   // TMA-staged binary32 RA: ghost-padded working fields
     size_t q0, q1, qs, w0, w1, g;  // byte offsets in the allocation
     // FD_F64_DW: w0 / w1 hold the double-word fields F; binary64 u, v, w, p and div u here
-    size_t w64_0 = (size_t)-1, w64_1 = (size_t)-1, dv = (size_t)-1;
+    size_t w64_0 = (size_t)-1, w64_1 = (size_t)-1, dv = (size_t)-1, rc = (size_t)-1;
 };
 
 // The binary32 mode keeps a double-word state; binary64 and the mixed mode a binary64 one.
@@ -158,6 +158,7 @@ void fill_hyb(const fd_batch* b, std::vector<fd::BatchHyb>& out) {
         I.W64[1] = reinterpret_cast<double*>(b->base() + h.w64_1);
         I.G = reinterpret_cast<fd::df64*>(b->base() + h.g);
         I.Dv = reinterpret_cast<double*>(b->base() + h.dv);
+        I.Rc = reinterpret_cast<fd::df64*>(b->base() + h.rc);
     }
 }
 
@@ -243,8 +244,9 @@ cudaError_t enqueue_step_hyb(fd_batch* b, int p, cudaStream_t st) {
         e = b->prof.timed(st, FD_KERNEL_GRAD,
                           [&] { return fd::launch_batch_grad_hyb(I, b->d_ss, b->n_ss, q, b->grid_grad, st); });
         if (e != cudaSuccess) return e;
-        e = b->prof.timed(st, FD_KERNEL_FUSED,
-                          [&] { return fd::launch_batch_ss_hyb(I, b->d_ss, b->n_ss, s, q, b->grid_ss_fused, st); });
+        e = b->prof.timed(st, FD_KERNEL_FUSED, [&] {
+            return fd::launch_batch_ss_hyb(I, b->d_ss, b->n_ss, s, q, b->grid_ra_fused, b->grid_ss_fused, st);
+        });
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -418,6 +420,7 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
             h.w64_0 = take(4 * (size_t)h.n * sizeof(double));
             h.w64_1 = take(4 * (size_t)h.n * sizeof(double));
             h.dv = take((size_t)h.n * sizeof(double));
+            h.rc = take(5 * (size_t)h.n * sizeof(fd::df64));
         }
     }
     std::vector<fd::BatchTile> t_ss, t_ra, t_all;
@@ -459,8 +462,9 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     if (sms <= 0) sms = 152;
-    if (hyb) {
+    if (hyb) {  // (the RA slot holds the grid of the first fused kernel: a mixed batch has no RA)
         b->grid_ss_fused = sms * fd::batch_hyb_blocks_per_sm(2);
+        b->grid_ra_fused = sms * fd::batch_hyb_blocks_per_sm(3);
         b->grid_grad = sms * fd::batch_hyb_blocks_per_sm(1);
     } else if (dtype == FD_F64) {
         b->grid_ss_fused = grid_for<double>(sms, true, true);

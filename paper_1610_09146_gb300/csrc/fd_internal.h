@@ -145,14 +145,17 @@ struct alignas(16) BatchHyb {
     double* W64[2];
     df64* G;
     double* Dv;
+    df64* Rc;  // convective part of the residual (first of the two fused kernels)
 };
-int batch_hyb_blocks_per_sm(int kernel);  // 0: primitives, 1: gradients, 2: fused
+int batch_hyb_blocks_per_sm(int kernel);  // 0: primitives, 1: gradients, 2: fused, 3: fused convective part
 cudaError_t launch_batch_prims_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int parity, int grid,
                                    cudaStream_t st);
 cudaError_t launch_batch_grad_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int parity, int grid,
                                   cudaStream_t st);
+// The two fused kernels of a stage (convective part, then the rest and the update); grid_conv and
+// grid the persistent grids of the two.
 cudaError_t launch_batch_ss_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int stage, int parity,
-                                int grid, cudaStream_t st);
+                                int grid_conv, int grid, cudaStream_t st);
 
 template <class T>
 int batch_blocks_per_sm(bool fused, bool stored_g);

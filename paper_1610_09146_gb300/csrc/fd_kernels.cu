@@ -1289,11 +1289,14 @@ __global__ void __launch_bounds__(256) k_ss_grad_hyb(Grid g, Coef<df64> k, const
 // record with its two mean-state terms (c_rho, c_E) set to zero: those enter
 // here in binary64, with c_E = -(rhoE0 + p0).
 // The convective part of the residual (PART 1), into Rc for ss_hyb_point.  The
-// residual is split over two kernels so that each fits its registers without
-// spilling (120 and 128 per thread, against 128 with 84 bytes of spill for the
-// whole residual in one kernel) at a higher occupancy for this one (five blocks
-// of 128 threads per SM): 256^3 step 11.53 -> 11.01 ms, 384^3 41.9 -> 38.3 ms,
-// for 40 bytes per point written and read again.
+// residual is split over two kernels so that each runs at a higher occupancy
+// than the whole residual could (128 registers and 84 bytes of spill at 16 warps
+// per SM): this one at five blocks of 128 threads per SM (96 registers), the
+// rest with the update at six (80 registers, 8 bytes of spill), for 40 bytes per
+// point written and read again.  The kernels are latency-bound on their tap
+// loads, so the warps pay: 256^3 step 11.53 ms (one kernel) -> 11.01 (two, four
+// blocks each) -> 9.63-9.89 (five and six blocks; four to eight blocks of either
+// measured within 1.3 % of this).
 __device__ __forceinline__ void ss_hyb_conv_point(const Grid& g, const Coef<df64>& k, const df64* __restrict__ F,
                                                   const df64* __restrict__ Gw, df64* __restrict__ Rc, int idx) {
     const int n = g.n;
@@ -1325,17 +1328,8 @@ __device__ __forceinline__ void ss_hyb_point(const Grid& g, const Coef<df64>& k,
         fused_residual<df64, true, GlobalAcc<df64>, false, 2>(GlobalAcc<df64>{s, n, F, F + 5 * (size_t)n, Gw}, k,
                                                               Rw);
     }
-    if (Rc) {
 #pragma unroll
-        for (int f = 0; f < 5; ++f) Rw[f] = renorm(add_nn(Rw[f], ld(Rc + (size_t)f * n, idx)));
-    } else {  // the convective part here too (batched kernel): the same sums, one kernel
-        const Nbr s = make_nbr(g, idx);
-        df64 Rcv[5];
-        fused_residual<df64, true, GlobalAcc<df64>, false, 1>(GlobalAcc<df64>{s, n, F, F + 5 * (size_t)n, Gw}, k,
-                                                              Rcv);
-#pragma unroll
-        for (int f = 0; f < 5; ++f) Rw[f] = renorm(add_nn(Rw[f], Rcv[f]));
-    }
+    for (int f = 0; f < 5; ++f) Rw[f] = renorm(add_nn(Rw[f], ld(Rc + (size_t)f * n, idx)));
     // the neighbour offsets again (cheaper than keeping them live through the residual)
     const Nbr s = make_nbr(g, idx);
     // -D_j p: 8 (p_{+1} - p_{-1}) + (p_{-2} - p_{+2}), differences exact in binary64
@@ -1369,7 +1363,7 @@ __device__ __forceinline__ void ss_hyb_point(const Grid& g, const Coef<df64>& k,
     }
 }
 template <bool RESID>
-__global__ void __launch_bounds__(128, 4) k_ss_hyb(Grid g, Coef<df64> k, Phys ph, RKStage rk, double c_E,
+__global__ void __launch_bounds__(128, 6) k_ss_hyb(Grid g, Coef<df64> k, Phys ph, RKStage rk, double c_E,
                                                    const df64* __restrict__ F, const df64* __restrict__ Gw,
                                                    const df64* __restrict__ Rc, const double* __restrict__ Dv,
                                                    const double* __restrict__ W64, const double* __restrict__ Q64,
@@ -1932,7 +1926,7 @@ __global__ void __launch_bounds__(256) k_batch_grad_hyb(const BatchHyb* __restri
     }
 }
 
-__global__ void __launch_bounds__(128, 3) k_batch_ss_hyb(const BatchHyb* __restrict__ insts,
+__global__ void __launch_bounds__(128, 4) k_batch_ss_hyb(const BatchHyb* __restrict__ insts,
                                                          const BatchTile* __restrict__ tiles, int ntiles, int stage,
                                                          int parity) {
     __shared__ BatchHyb I;
@@ -1941,9 +1935,22 @@ __global__ void __launch_bounds__(128, 3) k_batch_ss_hyb(const BatchHyb* __restr
         const BatchTile tl = tiles[t];
         stage_inst(I, insts, tl.inst, cur);
         for (int p = threadIdx.x; p < tl.count; p += blockDim.x)
-            ss_hyb_point<false>(I.g, I.k, I.ph, I.rk[stage], I.c_E, I.F[parity], I.G, nullptr, I.Dv, I.W64[parity],
+            ss_hyb_point<false>(I.g, I.k, I.ph, I.rk[stage], I.c_E, I.F[parity], I.G, I.Rc, I.Dv, I.W64[parity],
                                 I.Q[parity], I.Q[1 - parity], I.Qs, I.F[1 - parity], I.W64[1 - parity],
                                 tl.start + p);
+    }
+}
+
+__global__ void __launch_bounds__(128, 5) k_batch_ss_hyb_conv(const BatchHyb* __restrict__ insts,
+                                                              const BatchTile* __restrict__ tiles, int ntiles,
+                                                              int parity) {
+    __shared__ BatchHyb I;
+    int cur = -1;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        stage_inst(I, insts, tl.inst, cur);
+        for (int p = threadIdx.x; p < tl.count; p += blockDim.x)
+            ss_hyb_conv_point(I.g, I.k, I.F[parity], I.G, I.Rc, tl.start + p);
     }
 }
 
@@ -1951,7 +1958,8 @@ int batch_hyb_blocks_per_sm(int kernel) {
     int b = 0;
     cudaError_t e = kernel == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_prims_hyb, 256, 0)
                     : kernel == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_grad_hyb, 256, 0)
-                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_ss_hyb, 128, 0);
+                    : kernel == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_ss_hyb, 128, 0)
+                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_ss_hyb_conv, 128, 0);
     return e == cudaSuccess && b > 0 ? b : 1;
 }
 
@@ -1970,8 +1978,9 @@ cudaError_t launch_batch_grad_hyb(const BatchHyb* insts, const BatchTile* tiles,
 }
 
 cudaError_t launch_batch_ss_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int stage, int parity,
-                                int grid, cudaStream_t st) {
+                                int grid_conv, int grid, cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
+    k_batch_ss_hyb_conv<<<grid_conv, 128, 0, st>>>(insts, tiles, ntiles, parity);
     k_batch_ss_hyb<<<grid, 128, 0, st>>>(insts, tiles, ntiles, stage, parity);
     return cudaGetLastError();
 }

@@ -99,7 +99,7 @@ struct Layout {
     size_t q0, q1, qs, w0, w1, g, total;
     bool padded;  // binary32 RA staged by TMA: ghost-padded working fields
     // FD_F64_DW: w0 / w1 hold the double-word fields; binary64 u, v, w, p and div u here
-    size_t w64_0 = (size_t)-1, w64_1 = (size_t)-1, dv = (size_t)-1;
+    size_t w64_0 = (size_t)-1, w64_1 = (size_t)-1, dv = (size_t)-1, rc = (size_t)-1;
 };
 
 // Instance group of a request: 0 binary64, 1 binary32, 2 mixed binary64 / double-word.
@@ -135,6 +135,7 @@ Layout layout_of(const fd_request& r, bool tma) {
         L.w64_0 = take(4 * n * sizeof(double));
         L.w64_1 = take(4 * n * sizeof(double));
         L.dv = take(n * sizeof(double));
+        L.rc = take(5 * n * sizeof(fd::df64));
     }
     L.total = off;
     return L;
@@ -300,6 +301,7 @@ fd::BatchHyb record_hyb(const fd_server* s, const Active& a) {
     I.W64[1] = reinterpret_cast<double*>(b + a.L.w64_1);
     I.G = reinterpret_cast<fd::df64*>(b + a.L.g);
     I.Dv = reinterpret_cast<double*>(b + a.L.dv);
+    I.Rc = reinterpret_cast<fd::df64*>(b + a.L.rc);
     return I;
 }
 
@@ -456,10 +458,11 @@ cudaError_t run_group_hyb(fd_server* s, int round) {
             return e;
     }
     if (!n) return cudaSuccess;
-    const int gg = s->sms * fd::batch_hyb_blocks_per_sm(1), gs = s->sms * fd::batch_hyb_blocks_per_sm(2);
+    const int gg = s->sms * fd::batch_hyb_blocks_per_sm(1), gs = s->sms * fd::batch_hyb_blocks_per_sm(2),
+              gc = s->sms * fd::batch_hyb_blocks_per_sm(3);
     for (int st = 0, p = s->parity ^ (round & 1); st < 3; ++st, p ^= 1) {
         if ((e = fd::launch_batch_grad_hyb(I, s->tiles[2][0], n, p, gg, s->stream)) != cudaSuccess) return e;
-        if ((e = fd::launch_batch_ss_hyb(I, s->tiles[2][0], n, st, p, gs, s->stream)) != cudaSuccess) return e;
+        if ((e = fd::launch_batch_ss_hyb(I, s->tiles[2][0], n, st, p, gc, gs, s->stream)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
