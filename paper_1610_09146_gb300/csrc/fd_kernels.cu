@@ -1926,7 +1926,7 @@ __global__ void __launch_bounds__(256) k_batch_grad_hyb(const BatchHyb* __restri
     }
 }
 
-__global__ void __launch_bounds__(128, 4) k_batch_ss_hyb(const BatchHyb* __restrict__ insts,
+__global__ void __launch_bounds__(128, 6) k_batch_ss_hyb(const BatchHyb* __restrict__ insts,
                                                          const BatchTile* __restrict__ tiles, int ntiles, int stage,
                                                          int parity) {
     __shared__ BatchHyb I;
