@@ -212,7 +212,9 @@ size_t fd_device_bytes(const fd_handle* h);
  *   FD_KERNEL_PRIMS     primitive variables u_i, p, T (Eqs. 6-7), all families
  *   FD_KERNEL_GRAD      SS: the nine stored velocity gradients
  *   FD_KERNEL_FUSED     RA / SS: fused derivatives + residual + RK update;
- *                       BL: pointwise residual + RK update
+ *                       BL: pointwise residual + RK update; FD_F64_DW
+ *                       store-some: two kernels (the convective terms,
+ *                       then the rest with the update), timed as one pass
  *   FD_KERNEL_PRODUCTS  BL: product work arrays
  *   FD_KERNEL_DERIV1    BL: first-derivative work arrays
  *   FD_KERNEL_DERIV2    BL: second- and mixed-derivative work arrays */
@@ -231,8 +233,9 @@ size_t fd_device_bytes(const fd_handle* h);
  * fd_destroy.  Errors: FD_EINVAL, FD_ECUDA. */
 int fd_profile(fd_handle* h, int enable);
 
-/* Total device time in milliseconds and number of launches of one kernel
- * class since the last fd_profile call.  Synchronises the stream.  Either
+/* Total device time in milliseconds and number of timed passes of one
+ * kernel class since the last fd_profile call (one launch per pass, except
+ * the two-kernel FD_F64_DW fused pass).  Synchronises the stream.  Either
  * output may be NULL.  Errors: FD_EINVAL (class out of range), FD_ECUDA. */
 int fd_profile_read(fd_handle* h, int kernel_class, double* total_ms, long long* launches);
 
