@@ -125,7 +125,7 @@ COST = {
     # the saved register; flops / instructions from ncu at 160^3 (DADD + DMUL + 2 DFMA)
     ("f64", "recompute_all_inline", "fused"): (3095.7, 133.3, 1774.3),
     ("f64dw", "store_some", "fused"): (401.7, 514.7, 37.3),
-    ("f64dw", "store_some", "grad"): (59, 128, 14),
+    ("f64dw", "store_some", "grad"): (59, 128, 12),
     ("f64dw", "*", "prims"): (14, 200, 17),
 }
 # Thread instructions per point of one fused pass (all pipes): ncu's smsp__thread_inst_executed
@@ -308,7 +308,7 @@ TRAFFIC_BPP = {
     ("f64", "store_all", "fused"): 696.1, ("f64", "store_all", "deriv1"): 578.2,
     ("f64", "store_all", "deriv2"): 187.6, ("f64", "store_all", "products"): 200.4,
     ("f64", "recompute_all_inline", "fused"): 125.3,
-    ("f64dw", "store_some", "fused"): 501.9, ("f64dw", "store_some", "grad"): 116.9,
+    ("f64dw", "store_some", "fused"): 501.9, ("f64dw", "store_some", "grad"): 116.4,
     ("f32", "store_some", "fused"): 213.4, ("f32", "store_some", "grad"): 34.5,
     ("f32", "recompute_all", "fused"): 185.9, ("f32", "recompute_some", "fused"): 214.1,
     ("f32", "recompute_some", "grad"): 34.5, ("f32", "store_none", "fused"): 175.9,

@@ -43,10 +43,10 @@ cudaError_t launch_ra(const Grid& g, const Coef<T>& k, const Phys& ph, const RKS
                       const T* Wf, const state_t<T>* Q64, state_t<T>* out, state_t<T>* Qs, T* Wnext, cudaStream_t st);
 // RA with the fields staged through shared memory (same arithmetic as launch_ra).
 // binary32 recompute-all with TMA-staged planes.  Its ten working fields use a
-// ghost-padded layout, [10][nz][ny+4][nx+8] with the periodic images in the
+// ghost-padded layout, [10][nz][ny+4][nx+4] with the periodic images in the
 // padding (padded_field_points(g) values per field): launch_prims_padded
 // writes it from a state, and the kernel writes the next stage's fields in it.
-// `map` describes one such buffer (box 40 x 12 x 1 x 10, made by
+// `map` describes one such buffer (box 36 x 12 x 1 x 10, made by
 // encode_field_map); usable when tma_staging_ok(g).  prepare_ra_tma sets the
 // kernels' shared-memory size (host set-up, once per device).  A wait that
 // runs out (0.5 s) sets *err to 1 (2: the shared ring was misaligned).

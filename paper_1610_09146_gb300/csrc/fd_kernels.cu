@@ -210,24 +210,25 @@ __device__ __forceinline__ void prims_point(const Phys& ph, const df64 q[5], flo
 }
 
 // Ghost-padded layout of the binary32 working fields of the TMA-staged
-// recompute-all kernel: each field is an (nx + 8) x (ny + 4) x nz array that
-// holds x = -4 .. nx+3 and y = -2 .. ny+1, and the cells x = -2, -1, nx, nx+1
+// recompute-all kernel: each field is an (nx + 4) x (ny + 4) x nz array that
+// holds x = -2 .. nx+1 and y = -2 .. ny+1, and the cells x = -2, -1, nx, nx+1
 // and y = -2, -1, ny, ny+1 hold the periodic images, written by whoever writes
-// the point they copy.  Every TMA box is then inside the array (the columns
-// x = -4, -3, nx+2, nx+3 only pad the rows to 16-byte boundaries and are never
-// read), and no tile needs a special case at the periodic boundary.
+// the point they copy.  The box of the tile at x0 then starts at padded column
+// x0 (a multiple of 32 floats, so on a 16-byte boundary) and covers
+// x0 - 2 .. x0 + 33; rows are nx + 4 floats, a multiple of 16 bytes when
+// nx % 4 = 0; no tile needs a special case at the periodic boundary.
 struct PadLayout {
     int nx, ny, px, py;
     long long np;  // points per padded field
     __device__ __forceinline__ long long at(int x, int y, int z) const {
-        return ((long long)z * py + (y + 2)) * px + (x + 4);
+        return ((long long)z * py + (y + 2)) * px + (x + 2);
     }
 };
 __host__ __device__ __forceinline__ PadLayout pad_layout(const Grid& g) {
     PadLayout L;
     L.nx = g.nx;
     L.ny = g.ny;
-    L.px = g.nx + 8;
+    L.px = g.nx + 4;
     L.py = g.ny + 4;
     L.np = (long long)L.px * L.py * g.nz;
     return L;
@@ -850,9 +851,8 @@ __global__ void __launch_bounds__(kTX* kTY, sizeof(T) == 4 ? 2 : 1)
 
 // Recompute-all, binary32, with the planes staged by the Tensor Memory
 // Accelerator.  The ten working fields are one ghost-padded array (PadLayout)
-// [10][nz][ny+4][nx+8]; one four-dimensional TMA copy moves a 40 x 12 box of
-// all ten fields of one plane (the 32 x 8 tile, a two-point halo in y, and in
-// x a four-point halo so that the box starts on a 16-byte boundary) into a
+// [10][nz][ny+4][nx+4]; one four-dimensional TMA copy moves a 36 x 12 box of
+// all ten fields of one plane (the 32 x 8 tile and its two-point halos) into a
 // ring of six plane slots, each with its own mbarrier.  While plane z is
 // evaluated, plane z+3 is already in flight, so no thread issues a staging
 // load and the copy latency is hidden behind the stencil arithmetic.  The
@@ -860,15 +860,21 @@ __global__ void __launch_bounds__(kTX* kTY, sizeof(T) == 4 ? 2 : 1)
 // special.  Every wait is bounded (0.5 s of wall time): a wait that runs out
 // sets *err, drains the copies in flight (again bounded) and ends the block.
 constexpr int kMX = 32, kMY = 8, kMThreads = kMX * kMY;
-constexpr int kBX = kMX + 8, kBY = kMY + 4, kBPlane = kBX * kBY;
+constexpr int kBX = kMX + 4, kBY = kMY + 4, kBPlane = kBX * kBY;
 constexpr int kMSlots = 6, kMZChunk = 64;
+constexpr int kMLook = kMSlots - 5;  // planes in flight beyond the five a plane's stencils read
 constexpr int kMBlocks = kMY == 8 ? 2 : 1;  // resident blocks per SM the ring allows
-constexpr unsigned kMSlotBytes = kNF * kBPlane * 4;  // 19200, a multiple of 128
-// All of a block's shared memory is dynamic: the ring (6 x 19200 bytes, first,
+constexpr unsigned kMSlotBytes = kNF * kBPlane * 4;  // 17280, a multiple of 128
+// All of a block's shared memory is dynamic: the ring (6 x 17280 bytes, first,
 // so that it starts on the 128-byte boundary the TMA destination needs), the
-// six mbarriers, and in the batched kernel the staged instance record: two
-// blocks per SM, 2 x (115200 + 48 + 456 + 1024 reserved) <= 228 KB.
+// six mbarriers, and in the batched kernel the instance record: two blocks per
+// SM, 2 x (103680 + 48 + record + 1024 reserved) <= 228 KB.
 constexpr unsigned long long kMWaitNs = 500000000ull;  // a wait gives up after 0.5 s
+using TmaAcc = SmemAccT<float, kBX, kBY, 2, 2, true>;
+// Dynamic shared memory of a TMA block: ring, then mbarriers (then, batched,
+// the instance record on a 16-byte boundary).
+constexpr unsigned kMBarOff = kMSlots * kMSlotBytes;
+constexpr unsigned kMSmem = (kMBarOff + 8 * kMSlots + 15) / 16 * 16;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -922,7 +928,7 @@ __device__ __forceinline__ bool ra_tma_item(float* sm, unsigned bar0, unsigned& 
     const unsigned sm0 = smem_u32(sm);
     const PadLayout L = pad_layout(g);
     auto slot_of = [&](int p) { return (p - zbeg + 2) % kMSlots; };
-    auto issue = [&](int p) {  // one thread; padded coordinates of (x0 - 4, y0 - 2) are (x0, y0)
+    auto issue = [&](int p) {  // one thread; padded coordinates of (x0 - 2, y0 - 2) are (x0, y0)
         if (p == skip_plane) return;  // failure-detection test: this plane never arrives
         const int s = slot_of(p);
         const unsigned bar = bar0 + 8 * s, dst = sm0 + s * kMSlotBytes;
@@ -957,7 +963,7 @@ __device__ __forceinline__ bool ra_tma_item(float* sm, unsigned bar0, unsigned& 
         return false;
     };
 
-    int issued = zbeg + 2;
+    int issued = zbeg + 1 + kMLook;
     if (tid == 0)
         for (int p = zbeg - 2; p <= issued; ++p) issue(p);
     {
@@ -970,9 +976,9 @@ __device__ __forceinline__ bool ra_tma_item(float* sm, unsigned bar0, unsigned& 
     float aq[5];  // D_x u_x + D_y u_y of planes z-2 .. z+2 at (x, y)
     for (int z = zbeg; z < zend; ++z) {
         const int c = (z * ny + y) * nx + x;
-        if (z + 3 <= zlast) {
-            if (tid == 0) issue(z + 3);
-            issued = z + 3;
+        if (z + 2 + kMLook <= zlast) {
+            if (tid == 0) issue(z + 2 + kMLook);
+            issued = z + 2 + kMLook;
         }
         df64 qs[5];
         if (!RESID && inside) {
@@ -982,8 +988,7 @@ __device__ __forceinline__ bool ra_tma_item(float* sm, unsigned bar0, unsigned& 
         }
         if (__syncthreads_or(!wait(z + 2))) return fail(issued);
         if (inside) {
-            SmemAccT<float, kBX, kBY, 4, 2, true> A{
-                sm, {slot_of(z - 2), slot_of(z - 1), slot_of(z), slot_of(z + 1), slot_of(z + 2)}, tx, ty};
+            TmaAcc A{sm, {slot_of(z - 2), slot_of(z - 1), slot_of(z), slot_of(z + 1), slot_of(z + 2)}, tx, ty};
             if (z == zbeg) {
 #pragma unroll
                 for (int dz = -2; dz <= 1; ++dz) aq[dz + 2] = A.gxx_gyy(dz, k);
@@ -1031,7 +1036,7 @@ __global__ void __launch_bounds__(kMThreads, kMBlocks)
              float* __restrict__ Wnext, int* __restrict__ err, int zlen, int skip_plane) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     if (!tma_ring_aligned(smem_raw, err)) return;
-    const unsigned bar0 = smem_u32(smem_raw + kMSlots * kMSlotBytes);
+    const unsigned bar0 = smem_u32(smem_raw + kMBarOff);
     if (threadIdx.x == 0) mbar_init_ring(bar0);
     __syncthreads();
     unsigned phase = 0;
@@ -1055,18 +1060,20 @@ struct TmaItem {
     df64* Qs;
     float* Wnext;
 };
-// Two blocks per SM need 2 x (ring + item, in 128-byte units) + 2 x 1 KB of the
-// SM's 228 KB: the item may take at most 464 bytes beside the 115,248-byte ring.
-static_assert(kMBlocks == 1 || sizeof(TmaItem) <= 464, "TmaItem too large for two batched TMA blocks per SM");
+// Two blocks per SM need 2 x (ring + barriers + item) + 2 x 1 KB reserved of the
+// SM's 228 KB.
+static_assert(kMBlocks == 1 || 2 * (kMSmem + sizeof(TmaItem) + 1024) <= 228 * 1024,
+              "TmaItem too large for two batched TMA blocks per SM");
+static_assert(kMSmem % 16 == 0, "the instance record follows the mbarriers on a 16-byte boundary");
 
 template <bool RESID>
 __global__ void __launch_bounds__(kMThreads, kMBlocks)
     k_batch_ra_tma(const BatchInst<float>* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
                    int stage, int parity, int* __restrict__ err, int zlen) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    TmaItem& it = *reinterpret_cast<TmaItem*>(smem_raw + kMSlots * kMSlotBytes + 8 * kMSlots);
+    TmaItem& it = *reinterpret_cast<TmaItem*>(smem_raw + kMSmem);
     if (!tma_ring_aligned(smem_raw, err)) return;
-    const unsigned bar0 = smem_u32(smem_raw + kMSlots * kMSlotBytes);
+    const unsigned bar0 = smem_u32(smem_raw + kMBarOff);
     if (threadIdx.x == 0) mbar_init_ring(bar0);
     unsigned phase = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -1252,15 +1259,16 @@ __device__ __forceinline__ void ss_grad_hyb_point(const Grid& g, const Coef<df64
                                                   double* __restrict__ Dv, int idx) {
     const int n = g.n;
     const Nbr s = make_nbr(g, idx);
-    double div = 0.0;
+    // div u = sum_j s_j delta_j u_j with the scales folded into the sum (12 FP64
+    // instructions: 6 DADD + 3 DFMA for the differences, DMUL + 2 DFMA for the sum)
+    double d[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         double t[4];
         taps(W64 + j * (size_t)n, s.c, s.o[j], t);
-        const double gjj = g.inv12h[j] * delta1_taps(t);
-        div = j == 0 ? gjj : div + gjj;
+        d[j] = delta1_taps(t);
     }
-    Dv[s.c] = div;
+    Dv[s.c] = fmx(g.inv12h[0], d[0], fmx(g.inv12h[1], d[1], g.inv12h[2] * d[2]));
     df64 G[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -2266,7 +2274,7 @@ cudaError_t launch_prims_padded(const Grid& g, const Phys& ph, const df64* Q, fl
     return cudaGetLastError();
 }
 
-size_t tma_smem_bytes() { return (size_t)kMSlots * kMSlotBytes + 8 * kMSlots; }
+size_t tma_smem_bytes() { return kMSmem; }
 size_t batch_tma_smem_bytes() { return tma_smem_bytes() + sizeof(TmaItem); }
 
 cudaError_t launch_ra_tma(const CUtensorMap& map, const Grid& g, const Coef<float>& k, const Phys& ph,
