@@ -113,15 +113,17 @@ extern "C" {
 #define FD_DF64 2
 /* FD_F64_DW     binary64 results (the binary64 parity bound of FD_F64) from
  *               mixed arithmetic, store-some family only: the state, the saved
- *               register, the RK update and the pressure p of Eq. 6 (whose
- *               mean is ~70 times its variation at Mach 0.1, so its binary64
- *               rounding is what the smallest momentum component resolves)
- *               are binary64, and the pressure gradient differences the
- *               binary64 pressures exactly; every other term of the residual
- *               and the nine stored velocity gradients use the double-word
- *               arithmetic of FD_DF64 on shifted fields.  About 27 binary64
- *               instructions per point and stage instead of ~260.  No
- *               counterpart in the paper. */
+ *               register, the RK update, the velocities u_i, div u and the
+ *               pressure p of Eq. 6 (whose mean is ~70 times its variation at
+ *               Mach 0.1, so its binary64 rounding is what the smallest
+ *               momentum component resolves) are binary64, and the pressure
+ *               gradient differences the binary64 pressures exactly (their
+ *               p - p0 is held exactly as a double-word at Mach 0.1, within
+ *               2^-48 |p - p0| at higher Mach); every other term of the
+ *               residual and the nine stored velocity gradients use the
+ *               double-word arithmetic of FD_DF64 on shifted fields.  About 45
+ *               binary64 instructions per point and stage instead of ~260.
+ *               No counterpart in the paper. */
 #define FD_F64_DW 3
 
 /* Device allocator callbacks (for example PyTorch's caching allocator).

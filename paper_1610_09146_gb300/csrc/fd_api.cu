@@ -16,7 +16,7 @@
 //         (ghost-padded for the TMA-staged recompute-all kernel; W[0] then
 //         only serves as scratch of the diagnostics and the residual);
 //   Wd[2] df64 and mixed (FD_F64_DW) modes: the ten perturbation fields as
-//         double-words (the mixed mode keeps binary64 u, v, w, p in W[2]);
+//         double-words (the mixed mode keeps binary64 u, v, w in W[2]);
 //   and the reduction scratch.  In the binary32 and df64 modes Q[2] and Qs
 //   hold shifted double-words, converted to and from binary64 at the API.
 #include <cuda_runtime.h>
@@ -173,10 +173,10 @@ Layout plan(long long n, int algorithm, int dtype, size_t wf_points) {
     L.w1 = L.g = L.p = L.d1 = L.d2 = L.wf0 = L.wf1 = L.gf = L.wd0 = L.wd1 = L.gd = L.dv = L.rc = (size_t)-1;
     L.w0 = dtype == FD_DF64 || algorithm == FD_RECOMPUTE_ALL_INLINE
                ? (size_t)-1
-               : take(dtype == FD_F64_DW ? 4 * n * sizeof(double) : f5);
+               : take(dtype == FD_F64_DW ? 3 * n * sizeof(double) : f5);
     if (dtype == FD_F64_DW) {
-        // binary64 state; W[2] the binary64 u, v, w, p; Wd[2] the double-word working fields
-        L.w1 = take(4 * n * sizeof(double));
+        // binary64 state; W[2] the binary64 u, v, w; Wd[2] the double-word working fields
+        L.w1 = take(3 * n * sizeof(double));
         L.wd0 = take(10 * n * sizeof(fd::df64));
         L.wd1 = take(10 * n * sizeof(fd::df64));
         L.gd = take(fd::kGradArrays<fd::df64> * n * sizeof(fd::df64));
@@ -339,7 +339,7 @@ cudaError_t run_stage(fd_handle* h, int s, bool resid, double* out) {
                   [&] { return fd::launch_ss_grad_hyb(g, h->kw, h->Wd[wc] + 5 * n, h->W[wc], h->Gd, h->Dv, h->stream); });
         if (e != cudaSuccess) return e;
         return timed(h, FD_KERNEL_FUSED, [&] {
-            return fd::launch_ss_hyb(g, h->kw, ph, rk, resid, h->Wd[wc], h->Gd, h->Rc, h->Dv, h->W[wc], Qin, Qout, h->Qs,
+            return fd::launch_ss_hyb(g, h->kw, ph, rk, resid, h->Wd[wc], h->Gd, h->Rc, h->Dv, Qin, Qout, h->Qs,
                                      resid ? nullptr : h->Wd[1 - wc], resid ? nullptr : h->W[1 - wc], h->stream);
         });
     }

@@ -417,8 +417,8 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
                                                : fd::kGradArrays<float>;
         h.g = desc[i].algorithm == FD_STORE_SOME ? take(garrays * (size_t)h.n * tsize) : (size_t)-1;
         if (hyb) {
-            h.w64_0 = take(4 * (size_t)h.n * sizeof(double));
-            h.w64_1 = take(4 * (size_t)h.n * sizeof(double));
+            h.w64_0 = take(3 * (size_t)h.n * sizeof(double));
+            h.w64_1 = take(3 * (size_t)h.n * sizeof(double));
             h.dv = take((size_t)h.n * sizeof(double));
             h.rc = take(5 * (size_t)h.n * sizeof(fd::df64));
         }

@@ -75,8 +75,9 @@ cudaError_t launch_ss(const Grid& g, const Coef<T>& k, const Phys& ph, const RKS
 cudaError_t launch_ra_inline(const Grid& g, const Coef<double>& k, const Phys& ph, const RKStage& rk, bool resid,
                              const double* Q64, double* out, double* Qs, cudaStream_t st);
 // Store-some in mixed binary64 / double-word arithmetic (FD_F64_DW): binary64
-// state Q / Qs / out, binary64 velocities and pressure W64 = (u, v, w, p) (4
-// arrays), the ten shifted double-word working fields F (as in the df64 mode)
+// state Q / Qs / out, binary64 velocities W64 = (u, v, w) (3 arrays; the
+// binary64 pressure is kept only as p - p0 in F), the ten shifted double-word
+// working fields F (as in the df64 mode)
 // and the nine double-word gradients of launch_ss_grad<df64> (given the df64
 // coefficients k).  launch_prims_hyb writes F and W64 of a state.
 cudaError_t launch_prims_hyb(const Grid& g, const Phys& ph, const double* Q, df64* F, double* W64,
@@ -85,9 +86,8 @@ cudaError_t launch_prims_hyb(const Grid& g, const Phys& ph, const double* Q, df6
 cudaError_t launch_ss_grad_hyb(const Grid& g, const Coef<df64>& k, const df64* Wf, const double* W64, df64* Gw,
                                double* Dv, cudaStream_t st);
 cudaError_t launch_ss_hyb(const Grid& g, const Coef<df64>& k, const Phys& ph, const RKStage& rk, bool resid,
-                          const df64* F, const df64* Gw, df64* Rc, const double* Dv, const double* W64,
-                          const double* Q64, double* out, double* Qs, df64* Fnext, double* W64next,
-                          cudaStream_t st);
+                          const df64* F, const df64* Gw, df64* Rc, const double* Dv, const double* Q64, double* out,
+                          double* Qs, df64* Fnext, double* W64next, cudaStream_t st);
 template <class T>
 cudaError_t launch_bl_prod(const Grid& g, const T* Qf, const T* Wf, T* P, cudaStream_t st);
 template <class T>
@@ -130,7 +130,7 @@ struct BatchTile {
 
 // One instance of a batch in the mixed binary64 / double-word store-some
 // arithmetic (FD_F64_DW): binary64 state, double-word working fields F,
-// binary64 u, v, w, p (W64), double-word gradients G and binary64 div u (Dv).
+// binary64 u, v, w (W64), double-word gradients G and binary64 div u (Dv).
 // k is the df64 coefficient record with its mean-state terms zeroed (they
 // enter in binary64, c_E = -(rhoE0 + p0)).
 struct alignas(16) BatchHyb {

@@ -1185,9 +1185,9 @@ __global__ void __launch_bounds__(128) k_ss_f32(Grid g, Coef<float> k, Phys ph, 
 //     stored.  The mean of p, 1/(gamma M^2), is ~70 times its variation at
 //     M = 0.1, and its binary64 rounding (one unit is 1.4e-14) is what the
 //     smallest variable, rho w, resolves through -D_z p; the pressure
-//     gradient differences the binary64 values (neighbouring pressures
-//     differ by far less than a factor 2, so each difference is exact), and
-//     only the exact differences move to double-word arithmetic;
+//     gradient differences p - p0, exact in binary64 and held exactly by the
+//     double-word working field at M = 0.1 (ss_hyb_point), so the differences
+//     of the binary64 pressures are exact;
 //   - div u = sum_i D_i u_i from the binary64 velocities (formed by the
 //     gradient pass, k_ss_grad_hyb), for the two terms that carry a mean: -div
 //     in the mass residual and -(rhoE0 + p0) div in the energy residual (the
@@ -1203,16 +1203,16 @@ __global__ void __launch_bounds__(128) k_ss_f32(Grid g, Coef<float> k, Phys ph, 
 // Values move between the formats by integer operations on the IEEE fields
 // (dw_of_f64, f64_of_dw): a conversion instruction would cost a DFMA.
 //
-// Binary64 instructions per point and stage in the fused kernel: 6 pressure
-// differences, 2 FMAs adding the div terms, 5 sums hi + lo of the residual, 10
-// RK FMAs (5 in stage 2), and ~17 for the next stage's primitives (1 / rho,
-// u_i, p, and rho - 1, rho E - rhoE0, p - p0); 14 in the gradient pass (div u).
-// (div u moved from the fused kernel to the gradient pass: fused 3.67 -> 3.23
-// ms, gradients 0.35 -> 0.61 ms per 256^3 stage.)
+// Binary64 instructions per point and stage in the fused pass: 2 FMAs adding
+// the div terms, 5 sums hi + lo of the residual, 10 RK FMAs (5 in stage 2), and
+// ~17 for the next stage's primitives (1 / rho, u_i, p, and rho - 1,
+// rho E - rhoE0, p - p0); 12 in the gradient pass (div u).  (div u moved from
+// the fused kernel to the gradient pass: fused 3.67 -> 3.23 ms, gradients
+// 0.35 -> 0.61 ms per 256^3 stage.)
 
 // Working fields of a binary64 state: the ten shifted double-word fields F and
-// the binary64 velocities and pressure W64 = (u, v, w, p).  u_i and p are the
-// binary64 path's own formulas; rho - 1, rho E - rhoE0 and p - p0 are exact in
+// the binary64 velocities W64 = (u, v, w).  u_i and p are the binary64 path's
+// own formulas; rho - 1, rho E - rhoE0 and p - p0 are exact in
 // binary64 (operands within a factor 2) and then split, and
 // T - 1 = (gamma M^2 (p - p0) - (rho - 1)) / rho is double-word arithmetic
 // (gamma M^2 p0 = 1).
@@ -1236,7 +1236,6 @@ __device__ __forceinline__ void hyb_prims_point(const Phys& ph, const double q[5
     W64[c] = u;
     W64[n + c] = v;
     W64[2 * n + c] = w;
-    W64[3 * n + c] = p;
 }
 
 __global__ void __launch_bounds__(256) k_prims_hyb(Grid g, Phys ph, const double* __restrict__ Q,
@@ -1324,8 +1323,7 @@ __global__ void __launch_bounds__(128, 5) k_ss_hyb_conv(Grid g, Coef<df64> k, co
 template <bool RESID>
 __device__ __forceinline__ void ss_hyb_point(const Grid& g, const Coef<df64>& k, const Phys& ph, const RKStage& rk,
                                              double c_E, const df64* __restrict__ F, const df64* __restrict__ Gw,
-                                             const df64* __restrict__ Rc,
-                                             const double* __restrict__ Dv, const double* __restrict__ W64,
+                                             const df64* __restrict__ Rc, const double* __restrict__ Dv,
                                              const double* __restrict__ Q64, double* __restrict__ out,
                                              double* __restrict__ Qs, df64* __restrict__ Fnext,
                                              double* __restrict__ W64next, int idx) {
@@ -1340,13 +1338,21 @@ __device__ __forceinline__ void ss_hyb_point(const Grid& g, const Coef<df64>& k,
     for (int f = 0; f < 5; ++f) Rw[f] = renorm(add_nn(Rw[f], ld(Rc + (size_t)f * n, idx)));
     // the neighbour offsets again (cheaper than keeping them live through the residual)
     const Nbr s = make_nbr(g, idx);
-    // -D_j p: 8 (p_{+1} - p_{-1}) + (p_{-2} - p_{+2}), differences exact in binary64
-    const double* Pd = W64 + 3 * (size_t)n;
+    // -D_j p: 8 (p_{+1} - p_{-1}) + (p_{-2} - p_{+2}) from the double-word p - p0
+    // of the working fields (hyb_prims_point: the binary64 pressure minus p0,
+    // exact in binary64).  At Mach 0.1 (p0 = 71.4, whose binade holds every
+    // pressure of the flow) p - p0 is a multiple of 2^-46 below 0.5: at most 45
+    // significant bits, so the pair holds it exactly, and each difference of two
+    // taps is exact too (TwoSum of the leading words; the trailing words and the
+    // TwoSum error, multiples of 2^-46 below 2^-24, add exactly).  At higher Mach
+    // p0 is smaller and the pair may round p - p0, to 2^-48 |p - p0|: less than
+    // one unit in the last place of p0 while |p - p0| < p0 / 16.
+    const df64* Pw = F + 8 * (size_t)n;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        double t[4];
-        taps(Pd, s.c, s.o[j], t);
-        const df64 d = scale2(dw_of_f64(t[2] - t[1]), 8.0f) + dw_of_f64(t[0] - t[3]);
+        df64 t[4];
+        taps(Pw, s.c, s.o[j], t);
+        const df64 d = scale2(sub_nn(t[2], t[1]), 8.0f) + sub_nn(t[0], t[3]);
         Rw[1 + j] = fmx(k.cp[j], d, Rw[1 + j]);
     }
     const double div = ld(Dv, s.c);  // binary64 div u of the gradient pass
@@ -1374,12 +1380,12 @@ template <bool RESID>
 __global__ void __launch_bounds__(128, 6) k_ss_hyb(Grid g, Coef<df64> k, Phys ph, RKStage rk, double c_E,
                                                    const df64* __restrict__ F, const df64* __restrict__ Gw,
                                                    const df64* __restrict__ Rc, const double* __restrict__ Dv,
-                                                   const double* __restrict__ W64, const double* __restrict__ Q64,
+                                                   const double* __restrict__ Q64,
                                                    double* __restrict__ out, double* __restrict__ Qs,
                                                    df64* __restrict__ Fnext, double* __restrict__ W64next) {
     const int idx = grid_index();
     if (idx >= g.n) return;
-    ss_hyb_point<RESID>(g, k, ph, rk, c_E, F, Gw, Rc, Dv, W64, Q64, out, Qs, Fnext, W64next, idx);
+    ss_hyb_point<RESID>(g, k, ph, rk, c_E, F, Gw, Rc, Dv, Q64, out, Qs, Fnext, W64next, idx);
 }
 
 // ------------------------------------------------------------------ BL
@@ -1943,9 +1949,8 @@ __global__ void __launch_bounds__(128, 6) k_batch_ss_hyb(const BatchHyb* __restr
         const BatchTile tl = tiles[t];
         stage_inst(I, insts, tl.inst, cur);
         for (int p = threadIdx.x; p < tl.count; p += blockDim.x)
-            ss_hyb_point<false>(I.g, I.k, I.ph, I.rk[stage], I.c_E, I.F[parity], I.G, I.Rc, I.Dv, I.W64[parity],
-                                I.Q[parity], I.Q[1 - parity], I.Qs, I.F[1 - parity], I.W64[1 - parity],
-                                tl.start + p);
+            ss_hyb_point<false>(I.g, I.k, I.ph, I.rk[stage], I.c_E, I.F[parity], I.G, I.Rc, I.Dv, I.Q[parity],
+                                I.Q[1 - parity], I.Qs, I.F[1 - parity], I.W64[1 - parity], tl.start + p);
     }
 }
 
@@ -2406,19 +2411,18 @@ cudaError_t launch_ss_grad_hyb(const Grid& g, const Coef<df64>& k, const df64* W
 }
 
 cudaError_t launch_ss_hyb(const Grid& g, const Coef<df64>& k, const Phys& ph, const RKStage& rk, bool resid,
-                          const df64* F, const df64* Gw, df64* Rc, const double* Dv, const double* W64,
-                          const double* Q64, double* out, double* Qs, df64* Fnext, double* W64next,
-                          cudaStream_t st) {
+                          const df64* F, const df64* Gw, df64* Rc, const double* Dv, const double* Q64, double* out,
+                          double* Qs, df64* Fnext, double* W64next, cudaStream_t st) {
     Coef<df64> kh = k;  // the mean-state terms enter in binary64 (see k_ss_hyb)
     kh.c_rho = df64(0.0f, 0.0f);
     kh.c_E = df64(0.0f, 0.0f);
     const double c_E = -(ph.rhoE0 + ph.p0);
     k_ss_hyb_conv<<<blocks_for(g.n, 128), 128, 0, st>>>(g, kh, F, Gw, Rc);
     if (resid)
-        k_ss_hyb<true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, kh, ph, rk, c_E, F, Gw, Rc, Dv, W64, Q64, out, Qs,
+        k_ss_hyb<true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, kh, ph, rk, c_E, F, Gw, Rc, Dv, Q64, out, Qs,
                                                              Fnext, W64next);
     else
-        k_ss_hyb<false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, kh, ph, rk, c_E, F, Gw, Rc, Dv, W64, Q64, out, Qs,
+        k_ss_hyb<false><<<blocks_for(g.n, 128), 128, 0, st>>>(g, kh, ph, rk, c_E, F, Gw, Rc, Dv, Q64, out, Qs,
                                                               Fnext, W64next);
     return cudaGetLastError();
 }

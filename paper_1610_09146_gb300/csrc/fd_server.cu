@@ -132,8 +132,8 @@ Layout layout_of(const fd_request& r, bool tma) {
                                              : fd::kGradArrays<float>;
     L.g = r.algorithm == FD_STORE_SOME ? take(garrays * n * t) : (size_t)-1;
     if (hyb) {
-        L.w64_0 = take(4 * n * sizeof(double));
-        L.w64_1 = take(4 * n * sizeof(double));
+        L.w64_0 = take(3 * n * sizeof(double));
+        L.w64_1 = take(3 * n * sizeof(double));
         L.dv = take(n * sizeof(double));
         L.rc = take(5 * n * sizeof(fd::df64));
     }
