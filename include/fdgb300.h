@@ -307,7 +307,10 @@ const char* fd_batch_last_error(const fd_batch* b);
  * step count: their kinetic energy and enstrophy become results for
  * fd_server_poll, and their final state stays readable through
  * fd_server_get_state until the first tick after their result was polled,
- * which returns their memory to the arena.  Ticks are
+ * which returns their memory to the arena.  One tick stays in flight: a
+ * tick enqueues its work, then waits only for the previous tick's, so the
+ * solves a tick finishes become results at the next tick (at once when the
+ * tick leaves no solve active).  Ticks are
  * time-sliced: a solve advances by an odd number of RK3 steps per tick, one
  * for the solve with the dearest step of the active set and, for a cheaper
  * solve, as many as fit in that step's time (at most 31, never past its
@@ -356,7 +359,10 @@ size_t fd_server_footprint(const fd_request* req);
 int fd_server_cancel(fd_server* s, long long tag);
 
 /* Admit, advance every active solve by its steps for this tick (time-sliced,
- * see above), retire finished solves.  Synchronises the server's stream.
+ * see above), retire the solves the previous tick finished (and this tick's,
+ * if it leaves no solve active).  Waits for the previous tick's work on the
+ * server's stream (for its own too when it leaves no solve active); an error
+ * of a kernel's bounded wait is reported by the tick that retires the work.
  * *active_out (may be NULL) receives the number of solves active during this
  * tick.  Errors: FD_ECUDA. */
 int fd_server_tick(fd_server* s, int* active_out);
@@ -368,8 +374,8 @@ int fd_server_poll(fd_server* s, fd_result* out, int max, int* n_out);
 
 /* Copy the final state of a finished solve (layout and rules of fd_get_state:
  * 5*nx*ny*nz doubles, host or device dst, binary64 also for FD_F32_ACCDW
- * requests); valid from the tick that finished it until the first tick after
- * its result was polled.  If several kept solves share the tag, the one that
+ * requests); valid from the tick that finished it (before its result is
+ * retired, too) until the first tick after its result was polled.  If several kept solves share the tag, the one that
  * finished first.  Synchronises the server's stream.  Errors: FD_EINVAL (no
  * such solve, wrong n_elems, NULL), FD_ECUDA. */
 int fd_server_get_state(fd_server* s, long long tag, double* dst, size_t n_elems, int dst_is_device);

@@ -138,8 +138,10 @@ class Server:
     """Continuous-batching server (fd_server_* in include/fdgb300.h).
 
     submit(dict) queues a solve (keys: n, steps, Re, Mach, Pr, gamma, dt, dtype, algorithm,
-    tile_points, tag); tick() admits what fits, advances every active solve one RK3 step and
-    retires finished ones; poll() returns finished results as dicts."""
+    tile_points, tag); tick() admits what fits, advances every active solve by its steps for
+    the tick and retires the solves the previous tick finished (one tick stays in flight; a
+    tick that leaves no solve active retires its own at once); poll() returns finished
+    results as dicts."""
 
     def __init__(self, arena_bytes, max_active=256, stream=None, use_torch_allocator=True):
         import torch

@@ -11,13 +11,17 @@
 // active solves.  All active solves share one ping-pong parity: a newly
 // admitted solve writes its initial state into Q[parity], so every tick runs
 // one RK3 step of every active solve with the batched kernels, one group per
-// (dtype, family).  A tick ends synchronised; finished solves are retired
-// with their diagnostics; their state stays readable (fd_server_get_state)
-// until the first tick after their result was polled, which returns their
-// memory to the arena.
+// (dtype, family).  One tick stays in flight: a tick enqueues its work and
+// the diagnostics of the solves it finishes, then waits for the previous
+// tick's work only, and retires that tick's finished solves, so the device
+// runs tick k while the host plans tick k+1 (a tick that leaves no solve
+// active waits for its own work and retires at once).  A retired solve's
+// state stays readable (fd_server_get_state) until the first tick after its
+// result was polled, which returns its memory to the arena.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdlib>
 #include <cstdio>
@@ -174,6 +178,19 @@ struct Finished {
     int n;
     int parity;
     bool polled = false;
+    int done = 0;  // steps taken
+};
+
+// The solves one tick finished, waiting for that tick's work: the event
+// recorded after it, and the host slot its diagnostics and the staging-error
+// word are copied to (pinned; two slots, as two ticks can be outstanding).
+struct Pending {
+    std::vector<Finished> solves;
+    cudaEvent_t ev = nullptr;
+    double* host_res = nullptr;  // 2 per solve: KE, enstrophy
+    int* host_err = nullptr;
+    bool armed = false, check_err = false;
+    long long tick = 0;
 };
 
 // Time slicing.  A tick advances every active solve by an odd number of steps
@@ -216,6 +233,8 @@ struct fd_server {
     std::vector<Active> active;
     std::vector<fd_result> done;
     std::vector<Finished> finished;  // retired solves whose state is still kept
+    Pending pending[2];              // by tick parity: finished, not yet retired
+    void* host_pinned = nullptr;     // both slots' results and error words
     bool dirty = true;
     int parity = 0;
     long long submitted = 0, completed = 0, ticks = 0;
@@ -467,12 +486,53 @@ cudaError_t run_group_hyb(fd_server* s, int round) {
     return cudaSuccess;
 }
 
+// Retire the solves of pending slot i: wait for the tick that finished them,
+// check the staging-error word of that tick, and turn them into results (in
+// the order the tick finished them) whose states stay kept.
+int retire(fd_server* s, int i) {
+    Pending& P = s->pending[i];
+    if (!P.armed) return FD_OK;
+    P.armed = false;
+    cudaError_t e = cudaEventSynchronize(P.ev);
+    if (e != cudaSuccess) return s->cuda_fail(e, "fd_server_tick");
+    if (P.check_err && *P.host_err) {
+        const int v = *P.host_err;
+        P.solves.clear();
+        return s->fail(FD_ECUDA, "fd_server_tick: %s; the states are not valid",
+                       v == 2 ? "the TMA ring was not 128-byte aligned" : "a staging wait in a kernel ran out");
+    }
+    for (size_t k = 0; k < P.solves.size(); ++k) {
+        const Finished& f = P.solves[k];
+        const double ke = P.host_res[2 * k], en = P.host_res[2 * k + 1];
+        const int st = std::isfinite(ke) && std::isfinite(en) ? FD_OK : FD_EUNSTABLE;
+        s->done.push_back({f.r.tag, st, f.done, ke, en});
+        s->finished.push_back(f);
+        s->completed++;
+    }
+    P.solves.clear();
+    return FD_OK;
+}
+
+// Retire every outstanding tick, oldest first.
+int retire_all(fd_server* s) {
+    int first = s->pending[0].tick <= s->pending[1].tick ? 0 : 1;
+    int rc = retire(s, first);
+    if (rc == FD_OK) rc = retire(s, first ^ 1);
+    return rc;
+}
+
 void release_all(fd_server* s) {
     if (s->stream || s->arena_ptr) cudaStreamSynchronize(s->stream);
     s->dev_free(s->tab, s->tab_bytes);
     s->dev_free(s->fixed, s->fixed_bytes);
     s->dev_free(s->arena_ptr, s->arena.capacity());
     s->tab = s->fixed = s->arena_ptr = nullptr;
+    for (auto& P : s->pending) {
+        if (P.ev) cudaEventDestroy(P.ev);
+        P.ev = nullptr;
+    }
+    if (s->host_pinned) cudaFreeHost(s->host_pinned);
+    s->host_pinned = nullptr;
 }
 
 }  // namespace
@@ -519,7 +579,22 @@ int fd_server_create(fd_server** out, size_t arena_bytes, int max_active, const 
     s->kerr = reinterpret_cast<int*>(reinterpret_cast<char*>(s->results) + align256(2 * (size_t)max_active * sizeof(double)));
     const char* off_env = std::getenv("FDGB300_NO_TMA");
     s->tma_allowed = !(off_env && off_env[0] == '1');
-    cudaError_t e = cudaMemsetAsync(s->kerr, 0, sizeof(int), s->stream);
+    // two pending slots: 2 results per solve, then an error word, each slot
+    const size_t slot_bytes = align256(2 * (size_t)max_active * sizeof(double) + sizeof(int));
+    cudaError_t e = cudaMallocHost(&s->host_pinned, 2 * slot_bytes);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        Pending& P = s->pending[i];
+        P.host_res = reinterpret_cast<double*>(static_cast<char*>(s->host_pinned) + i * slot_bytes);
+        P.host_err = reinterpret_cast<int*>(P.host_res + 2 * (size_t)max_active);
+        *P.host_err = 0;
+        e = cudaEventCreateWithFlags(&P.ev, cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        release_all(s);
+        delete s;
+        return fail_global(FD_ENOMEM, "fd_server_create: host result buffers: %s", cudaGetErrorString(e));
+    }
+    e = cudaMemsetAsync(s->kerr, 0, sizeof(int), s->stream);
     if (e == cudaSuccess && s->tma_allowed) {
         e = fd::prepare_ra_tma();
         s->tma_blocks = fd::batch_tma_blocks_per_sm();
@@ -626,7 +701,7 @@ int fd_server_tick(fd_server* s, int* active_out) {
         s->dirty = true;
     }
     if (active_out) *active_out = (int)s->active.size();
-    if (s->active.empty()) return FD_OK;
+    if (s->active.empty()) return retire_all(s);  // nothing to overlap with
     // 3. steps per solve, tables, then k RK3 steps of every active solve
     double dearest = 0;
     for (auto& a : s->active) dearest = std::max(dearest, step_cost(a.r));
@@ -657,8 +732,17 @@ int fd_server_tick(fd_server* s, int* active_out) {
         a.fresh = false;
         a.done += a.k;
     }
-    // 4. diagnostics of finished solves (scratch: the working fields the next
-    //    stage would overwrite), then synchronise and retire them
+    // 4. diagnostics of the solves this tick finishes (scratch: the working
+    //    fields the next stage would overwrite) and the staging-error word,
+    //    copied to this tick's pending slot; then wait for the previous tick
+    //    only and retire its solves, so the work just enqueued keeps the device
+    //    busy while the caller plans the next tick.
+    const int slot = (int)(s->ticks & 1);
+    Pending& P = s->pending[slot];
+    if (P.armed) {  // left by a tick that failed before it retired this slot
+        const int rc = retire(s, slot);
+        if (rc != FD_OK) return rc;
+    }
     std::vector<int> fin;
     for (int i = 0; i < (int)s->active.size(); ++i)
         if (s->active[i].done >= s->active[i].r.steps) fin.push_back(i);
@@ -677,31 +761,26 @@ int fd_server_tick(fd_server* s, int* active_out) {
         double* Wv = reinterpret_cast<double*>(b + (s->parity ? a.L.w0 : a.L.w1));
         if (e == cudaSuccess) e = fd::launch_diagnostics_f64(g, Q, Wv, s->partial, s->results + 2 * k, s->stream);
     }
-    std::vector<double> res(2 * fin.size());
     if (e == cudaSuccess && !fin.empty())
-        e = cudaMemcpyAsync(res.data(), s->results, res.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        e = cudaMemcpyAsync(P.host_res, s->results, 2 * fin.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                            s->stream);
+    P.check_err = s->ntiles[1][2][0] != 0;
+    if (e == cudaSuccess && P.check_err)
+        e = cudaMemcpyAsync(P.host_err, s->kerr, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(P.ev, s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "fd_server_tick");
-    if (s->ntiles[1][2][0]) {
-        int v = 0;
-        e = cudaMemcpyAsync(&v, s->kerr, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-        if (e != cudaSuccess) return s->cuda_fail(e, "fd_server_tick");
-        if (v)
-            return s->fail(FD_ECUDA, "fd_server_tick: %s; the states are not valid",
-                           v == 2 ? "the TMA ring was not 128-byte aligned" : "a staging wait in a kernel ran out");
-    }
+    P.armed = true;
+    P.tick = s->ticks;
     for (size_t k = fin.size(); k-- > 0;) {
-        Active& a = s->active[fin[k]];
-        double ke = res[2 * k], en = res[2 * k + 1];
-        int st = std::isfinite(ke) && std::isfinite(en) ? FD_OK : FD_EUNSTABLE;
-        s->done.push_back({a.r.tag, st, a.done, ke, en});
-        s->finished.push_back({a.r, a.L, a.off, a.n, s->parity, false});
+        const Active& a = s->active[fin[k]];
+        Finished f{a.r, a.L, a.off, a.n, s->parity, false, a.done};
+        P.solves.insert(P.solves.begin(), f);
         s->active.erase(s->active.begin() + fin[k]);
-        s->completed++;
         s->dirty = true;
     }
-    return FD_OK;
+    int rc = retire(s, slot ^ 1);
+    if (rc == FD_OK && s->active.empty()) rc = retire(s, slot);
+    return rc;
 }
 
 int fd_server_poll(fd_server* s, fd_result* out, int max, int* n_out) {
@@ -731,6 +810,11 @@ int fd_server_get_state(fd_server* s, long long tag, double* dst, size_t n_elems
             f = &x;
             break;
         }
+    // finished by an outstanding tick (the copy below waits for its work)
+    const int first = s->pending[0].tick <= s->pending[1].tick ? 0 : 1;
+    for (int i : {first, first ^ 1})
+        for (const auto& x : s->pending[i].solves)
+            if (!f && x.r.tag == tag) f = &x;
     if (!f) return s->fail(FD_EINVAL, "fd_server_get_state: no kept state of a finished solve with tag %lld", tag);
     if (n_elems != 5 * (size_t)f->n)
         return s->fail(FD_EINVAL, "fd_server_get_state: n_elems = %zu, expected %zu", n_elems, 5 * (size_t)f->n);
