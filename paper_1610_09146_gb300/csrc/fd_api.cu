@@ -335,11 +335,8 @@ cudaError_t run_stage(fd_handle* h, int s, bool resid, double* out) {
             if (e != cudaSuccess) return e;
             h->wvalid = true;
         }
-        e = timed(h, FD_KERNEL_GRAD,
-                  [&] { return fd::launch_ss_grad_hyb(g, h->kw, h->Wd[wc] + 5 * n, h->W[wc], h->Gd, h->Dv, h->stream); });
-        if (e != cudaSuccess) return e;
         return timed(h, FD_KERNEL_FUSED, [&] {
-            return fd::launch_ss_hyb(g, h->kw, ph, rk, resid, h->Wd[wc], h->Gd, h->Rc, h->Dv, Qin, Qout, h->Qs,
+            return fd::launch_ss_hyb(g, h->kw, ph, rk, resid, h->Wd[wc], h->W[wc], h->Gd, h->Rc, h->Dv, Qin, Qout, h->Qs,
                                      resid ? nullptr : h->Wd[1 - wc], resid ? nullptr : h->W[1 - wc], h->stream);
         });
     }

@@ -236,14 +236,12 @@ cudaError_t enqueue_step(fd_batch* b, int p, cudaStream_t st0, cudaStream_t st1)
     return cudaSuccess;
 }
 
-// Mixed store-some batch (FD_F64_DW): three stages of gradients then fused.
+// Mixed store-some batch (FD_F64_DW): three stages of the two fused kernels
+// (the first also forms the gradients).
 cudaError_t enqueue_step_hyb(fd_batch* b, int p, cudaStream_t st) {
     auto* I = static_cast<const fd::BatchHyb*>(b->d_inst);
     cudaError_t e;
     for (int s = 0, q = p; s < 3; ++s, q ^= 1) {
-        e = b->prof.timed(st, FD_KERNEL_GRAD,
-                          [&] { return fd::launch_batch_grad_hyb(I, b->d_ss, b->n_ss, q, b->grid_grad, st); });
-        if (e != cudaSuccess) return e;
         e = b->prof.timed(st, FD_KERNEL_FUSED, [&] {
             return fd::launch_batch_ss_hyb(I, b->d_ss, b->n_ss, s, q, b->grid_ra_fused, b->grid_ss_fused, st);
         });
@@ -463,9 +461,9 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     if (sms <= 0) sms = 152;
     if (hyb) {  // (the RA slot holds the grid of the first fused kernel: a mixed batch has no RA)
-        b->grid_ss_fused = sms * fd::batch_hyb_blocks_per_sm(2);
-        b->grid_ra_fused = sms * fd::batch_hyb_blocks_per_sm(3);
-        b->grid_grad = sms * fd::batch_hyb_blocks_per_sm(1);
+        b->grid_ss_fused = sms * fd::batch_hyb_blocks_per_sm(1);
+        b->grid_ra_fused = sms * fd::batch_hyb_blocks_per_sm(2);
+        b->grid_grad = b->grid_ss_fused;  // (no gradient pass of its own)
     } else if (dtype == FD_F64) {
         b->grid_ss_fused = grid_for<double>(sms, true, true);
         b->grid_ra_fused = grid_for<double>(sms, true, false);

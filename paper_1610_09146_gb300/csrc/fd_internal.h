@@ -79,15 +79,15 @@ cudaError_t launch_ra_inline(const Grid& g, const Coef<double>& k, const Phys& p
 // binary64 pressure is kept only as p - p0 in F), the ten shifted double-word
 // working fields F (as in the df64 mode)
 // and the nine double-word gradients of launch_ss_grad<df64> (given the df64
-// coefficients k).  launch_prims_hyb writes F and W64 of a state.
+// coefficients k) with binary64 div u (Dv, from the binary64 velocities).
+// launch_prims_hyb writes F and W64 of a state.
 cudaError_t launch_prims_hyb(const Grid& g, const Phys& ph, const double* Q, df64* F, double* W64,
                              cudaStream_t st);
-// The gradient pass also writes div u in binary64 (Dv, from the binary64 velocities).
-cudaError_t launch_ss_grad_hyb(const Grid& g, const Coef<df64>& k, const df64* Wf, const double* W64, df64* Gw,
-                               double* Dv, cudaStream_t st);
+// The fused pass: the gradients, div u and the convective part (one kernel),
+// then the rest of the residual and the update (a second).
 cudaError_t launch_ss_hyb(const Grid& g, const Coef<df64>& k, const Phys& ph, const RKStage& rk, bool resid,
-                          const df64* F, const df64* Gw, df64* Rc, const double* Dv, const double* Q64, double* out,
-                          double* Qs, df64* Fnext, double* W64next, cudaStream_t st);
+                          const df64* F, const double* W64, df64* Gw, df64* Rc, double* Dv, const double* Q64,
+                          double* out, double* Qs, df64* Fnext, double* W64next, cudaStream_t st);
 template <class T>
 cudaError_t launch_bl_prod(const Grid& g, const T* Qf, const T* Wf, T* P, cudaStream_t st);
 template <class T>
@@ -147,13 +147,11 @@ struct alignas(16) BatchHyb {
     double* Dv;
     df64* Rc;  // convective part of the residual (first of the two fused kernels)
 };
-int batch_hyb_blocks_per_sm(int kernel);  // 0: primitives, 1: gradients, 2: fused, 3: fused convective part
+int batch_hyb_blocks_per_sm(int kernel);  // 0: primitives, 1: fused (second kernel), 2: gradients + convective part
 cudaError_t launch_batch_prims_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int parity, int grid,
                                    cudaStream_t st);
-cudaError_t launch_batch_grad_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int parity, int grid,
-                                  cudaStream_t st);
-// The two fused kernels of a stage (convective part, then the rest and the update); grid_conv and
-// grid the persistent grids of the two.
+// The two fused kernels of a stage (gradients, div u and the convective part, then the rest and the
+// update); grid_conv and grid the persistent grids of the two.
 cudaError_t launch_batch_ss_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int stage, int parity,
                                 int grid_conv, int grid, cudaStream_t st);
 

@@ -1188,8 +1188,8 @@ __global__ void __launch_bounds__(128) k_ss_f32(Grid g, Coef<float> k, Phys ph, 
 //     gradient differences p - p0, exact in binary64 and held exactly by the
 //     double-word working field at M = 0.1 (ss_hyb_point), so the differences
 //     of the binary64 pressures are exact;
-//   - div u = sum_i D_i u_i from the binary64 velocities (formed by the
-//     gradient pass, k_ss_grad_hyb), for the two terms that carry a mean: -div
+//   - div u = sum_i D_i u_i from the binary64 velocities (formed with the
+//     gradients by the first fused kernel), for the two terms that carry a mean: -div
 //     in the mass residual and -(rhoE0 + p0) div in the energy residual (the
 //     mean energy and the mean pressure work; ~250 div at M = 0.1, which would
 //     magnify a double-word div 250-fold);
@@ -1249,13 +1249,14 @@ __global__ void __launch_bounds__(256) k_prims_hyb(Grid g, Phys ph, const double
     hyb_prims_point(ph, q, F, W64, n, idx);
 }
 
-// Gradient pass of the mixed kernel: the nine double-word gradients as
-// k_ss_grad<df64> forms them, and div u = sum_i D_i u_i in binary64 from the
-// binary64 velocities W64 (as the binary64 gradient pass forms D_i u_i), which
-// the fused kernel reads for the two mean-state terms.
+// Gradients of the mixed kernels at one point: the nine double-word gradients
+// as k_ss_grad<df64> forms them (stored, and returned in G), and div u =
+// sum_i D_i u_i in binary64 from the binary64 velocities W64 (as the binary64
+// gradient pass forms D_i u_i), which the second fused kernel reads for the
+// two mean-state terms.
 __device__ __forceinline__ void ss_grad_hyb_point(const Grid& g, const Coef<df64>& k, const df64* __restrict__ Wf,
                                                   const double* __restrict__ W64, df64* __restrict__ Gw,
-                                                  double* __restrict__ Dv, int idx) {
+                                                  double* __restrict__ Dv, int idx, df64 G[3][3]) {
     const int n = g.n;
     const Nbr s = make_nbr(g, idx);
     // div u = sum_j s_j delta_j u_j with the scales folded into the sum (12 FP64
@@ -1268,7 +1269,6 @@ __device__ __forceinline__ void ss_grad_hyb_point(const Grid& g, const Coef<df64
         d[j] = delta1_taps(t);
     }
     Dv[s.c] = fmx(g.inv12h[0], d[0], fmx(g.inv12h[1], d[1], g.inv12h[2] * d[2]));
-    df64 G[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -1279,13 +1279,6 @@ __device__ __forceinline__ void ss_grad_hyb_point(const Grid& g, const Coef<df64
             Gw[(3 * i + j) * n + s.c] = G[i][j];
         }
     store_pair_sums(G, Gw + 9 * (size_t)n, n, s.c);
-}
-__global__ void __launch_bounds__(256) k_ss_grad_hyb(Grid g, Coef<df64> k, const df64* __restrict__ Wf,
-                                                    const double* __restrict__ W64, df64* __restrict__ Gw,
-                                                    double* __restrict__ Dv) {
-    const int idx = grid_index();
-    if (idx >= g.n) return;
-    ss_grad_hyb_point(g, k, Wf, W64, Gw, Dv, idx);
 }
 
 // Fused residual + RK update + next-stage working fields.  F / W64: the
@@ -1304,20 +1297,35 @@ __global__ void __launch_bounds__(256) k_ss_grad_hyb(Grid g, Coef<df64> k, const
 // loads, so the warps pay: 256^3 step 11.53 ms (one kernel) -> 11.01 (two, four
 // blocks each) -> 9.63-9.89 (five and six blocks; four to eight blocks of either
 // measured within 1.3 % of this).
+// The gradient pass rides in this kernel: the point's nine gradients and
+// binary64 div u (ss_grad_hyb_point, the same bits) are stored for the second
+// kernel, whose stencils read them at neighbouring points, and the convective
+// part takes G_ii from registers.  Its binary64 div u fills the FP64 pipe,
+// idle in the double-word convective sums.
+template <class Acc>
+struct RegGradAcc : Acc {
+    const df64 (*Gr)[3];
+    __device__ __forceinline__ df64 grad(int i, int j) const { return Gr[i][j]; }
+};
 __device__ __forceinline__ void ss_hyb_conv_point(const Grid& g, const Coef<df64>& k, const df64* __restrict__ F,
-                                                  const df64* __restrict__ Gw, df64* __restrict__ Rc, int idx) {
+                                                  const double* __restrict__ W64, df64* __restrict__ Gw,
+                                                  double* __restrict__ Dv, df64* __restrict__ Rc, int idx) {
     const int n = g.n;
+    df64 G[3][3];
+    ss_grad_hyb_point(g, k, F + 5 * (size_t)n, W64, Gw, Dv, idx, G);
     const Nbr s = make_nbr(g, idx);
     df64 R[5];
-    fused_residual<df64, true, GlobalAcc<df64>, false, 1>(GlobalAcc<df64>{s, n, F, F + 5 * (size_t)n, Gw}, k, R);
+    using A = RegGradAcc<GlobalAcc<df64>>;
+    fused_residual<df64, true, A, false, 1>(A{{s, n, F, F + 5 * (size_t)n, Gw}, G}, k, R);
 #pragma unroll
     for (int f = 0; f < 5; ++f) Rc[(size_t)f * n + idx] = R[f];
 }
 __global__ void __launch_bounds__(128, 5) k_ss_hyb_conv(Grid g, Coef<df64> k, const df64* __restrict__ F,
-                                                       const df64* __restrict__ Gw, df64* __restrict__ Rc) {
+                                                       const double* __restrict__ W64, df64* __restrict__ Gw,
+                                                       double* __restrict__ Dv, df64* __restrict__ Rc) {
     const int idx = grid_index();
     if (idx >= g.n) return;
-    ss_hyb_conv_point(g, k, F, Gw, Rc, idx);
+    ss_hyb_conv_point(g, k, F, W64, Gw, Dv, Rc, idx);
 }
 
 template <bool RESID>
@@ -1906,7 +1914,7 @@ __global__ void __launch_bounds__(256) k_batch_prims(const BatchInst<T>* __restr
 }
 
 // Batched mixed store-some: the single-instance per-point code (hyb_prims_point,
-// ss_grad_hyb_point, ss_hyb_point) over the tile work lists, so a batched
+// ss_hyb_conv_point, ss_hyb_point) over the tile work lists, so a batched
 // instance evolves bitwise as it would alone.
 __global__ void __launch_bounds__(256) k_batch_prims_hyb(const BatchHyb* __restrict__ insts,
                                                          const BatchTile* __restrict__ tiles, int ntiles,
@@ -1924,19 +1932,6 @@ __global__ void __launch_bounds__(256) k_batch_prims_hyb(const BatchHyb* __restr
             for (int f = 0; f < 5; ++f) q[f] = I.Q[parity][f * n + c];
             hyb_prims_point(I.ph, q, I.F[parity], I.W64[parity], n, c);
         }
-    }
-}
-
-__global__ void __launch_bounds__(256) k_batch_grad_hyb(const BatchHyb* __restrict__ insts,
-                                                        const BatchTile* __restrict__ tiles, int ntiles,
-                                                        int parity) {
-    __shared__ BatchHyb I;
-    int cur = -1;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const BatchTile tl = tiles[t];
-        stage_inst(I, insts, tl.inst, cur);
-        for (int p = threadIdx.x; p < tl.count; p += blockDim.x)
-            ss_grad_hyb_point(I.g, I.k, I.F[parity] + 5 * (size_t)I.g.n, I.W64[parity], I.G, I.Dv, tl.start + p);
     }
 }
 
@@ -1963,15 +1958,14 @@ __global__ void __launch_bounds__(128, 5) k_batch_ss_hyb_conv(const BatchHyb* __
         const BatchTile tl = tiles[t];
         stage_inst(I, insts, tl.inst, cur);
         for (int p = threadIdx.x; p < tl.count; p += blockDim.x)
-            ss_hyb_conv_point(I.g, I.k, I.F[parity], I.G, I.Rc, tl.start + p);
+            ss_hyb_conv_point(I.g, I.k, I.F[parity], I.W64[parity], I.G, I.Dv, I.Rc, tl.start + p);
     }
 }
 
 int batch_hyb_blocks_per_sm(int kernel) {
     int b = 0;
     cudaError_t e = kernel == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_prims_hyb, 256, 0)
-                    : kernel == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_grad_hyb, 256, 0)
-                    : kernel == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_ss_hyb, 128, 0)
+                    : kernel == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_ss_hyb, 128, 0)
                                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_ss_hyb_conv, 128, 0);
     return e == cudaSuccess && b > 0 ? b : 1;
 }
@@ -1983,12 +1977,6 @@ cudaError_t launch_batch_prims_hyb(const BatchHyb* insts, const BatchTile* tiles
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_grad_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int parity, int grid,
-                                  cudaStream_t st) {
-    if (ntiles <= 0) return cudaSuccess;
-    k_batch_grad_hyb<<<grid, 256, 0, st>>>(insts, tiles, ntiles, parity);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_batch_ss_hyb(const BatchHyb* insts, const BatchTile* tiles, int ntiles, int stage, int parity,
                                 int grid_conv, int grid, cudaStream_t st) {
@@ -2404,20 +2392,15 @@ cudaError_t launch_prims_hyb(const Grid& g, const Phys& ph, const double* Q, df6
     return cudaGetLastError();
 }
 
-cudaError_t launch_ss_grad_hyb(const Grid& g, const Coef<df64>& k, const df64* Wf, const double* W64, df64* Gw,
-                               double* Dv, cudaStream_t st) {
-    k_ss_grad_hyb<<<blocks_for(g.n, 256), 256, 0, st>>>(g, k, Wf, W64, Gw, Dv);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_ss_hyb(const Grid& g, const Coef<df64>& k, const Phys& ph, const RKStage& rk, bool resid,
-                          const df64* F, const df64* Gw, df64* Rc, const double* Dv, const double* Q64, double* out,
-                          double* Qs, df64* Fnext, double* W64next, cudaStream_t st) {
+                          const df64* F, const double* W64, df64* Gw, df64* Rc, double* Dv, const double* Q64,
+                          double* out, double* Qs, df64* Fnext, double* W64next, cudaStream_t st) {
     Coef<df64> kh = k;  // the mean-state terms enter in binary64 (see k_ss_hyb)
     kh.c_rho = df64(0.0f, 0.0f);
     kh.c_E = df64(0.0f, 0.0f);
     const double c_E = -(ph.rhoE0 + ph.p0);
-    k_ss_hyb_conv<<<blocks_for(g.n, 128), 128, 0, st>>>(g, kh, F, Gw, Rc);
+    k_ss_hyb_conv<<<blocks_for(g.n, 128), 128, 0, st>>>(g, kh, F, W64, Gw, Dv, Rc);
     if (resid)
         k_ss_hyb<true><<<blocks_for(g.n, 128), 128, 0, st>>>(g, kh, ph, rk, c_E, F, Gw, Rc, Dv, Q64, out, Qs,
                                                              Fnext, W64next);

@@ -465,7 +465,8 @@ cudaError_t run_group(fd_server* s, int d, int round) {
     return cudaSuccess;
 }
 
-// The mixed (FD_F64_DW) group: store-some only, gradients then fused per stage.
+// The mixed (FD_F64_DW) group: store-some only, the two fused kernels per stage (the first also
+// forms the gradients).
 cudaError_t run_group_hyb(fd_server* s, int round) {
     auto* I = static_cast<const fd::BatchHyb*>(s->inst[2]);
     cudaError_t e;
@@ -477,10 +478,8 @@ cudaError_t run_group_hyb(fd_server* s, int round) {
             return e;
     }
     if (!n) return cudaSuccess;
-    const int gg = s->sms * fd::batch_hyb_blocks_per_sm(1), gs = s->sms * fd::batch_hyb_blocks_per_sm(2),
-              gc = s->sms * fd::batch_hyb_blocks_per_sm(3);
+    const int gs = s->sms * fd::batch_hyb_blocks_per_sm(1), gc = s->sms * fd::batch_hyb_blocks_per_sm(2);
     for (int st = 0, p = s->parity ^ (round & 1); st < 3; ++st, p ^= 1) {
-        if ((e = fd::launch_batch_grad_hyb(I, s->tiles[2][0], n, p, gg, s->stream)) != cudaSuccess) return e;
         if ((e = fd::launch_batch_ss_hyb(I, s->tiles[2][0], n, st, p, gc, gs, s->stream)) != cudaSuccess) return e;
     }
     return cudaSuccess;
