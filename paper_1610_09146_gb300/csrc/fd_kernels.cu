@@ -422,9 +422,10 @@ struct GlobalAcc {
 // PGRAD = false leaves the pressure gradient -D_i p out of the momentum
 // residuals (the mixed binary64 / double-word kernel adds it in binary64).
 // PART (not in the binary64 tap-weighted form): 0 the whole residual; 1 the
-// convective part (Q_f (-div/2), the convective sums, the pressure terms, the
-// mean-state terms); 2 the rest (heat flux, viscous stress divergence and its
-// work, dissipation), so that two kernels can each evaluate one part.
+// convective part (Q_f (-div/2), the convective sums, the pressure gradient,
+// the mean-state terms); 2 the rest (pressure work, heat flux, viscous stress
+// divergence and its work, dissipation), so that two kernels can each
+// evaluate one part.
 template <class T, bool STORED_G, class Acc, bool PGRAD = true, int PART = 0>
 __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T R[5]) {
     static_assert(PART == 0 || !kTapWeighted<T>, "the binary64 tap-weighted residual is not split");
@@ -568,6 +569,17 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
                 R[f] = acc(k.c1[j], delta1_prod(qt, st), R[f]);
             }
             if constexpr (PGRAD) R[1 + j] = acc(k.cp[j], delta1_taps(pt), R[1 + j]);
+            if constexpr (PART == 0) R[4] = acc(k.cp[j], delta1_prod(pt, ut), R[4]);
+        }
+    }
+    // split residual: the pressure work goes with the rest, whose pressure
+    // gradient and viscous terms load the same p and u_j taps
+    if constexpr (PART == 2) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T ut[4], pt[4];
+            A.taps(U + j, j, ut);
+            A.taps(P, j, pt);
             R[4] = acc(k.cp[j], delta1_prod(pt, ut), R[4]);
         }
     }
@@ -1291,12 +1303,13 @@ __device__ __forceinline__ void ss_grad_hyb_point(const Grid& g, const Coef<df64
 // The convective part of the residual (PART 1), into Rc for ss_hyb_point.  The
 // residual is split over two kernels so that each runs at a higher occupancy
 // than the whole residual could (128 registers and 84 bytes of spill at 16 warps
-// per SM): this one at five blocks of 128 threads per SM (96 registers), the
-// rest with the update at six (80 registers, 8 bytes of spill), for 40 bytes per
-// point written and read again.  The kernels are latency-bound on their tap
-// loads, so the warps pay: 256^3 step 11.53 ms (one kernel) -> 11.01 (two, four
-// blocks each) -> 9.63-9.89 (five and six blocks; four to eight blocks of either
-// measured within 1.3 % of this).
+// per SM): both at five blocks of 128 threads per SM (96 registers), for 40
+// bytes per point written and read again.  The kernels are latency-bound on
+// their tap loads, so the warps pay: 256^3 step 11.53 ms (one kernel) -> 11.01
+// (two, four blocks each) -> 9.63-9.89 (five and six blocks; four to eight
+// blocks of either measured within 1.3 % of this).  The pressure work later
+// moved to the second kernel, which loads its taps anyway (9.10 -> 9.00 ms at
+// five blocks; 9.22 at six, where it spilled).
 // The gradient pass rides in this kernel: the point's nine gradients and
 // binary64 div u (ss_grad_hyb_point, the same bits) are stored for the second
 // kernel, whose stencils read them at neighbouring points, and the convective
@@ -1385,7 +1398,7 @@ __device__ __forceinline__ void ss_hyb_point(const Grid& g, const Coef<df64>& k,
     }
 }
 template <bool RESID>
-__global__ void __launch_bounds__(128, 6) k_ss_hyb(Grid g, Coef<df64> k, Phys ph, RKStage rk, double c_E,
+__global__ void __launch_bounds__(128, 5) k_ss_hyb(Grid g, Coef<df64> k, Phys ph, RKStage rk, double c_E,
                                                    const df64* __restrict__ F, const df64* __restrict__ Gw,
                                                    const df64* __restrict__ Rc, const double* __restrict__ Dv,
                                                    const double* __restrict__ Q64,
@@ -1935,7 +1948,7 @@ __global__ void __launch_bounds__(256) k_batch_prims_hyb(const BatchHyb* __restr
     }
 }
 
-__global__ void __launch_bounds__(128, 6) k_batch_ss_hyb(const BatchHyb* __restrict__ insts,
+__global__ void __launch_bounds__(128, 5) k_batch_ss_hyb(const BatchHyb* __restrict__ insts,
                                                          const BatchTile* __restrict__ tiles, int ntiles, int stage,
                                                          int parity) {
     __shared__ BatchHyb I;
