@@ -561,7 +561,7 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
             A.taps(U + j, j, ut);
             A.taps(P, j, pt);
 #pragma unroll
-            for (int a = 0; a < 4; ++a) st[a] = ut[a] + uc[j];
+            for (int a = 0; a < 4; ++a) st[a] = sum(ut[a], uc[j]);
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
                 T qt[4];
@@ -1287,7 +1287,7 @@ __device__ __forceinline__ void ss_grad_hyb_point(const Grid& g, const Coef<df64
         for (int j = 0; j < 3; ++j) {
             df64 t[4];
             taps(Wf + i * n, s.c, s.o[j], t);
-            G[i][j] = k.s1[j] * delta1_taps(t);
+            G[i][j] = mul_nn(k.s1[j], delta1_taps(t));  // unnormalised, as the stencil sums
             Gw[(3 * i + j) * n + s.c] = G[i][j];
         }
     store_pair_sums(G, Gw + 9 * (size_t)n, n, s.c);
