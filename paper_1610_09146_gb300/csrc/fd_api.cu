@@ -179,7 +179,7 @@ Layout plan(long long n, int algorithm, int dtype, size_t wf_points) {
         L.w1 = take(3 * n * sizeof(double));
         L.wd0 = take(10 * n * sizeof(fd::df64));
         L.wd1 = take(10 * n * sizeof(fd::df64));
-        L.gd = take(fd::kGradArrays<fd::df64> * n * sizeof(fd::df64));
+        L.gd = take(fd::kHybGradArrays * n * sizeof(fd::df64));  // G_ii only
         L.dv = take(n * sizeof(double));  // binary64 div u of the stage (gradient pass -> fused kernel)
         L.rc = take(5 * n * sizeof(fd::df64));  // convective part of the residual (first fused kernel)
     } else if (dtype == FD_DF64) {

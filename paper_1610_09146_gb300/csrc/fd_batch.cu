@@ -411,7 +411,7 @@ int fd_batch_create(fd_batch** out, const fd_instance_desc* desc, int count, int
         h.w0 = take(wfields * wpts * tsize);
         h.w1 = take(wfields * wpts * tsize);
         const size_t garrays = dtype == FD_F64 ? fd::kGradArrays<double>
-                               : hyb           ? fd::kGradArrays<fd::df64>
+                               : hyb           ? (size_t)fd::kHybGradArrays
                                                : fd::kGradArrays<float>;
         h.g = desc[i].algorithm == FD_STORE_SOME ? take(garrays * (size_t)h.n * tsize) : (size_t)-1;
         if (hyb) {

@@ -85,6 +85,8 @@ constexpr bool kTapWeighted<double> = true;
 // Gradient arrays of the store-some / recompute-some families per precision.
 template <class T>
 constexpr int kGradArrays = kStoresPairSums<T> ? 12 : 9;
+// Gradient arrays of the mixed binary64 / double-word store-some form: G_ii only.
+constexpr int kHybGradArrays = 3;
 template <>
 struct Prec<double> {
     using S = double;
@@ -196,7 +198,11 @@ __device__ __forceinline__ df64 delta2_taps(const df64 t[4], df64 f0) {
 __device__ __forceinline__ double acc(double a, double b, double c) { return fmx(a, b, c); }
 __device__ __forceinline__ float acc(float a, float b, float c) { return fmx(a, b, c); }
 __device__ __forceinline__ df64 acc(df64 a, df64 b, df64 c) { return add_nn(mul_nn(a, b), c); }
-// The same for a sum a + b, and the final renormalisation of a residual.
+// The same for a product a b and a sum a + b, and the final renormalisation of
+// a residual.
+__device__ __forceinline__ double prod(double a, double b) { return a * b; }
+__device__ __forceinline__ float prod(float a, float b) { return a * b; }
+__device__ __forceinline__ df64 prod(df64 a, df64 b) { return mul_nn(a, b); }
 __device__ __forceinline__ double sum(double a, double b) { return a + b; }
 __device__ __forceinline__ float sum(float a, float b) { return a + b; }
 __device__ __forceinline__ df64 sum(df64 a, df64 b) { return add_nn(a, b); }

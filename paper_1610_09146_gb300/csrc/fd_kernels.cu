@@ -450,8 +450,8 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
                 G[i][j] = k.s1[j] * delta1_taps(t);
             }
     }
-    const T div = G[0][0] + G[1][1] + G[2][2];
-    const T hd = T(-0.5) * div;
+    const T div = sum(sum(G[0][0], G[1][1]), G[2][2]);
+    const T hd = prod(T(-0.5), div);
     // viscous stress divergence v_i = nu [ sum_j D2_j u_i + 1/3 sum_k D_ik u_k ]
     auto viscous = [&](int i) {
         T vi = 0;
@@ -521,7 +521,7 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
         for (int f = 0; f < 5; ++f) R[f] = T(0);
     } else {
 #pragma unroll
-        for (int f = 0; f < 5; ++f) R[f] = A.center(f) * hd;
+        for (int f = 0; f < 5; ++f) R[f] = prod(A.center(f), hd);
     }
 
     // convective sums, pressure gradient and pressure work, direction by direction
@@ -624,15 +624,15 @@ __device__ __forceinline__ void fused_residual(const Acc& A, const Coef<T>& k, T
 
     // viscous dissipation tau_ij D_j u_i
     if constexpr (PART != 1) {
-        T d = G[0][0] * G[0][0];
+        T d = prod(G[0][0], G[0][0]);
         d = acc(G[1][1], G[1][1], d);
         d = acc(G[2][2], G[2][2], d);
-        T s01 = G[0][1] + G[1][0], s02 = G[0][2] + G[2][0], s12 = G[1][2] + G[2][1];
-        T o = s01 * s01;
+        T s01 = sum(G[0][1], G[1][0]), s02 = sum(G[0][2], G[2][0]), s12 = sum(G[1][2], G[2][1]);
+        T o = prod(s01, s01);
         o = acc(s02, s02, o);
         o = acc(s12, s12, o);
         T diss = acc(T(2), d, o);
-        diss = acc(T(-2.0 / 3.0) * div, div, diss);
+        diss = acc(prod(T(-2.0 / 3.0), div), div, diss);
         R[4] = acc(k.nu, diss, R[4]);
     }
     // the perturbation form's mean-state terms (binary64 fields are not shifted)
@@ -1261,11 +1261,19 @@ __global__ void __launch_bounds__(256) k_prims_hyb(Grid g, Phys ph, const double
     hyb_prims_point(ph, q, F, W64, n, idx);
 }
 
-// Gradients of the mixed kernels at one point: the nine double-word gradients
-// as k_ss_grad<df64> forms them (stored, and returned in G), and div u =
-// sum_i D_i u_i in binary64 from the binary64 velocities W64 (as the binary64
-// gradient pass forms D_i u_i), which the second fused kernel reads for the
-// two mean-state terms.
+// One double-word velocity gradient G_ij = D_j u_i at a point, from the taps
+// of u_i along j (both fused kernels form it this way, so the bits agree).
+__device__ __forceinline__ df64 hyb_grad(const Coef<df64>& k, int j, const df64 t[4]) {
+    return mul_nn(k.s1[j], delta1_taps(t));  // unnormalised, as the stencil sums
+}
+// Gradients of the mixed kernels at one point: the three double-word
+// gradients G_ii (stored as Gw[i], returned in G) and div u = sum_i D_i u_i in
+// binary64 from the binary64 velocities W64 (as the binary64 gradient pass
+// forms D_i u_i), which the second fused kernel reads for the two mean-state
+// terms.  The second kernel differences G_jj + G_kk at its neighbours for the
+// mixed derivatives; the six G_ij, i != j, it needs only at the point itself
+// (the dissipation), and forms them there from the u_i taps its viscous terms
+// load anyway (hyb_grad, the same bits).
 __device__ __forceinline__ void ss_grad_hyb_point(const Grid& g, const Coef<df64>& k, const df64* __restrict__ Wf,
                                                   const double* __restrict__ W64, df64* __restrict__ Gw,
                                                   double* __restrict__ Dv, int idx, df64 G[3][3]) {
@@ -1282,15 +1290,14 @@ __device__ __forceinline__ void ss_grad_hyb_point(const Grid& g, const Coef<df64
     }
     Dv[s.c] = fmx(g.inv12h[0], d[0], fmx(g.inv12h[1], d[1], g.inv12h[2] * d[2]));
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i) {
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            df64 t[4];
-            taps(Wf + i * n, s.c, s.o[j], t);
-            G[i][j] = mul_nn(k.s1[j], delta1_taps(t));  // unnormalised, as the stencil sums
-            Gw[(3 * i + j) * n + s.c] = G[i][j];
-        }
-    store_pair_sums(G, Gw + 9 * (size_t)n, n, s.c);
+        for (int j = 0; j < 3; ++j) G[i][j] = df64(0.0f, 0.0f);  // (only G_ii is formed here)
+        df64 t[4];
+        taps(Wf + i * n, s.c, s.o[i], t);
+        G[i][i] = hyb_grad(k, i, t);
+        Gw[(size_t)i * n + s.c] = G[i][i];
+    }
 }
 
 // Fused residual + RK update + next-stage working fields.  F / W64: the
@@ -1310,15 +1317,32 @@ __device__ __forceinline__ void ss_grad_hyb_point(const Grid& g, const Coef<df64
 // blocks of either measured within 1.3 % of this).  The pressure work later
 // moved to the second kernel, which loads its taps anyway (9.10 -> 9.00 ms at
 // five blocks; 9.22 at six, where it spilled).
-// The gradient pass rides in this kernel: the point's nine gradients and
-// binary64 div u (ss_grad_hyb_point, the same bits) are stored for the second
-// kernel, whose stencils read them at neighbouring points, and the convective
-// part takes G_ii from registers.  Its binary64 div u fills the FP64 pipe,
-// idle in the double-word convective sums.
+// The gradient pass rides in this kernel: the point's G_ii and binary64 div u
+// (ss_grad_hyb_point) are stored for the second kernel, whose stencils read the
+// G_ii at neighbouring points, and the convective part takes G_ii from
+// registers.  Its binary64 div u fills the FP64 pipe, idle in the double-word
+// convective sums.
 template <class Acc>
 struct RegGradAcc : Acc {
     const df64 (*Gr)[3];
     __device__ __forceinline__ df64 grad(int i, int j) const { return Gr[i][j]; }
+};
+// The second kernel's view of the gradients: G_ii from the three stored
+// arrays, G_ij (i != j) formed from the u_i taps along j (hyb_grad).
+struct HybRestAcc : GlobalAcc<df64> {
+    const Coef<df64>& k;
+    __device__ __forceinline__ df64 grad(int i, int j) const {
+        if (i == j) return ld(Gw + (size_t)i * n, s.c);
+        df64 t[4];
+        taps(5 + i, j, t);
+        return hyb_grad(k, j, t);
+    }
+    __device__ __forceinline__ void grad_pair_taps(int ga, int gb, int i, df64 t[4]) const {
+        const df64* pa = Gw + (size_t)ga * n;
+        const df64* pb = Gw + (size_t)gb * n;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) t[a] = ld(pa, s.c + s.o[i][a]) + ld(pb, s.c + s.o[i][a]);
+    }
 };
 __device__ __forceinline__ void ss_hyb_conv_point(const Grid& g, const Coef<df64>& k, const df64* __restrict__ F,
                                                   const double* __restrict__ W64, df64* __restrict__ Gw,
@@ -1352,8 +1376,7 @@ __device__ __forceinline__ void ss_hyb_point(const Grid& g, const Coef<df64>& k,
     df64 Rw[5];
     {
         const Nbr s = make_nbr(g, idx);
-        fused_residual<df64, true, GlobalAcc<df64>, false, 2>(GlobalAcc<df64>{s, n, F, F + 5 * (size_t)n, Gw}, k,
-                                                              Rw);
+        fused_residual<df64, true, HybRestAcc, false, 2>(HybRestAcc{{s, n, F, F + 5 * (size_t)n, Gw}, k}, k, Rw);
     }
 #pragma unroll
     for (int f = 0; f < 5; ++f) Rw[f] = renorm(add_nn(Rw[f], ld(Rc + (size_t)f * n, idx)));

@@ -132,7 +132,7 @@ Layout layout_of(const fd_request& r, bool tma) {
     L.w0 = take(wf * wpts * t);
     L.w1 = take(wf * wpts * t);
     const size_t garrays = r.dtype == FD_F64 ? fd::kGradArrays<double>
-                           : hyb             ? fd::kGradArrays<fd::df64>
+                           : hyb             ? (size_t)fd::kHybGradArrays
                                              : fd::kGradArrays<float>;
     L.g = r.algorithm == FD_STORE_SOME ? take(garrays * n * t) : (size_t)-1;
     if (hyb) {
