@@ -1310,13 +1310,15 @@ __device__ __forceinline__ void ss_grad_hyb_point(const Grid& g, const Coef<df64
 // The convective part of the residual (PART 1), into Rc for ss_hyb_point.  The
 // residual is split over two kernels so that each runs at a higher occupancy
 // than the whole residual could (128 registers and 84 bytes of spill at 16 warps
-// per SM): both at five blocks of 128 threads per SM (96 registers), for 40
-// bytes per point written and read again.  The kernels are latency-bound on
-// their tap loads, so the warps pay: 256^3 step 11.53 ms (one kernel) -> 11.01
-// (two, four blocks each) -> 9.63-9.89 (five and six blocks; four to eight
-// blocks of either measured within 1.3 % of this).  The pressure work later
-// moved to the second kernel, which loads its taps anyway (9.10 -> 9.00 ms at
-// five blocks; 9.22 at six, where it spilled).
+// per SM): this one at five blocks of 128 threads per SM (96 registers), the
+// second at six (80 registers and 88 bytes of spill, 1 % faster than five
+// without; the batched form stays at five), for 40 bytes per point written
+// and read again.  The kernels are latency-bound on their tap loads, so the
+// warps pay: 256^3 step 11.53 ms (one kernel) -> 11.01 (two, four blocks
+// each) -> 9.63-9.89 (five and six blocks).  The pressure work later moved to
+// the second kernel, which loads its taps anyway (9.10 -> 9.00 ms), and so
+// did the six off-diagonal gradients (8.74 -> 8.54 ms); forming the
+// dissipation there before the stencil sums was slower (9.63 ms).
 // The gradient pass rides in this kernel: the point's G_ii and binary64 div u
 // (ss_grad_hyb_point) are stored for the second kernel, whose stencils read the
 // G_ii at neighbouring points, and the convective part takes G_ii from
@@ -1421,7 +1423,7 @@ __device__ __forceinline__ void ss_hyb_point(const Grid& g, const Coef<df64>& k,
     }
 }
 template <bool RESID>
-__global__ void __launch_bounds__(128, 5) k_ss_hyb(Grid g, Coef<df64> k, Phys ph, RKStage rk, double c_E,
+__global__ void __launch_bounds__(128, 6) k_ss_hyb(Grid g, Coef<df64> k, Phys ph, RKStage rk, double c_E,
                                                    const df64* __restrict__ F, const df64* __restrict__ Gw,
                                                    const df64* __restrict__ Rc, const double* __restrict__ Dv,
                                                    const double* __restrict__ Q64,
