@@ -115,24 +115,24 @@ COST = {
     # mixed binary64 / double-word store-some (dtype f64dw): flops are the binary64 algorithm's
     # (the binary64 SS kernels' fused pass and gradient pass).  A stage is two kernels: the first
     # reads the conserved fields, u_i and p (9 double-words) and the binary64 u_i, and writes the
-    # nine gradients G, div u and its five convective residuals Rc (216 bytes per point); the
-    # second reads u_i, p, T (5 double-words), G (9), Rc, div u and the saved register, and
-    # writes the state, the saved register (stages 0 and 1), F (10 double-words) and W64 =
-    # (u, v, w) of the next stage (370.7 bytes).  Binary64 instructions per point from ncu at
+    # diagonal gradients G_ii, div u and its five convective residuals Rc (168 bytes per point);
+    # the second reads u_i, p, T (5 double-words), G_ii (3), Rc, div u and the saved register,
+    # and writes the state, the saved register (stages 0 and 1), F (10 double-words) and W64 =
+    # (u, v, w) of the next stage (322.7 bytes).  Binary64 instructions per point from ncu at
     # 160^3
     # binary64 recompute-all with the primitives recomputed at every tap (no primitive arrays):
     # bytes per point read the state taps once and the saved register, write the state and
     # the saved register; flops / instructions from ncu at 160^3 (DADD + DMUL + 2 DFMA)
     ("f64", "recompute_all_inline", "fused"): (3095.7, 133.3, 1774.3),
-    ("f64dw", "store_some", "fused"): (460.7, 586.7, 43.3),
+    ("f64dw", "store_some", "fused"): (460.7, 490.7, 43.3),
     ("f64dw", "*", "prims"): (14, 144, 17),  # reads Q (40 B), writes F (80) and W64 (24)
 }
 # Thread instructions per point of one fused pass (all pipes): ncu's smsp__thread_inst_executed
-# of the two kernels at 160^3, the gradients with the convective part 2144 per point and the rest
-# 2376, 2372, 2342 (stages 0-2, mean 2363.3); the issue-slot cost of the mixed pass.  Its binary64
-# instructions (first kernel DADD 6, DMUL 1, DFMA 5; second DADD 9, DMUL 5, DFMA 19/19/14 per
-# point) give the 43.3 of the cost table.
-ISSUE_COST = {("f64dw", "store_some", "fused"): 4507.3}
+# of the two kernels at 160^3, the diagonal gradients with the convective part 1527 per point and
+# the rest 2723, 2719, 2689 (stages 0-2, mean 2710.3); the issue-slot cost of the mixed pass.  Its
+# binary64 instructions (first kernel DADD 6, DMUL 1, DFMA 5; second DADD 9, DMUL 5, DFMA
+# 19/19/14 per point) give the 43.3 of the cost table.
+ISSUE_COST = {("f64dw", "store_some", "fused"): 4237.3}
 # Kernels launched per timed pass of a class, where a pass is more than one launch.
 KERNELS_PER_PASS = {("f64dw", "store_some", "fused"): 2}
 # FP64 pipe issue peak: 2 instructions per SM per clock.
@@ -300,7 +300,7 @@ def roofline_of(dtype, alg, kern, n, hbm_peak, hbm_src, fp64_peak=None):
 # binary32 RA kernel gives 180.0 B/point at 160^3 and 187.4 at 256^3; its entry is the 256^3 capture
 # of the kernel's current 36 x 12 staging box).  The roofline entry's `traffic` is this times the
 # points of the run.  The mixed store-some entries are a later capture
-# of the same 160^3 grid through the public API (fused pass: both kernels, 209.3 + 362.0).
+# of the same 160^3 grid through the public API (fused pass: both kernels, 154.1 + 325.6).
 TRAFFIC_BPP = {
     ("f64", "store_some", "fused"): 304.5, ("f64", "store_some", "grad"): 105.9,
     ("f64", "recompute_all", "fused"): 205.9, ("f64", "recompute_some", "fused"): 281.0,
@@ -308,7 +308,7 @@ TRAFFIC_BPP = {
     ("f64", "store_all", "fused"): 696.1, ("f64", "store_all", "deriv1"): 578.2,
     ("f64", "store_all", "deriv2"): 187.6, ("f64", "store_all", "products"): 200.4,
     ("f64", "recompute_all_inline", "fused"): 125.3,
-    ("f64dw", "store_some", "fused"): 571.3,
+    ("f64dw", "store_some", "fused"): 479.7,
     ("f32", "store_some", "fused"): 213.4, ("f32", "store_some", "grad"): 34.5,
     ("f32", "recompute_all", "fused"): 187.4, ("f32", "recompute_some", "fused"): 214.1,
     ("f32", "recompute_some", "grad"): 34.5, ("f32", "store_none", "fused"): 175.9,
