@@ -212,11 +212,13 @@ size_t fd_device_bytes(const fd_handle* h);
 /* ---- per-kernel timing ----------------------------------------------------
  * Kernel classes of one stage (Fig. 1), for fd_profile_read:
  *   FD_KERNEL_PRIMS     primitive variables u_i, p, T (Eqs. 6-7), all families
- *   FD_KERNEL_GRAD      SS: the nine stored velocity gradients
+ *   FD_KERNEL_GRAD      SS: the nine stored velocity gradients (not in
+ *                       FD_F64_DW, whose first fused kernel forms them)
  *   FD_KERNEL_FUSED     RA / SS: fused derivatives + residual + RK update;
  *                       BL: pointwise residual + RK update; FD_F64_DW
- *                       store-some: two kernels (the convective terms,
- *                       then the rest with the update), timed as one pass
+ *                       store-some: two kernels (the diagonal gradients,
+ *                       div u and the convective terms, then the rest with
+ *                       the update), timed as one pass
  *   FD_KERNEL_PRODUCTS  BL: product work arrays
  *   FD_KERNEL_DERIV1    BL: first-derivative work arrays
  *   FD_KERNEL_DERIV2    BL: second- and mixed-derivative work arrays */
