@@ -953,7 +953,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--grid", type=int, default=N_GRID)
-    ap.add_argument("--dtype", choices=["f64", "f32", "df64"], default="f64")
+    ap.add_argument("--dtype", choices=["f64", "f32", "df64", "f64dw"], default="f64",
+                    help="arithmetic of the line's families (f64 also times the mixed f64dw store-some form); "
+                         "f64dw: the mixed form alone (store-some)")
     ap.add_argument("--variants", nargs="+", default=VARIANTS, choices=VARIANTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-df64", action="store_true", help="skip the df64 and binary32 families beside the line")
@@ -996,10 +998,14 @@ def main():
             args.steps = 10
         run_sweep(args)
     elif args.workload == "history":
+        if args.dtype == "f64dw":
+            args.variants = ["store_some"]
         if args.variants == VARIANTS:
             args.variants = ["recompute_all" if args.dtype == "f32" else "store_some"]
         run_history(args)
     else:
+        if args.dtype == "f64dw":  # the mixed form exists for the store-some family only
+            args.variants = ["store_some"]
         run_ours(args)
 
 
