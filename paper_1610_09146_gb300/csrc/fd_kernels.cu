@@ -1312,7 +1312,8 @@ __device__ __forceinline__ void ss_grad_hyb_point(const Grid& g, const Coef<df64
 // than the whole residual could (128 registers and 84 bytes of spill at 16 warps
 // per SM): this one at five blocks of 128 threads per SM (96 registers), the
 // second at six (80 registers and 88 bytes of spill, 1 % faster than five
-// without; the batched form stays at five), for 40 bytes per point written
+// without; the batched form runs at four: 26.5 solves/s on the 64-solve
+// ensemble against 26.0 at five and 24.8 at six), for 40 bytes per point written
 // and read again.  The kernels are latency-bound on their tap loads, so the
 // warps pay: 256^3 step 11.53 ms (one kernel) -> 11.01 (two, four blocks
 // each) -> 9.63-9.89 (five and six blocks).  The pressure work later moved to
@@ -1973,7 +1974,7 @@ __global__ void __launch_bounds__(256) k_batch_prims_hyb(const BatchHyb* __restr
     }
 }
 
-__global__ void __launch_bounds__(128, 5) k_batch_ss_hyb(const BatchHyb* __restrict__ insts,
+__global__ void __launch_bounds__(128, 4) k_batch_ss_hyb(const BatchHyb* __restrict__ insts,
                                                          const BatchTile* __restrict__ tiles, int ntiles, int stage,
                                                          int parity) {
     __shared__ BatchHyb I;
